@@ -1,0 +1,296 @@
+/*
+ * messi_oracle.c -- plain FP64 CPU reference of the MESSI exact k-NN method.
+ *
+ * TEST INFRASTRUCTURE ONLY (see messi_oracle.h).  Built with gcc
+ * -O2 -fopenmp -ffp-contract=off so every FP64 operation is a separately
+ * rounded IEEE operation in the order written here.
+ */
+#include "messi_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- Sec. 2.2 */
+
+/* Phi(x) - p, evaluated where it keeps full relative accuracy: through
+ * erfc in the lower tail, through erf (as (Phi(x) - 1/2) - (p - 1/2), both
+ * parts exact or accurately rounded) near the centre. */
+static double cdf_minus(double x, double p)
+{
+    if (x < -0.6) return 0.5 * erfc(-x / sqrt(2.0)) - p;
+    return 0.5 * erf(x / sqrt(2.0)) - (p - 0.5);
+}
+
+/* PhiInv(p) by bisection: shrink [lo, hi] until the two ends are adjacent
+ * doubles, then keep the end whose CDF is nearer p. */
+static double std_normal_quantile(double p)
+{
+    double lo = -40.0, hi = 40.0;
+    for (int it = 0; it < 2000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (cdf_minus(mid, p) < 0.0) lo = mid; else hi = mid;
+    }
+    return (fabs(cdf_minus(lo, p)) < fabs(cdf_minus(hi, p))) ? lo : hi;
+}
+
+void orc_breakpoints(int card, double *beta)
+{
+    /* Lower half by bisection (where erfc is evaluated at positive arguments
+     * and keeps full relative accuracy); the upper half by the symmetry of
+     * N(0,1), PhiInv(1 - p) = -PhiInv(p); the median is 0. */
+    for (int j = 1; 2 * j < card; ++j)
+        beta[j - 1] = std_normal_quantile((double)j / (double)card);
+    for (int j = 1; j < card; ++j) {
+        if (2 * j == card) beta[j - 1] = 0.0;
+        else if (2 * j > card) beta[j - 1] = -beta[card - j - 1];
+    }
+}
+
+void orc_paa(const float *x, int n, int w, double *paa)
+{
+    int m = n / w;
+    for (int s = 0; s < w; ++s) {
+        double sum = 0.0;
+        for (int t = s * m; t < (s + 1) * m; ++t) sum += (double)x[t];
+        paa[s] = sum / (double)m;
+    }
+}
+
+void orc_sax(const double *paa, int w, int card, const double *beta, uint8_t *sym)
+{
+    for (int s = 0; s < w; ++s) {
+        int count = 0;
+        for (int j = 1; j < card; ++j)
+            if (beta[j - 1] <= paa[s]) ++count;
+        sym[s] = (uint8_t)count;
+    }
+}
+
+void orc_summarize(const float *data, int64_t N, int n, int w, int card,
+                   const double *beta, uint8_t *sax)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        double paa[64];
+        orc_paa(data + i * (int64_t)n, n, w, paa);
+        orc_sax(paa, w, card, beta, sax + i * (int64_t)w);
+    }
+}
+
+static int log2_card(int card)
+{
+    int b = 0;
+    while ((1 << b) < card) ++b;
+    return b;
+}
+
+void orc_isax_key(const uint8_t *sym, int w, int card, uint32_t key[4])
+{
+    int b = log2_card(card);
+    key[0] = key[1] = key[2] = key[3] = 0u;
+    for (int j = 0; j < b; ++j)
+        for (int s = 0; s < w; ++s) {
+            int p = j * w + s;                          /* position from the MSB */
+            uint32_t bit = (sym[s] >> (b - 1 - j)) & 1u;
+            key[p / 32] |= bit << (31 - (p % 32));
+        }
+}
+
+/* ---------------------------------------------------------------- Sec. 2.1 */
+
+double orc_ed2(const float *q, const float *x, int n)
+{
+    double s = 0.0;
+    for (int t = 0; t < n; ++t) {
+        double d = (double)q[t] - (double)x[t];
+        s += d * d;
+    }
+    return s;
+}
+
+/* ------------------------------------------------------ Property 1, Sec. 4 */
+
+/* Region [lo, hi] of symbol v: lo = beta_v (-inf for v = 0),
+ * hi = beta_{v+1} (+inf for v = c-1). */
+static double region_lo(int v, const double *beta) { return v == 0 ? -INFINITY : beta[v - 1]; }
+static double region_hi(int v, int card, const double *beta) { return v == card - 1 ? INFINITY : beta[v]; }
+
+double orc_mindist_ed2(const double *paa_q, const uint8_t *sym, int w, int m,
+                       int card, const double *beta)
+{
+    double s = 0.0;
+    for (int k = 0; k < w; ++k) {
+        double lo = region_lo(sym[k], beta), hi = region_hi(sym[k], card, beta);
+        double d = 0.0;
+        if (paa_q[k] < lo) d = lo - paa_q[k];
+        else if (paa_q[k] > hi) d = paa_q[k] - hi;
+        s += d * d;
+    }
+    return (double)m * s;
+}
+
+/* ---------------------------------------------------------------- Sec. 3.4 */
+
+void orc_envelope(const float *q, int n, int r, double *U, double *L)
+{
+    for (int i = 0; i < n; ++i) {
+        int a = i - r < 0 ? 0 : i - r;
+        int b = i + r > n - 1 ? n - 1 : i + r;
+        double hi = (double)q[a], lo = (double)q[a];
+        for (int j = a + 1; j <= b; ++j) {
+            if ((double)q[j] > hi) hi = (double)q[j];
+            if ((double)q[j] < lo) lo = (double)q[j];
+        }
+        U[i] = hi;
+        L[i] = lo;
+    }
+}
+
+double orc_lb_keogh2(const double *U, const double *L, const float *x, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double c = (double)x[i], d = 0.0;
+        if (c > U[i]) d = c - U[i];
+        else if (c < L[i]) d = c - L[i];
+        s += d * d;
+    }
+    return s;
+}
+
+double orc_mindist_dtw2(const double *paaU, const double *paaL, const uint8_t *sym,
+                        int w, int m, int card, const double *beta)
+{
+    double s = 0.0;
+    for (int k = 0; k < w; ++k) {
+        double lo = region_lo(sym[k], beta), hi = region_hi(sym[k], card, beta);
+        double d = 0.0;
+        if (paaU[k] < lo) d = lo - paaU[k];          /* ABOVE */
+        else if (paaL[k] > hi) d = paaL[k] - hi;     /* BELOW */
+        s += d * d;                                  /* IN: 0 */
+    }
+    return (double)m * s;
+}
+
+double orc_dtw2(const float *q, const float *x, int n, int r)
+{
+    /* D is an n x n table; only cells inside the window are ever written or
+     * read (a cell outside the window is +inf and never the minimum). */
+    static __thread double *D = NULL;
+    static __thread size_t cap = 0;
+    size_t need = (size_t)n * (size_t)n;
+    if (need > cap) {
+        free(D);
+        D = (double *)malloc(sizeof(double) * need);
+        cap = need;
+    }
+    if (r > n - 1) r = n - 1;
+    for (int i = 0; i < n; ++i) {
+        int jlo = i - r < 0 ? 0 : i - r;
+        int jhi = i + r > n - 1 ? n - 1 : i + r;
+        for (int j = jlo; j <= jhi; ++j) {
+            double d = (double)q[i] - (double)x[j];
+            double cost = d * d;
+            double best;
+            if (i == 0 && j == 0) best = 0.0;
+            else {
+                best = INFINITY;
+                if (i > 0 && abs(i - 1 - j) <= r && D[(size_t)(i - 1) * n + j] < best)
+                    best = D[(size_t)(i - 1) * n + j];
+                if (j > 0 && abs(i - (j - 1)) <= r && D[(size_t)i * n + j - 1] < best)
+                    best = D[(size_t)i * n + j - 1];
+                if (i > 0 && j > 0 && D[(size_t)(i - 1) * n + j - 1] < best)
+                    best = D[(size_t)(i - 1) * n + j - 1];
+            }
+            D[(size_t)i * n + j] = cost + best;
+        }
+    }
+    return D[need - 1];
+}
+
+/* ------------------------------------------------------- k-NN, Sec. 5.4 */
+
+/* (d2, id) lexicographic order. */
+static int before(double da, int64_t ia, double db, int64_t ib)
+{
+    return da < db || (da == db && ia < ib);
+}
+
+/* Insert (d, id) into a sorted array of capacity k holding *cnt entries. */
+static void topk_insert(double *kd, int64_t *ki, int *cnt, int k, double d, int64_t id)
+{
+    if (*cnt == k && !before(d, id, kd[k - 1], ki[k - 1])) return;
+    int pos = (*cnt < k) ? (*cnt)++ : k - 1;
+    while (pos > 0 && before(d, id, kd[pos - 1], ki[pos - 1])) {
+        kd[pos] = kd[pos - 1];
+        ki[pos] = ki[pos - 1];
+        --pos;
+    }
+    kd[pos] = d;
+    ki[pos] = id;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_knn(const float *data, int64_t N, int n, const float *queries, int nq,
+             int k, int dist, int r, int64_t id_base, int threads,
+             int64_t *ids, double *d2)
+{
+    int T = threads > 0 ? threads : orc_max_threads();
+    if (T < 1) T = 1;
+    /* Each worker scans a contiguous block of rows and keeps its own k best
+     * per query; the blocks partition the rows, so the k best of the union
+     * of the per-block results is the k best of all rows. */
+    size_t slots = (size_t)T * (size_t)nq * (size_t)k;
+    double *bd = (double *)malloc(sizeof(double) * slots);
+    int64_t *bi = (int64_t *)malloc(sizeof(int64_t) * slots);
+    int *bc = (int *)calloc((size_t)T * (size_t)nq, sizeof(int));
+
+#pragma omp parallel num_threads(T)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+        int nt = omp_get_num_threads();
+#else
+        int nt = 1;
+#endif
+        int64_t lo = N * t / nt, hi = N * (t + 1) / nt;
+        for (int64_t row = lo; row < hi; ++row) {
+            const float *x = data + row * (int64_t)n;
+            for (int qi = 0; qi < nq; ++qi) {
+                const float *q = queries + (int64_t)qi * n;
+                double d = (dist == 0) ? orc_ed2(q, x, n) : orc_dtw2(q, x, n, r);
+                size_t base = ((size_t)t * nq + qi) * (size_t)k;
+                topk_insert(bd + base, bi + base, &bc[(size_t)t * nq + qi], k, d, id_base + row);
+            }
+        }
+    }
+
+    for (int qi = 0; qi < nq; ++qi) {
+        int cnt = 0;
+        double *od = d2 + (size_t)qi * k;
+        int64_t *oi = ids + (size_t)qi * k;
+        for (int t = 0; t < T; ++t) {
+            size_t base = ((size_t)t * nq + qi) * (size_t)k;
+            for (int e = 0; e < bc[(size_t)t * nq + qi]; ++e)
+                topk_insert(od, oi, &cnt, k, bd[base + e], bi[base + e]);
+        }
+        for (int e = cnt; e < k; ++e) { od[e] = INFINITY; oi[e] = -1; }
+    }
+    free(bd);
+    free(bi);
+    free(bc);
+}

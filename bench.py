@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Exact k-NN throughput of the GB300 iSAX engine (MESSI, arXiv 2110.07519).
+
+Workload (default): 100,000,000 seeded random walks of length 256, z-normalised
+(the paper's 100 GB synthetic collection, Sec. 5.1), iSAX with 16 segments and
+8-bit symbols; queries half fresh random walks, half dataset members plus
+N(0, sigma) noise, sigma in {0.1, 0.5, 1.0} (Sec. 5.3); exact 1-NN under ED.
+A step answers one batch of queries against the resident index.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(brute force) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact 1-NN queries/sec and p50/p99 ms on 100M x 256 fp32 ED at 1 GB300; % HBM roofline"
+PAPER_QPS = 20.0          # ~50 ms per exact 1-NN ED query on 100M x 256 (paper, 2x Xeon E5-2650 v4)
+DATA_DESC = ("synthetic: seeded random walks (x0~N(0,1), x_t=x_{t-1}+N(0,1)), z-normalised; queries half "
+             "fresh walks (separate seed), half dataset members + N(0,sigma) noise, sigma 0.1/0.5/1.0")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="messi", choices=["messi", "reference"])
+    ap.add_argument("--n", type=int, default=100_000_000)
+    ap.add_argument("--len", type=int, default=256)
+    ap.add_argument("--batch", type=int, default=256, help="queries per step")
+    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--cpu-sample", type=int, default=4, help="queries in the CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def scan_source_sha():
+    h = hashlib.sha256()
+    for name in ("query.cu", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2110_07519_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(n_series: int):
+    """DRAM bytes per scan launch from the committed ncu summary, scaled to
+    n_series, or None when the scan source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "lb_scan_traffic.txt")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    sha = re.search(r"source_sha:\s*(\w+)", text)
+    per = re.search(r"dram_bytes_per_series:\s*([0-9.eE+-]+)", text)
+    if not sha or not per or sha.group(1) != scan_source_sha():
+        return None
+    return float(per.group(1)) * n_series
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(data_t, queries_np, k, chunk=1 << 20):
+    """FP64 brute force of `queries_np` over the device collection `data_t`,
+    copied to the host chunk by chunk; returns (ids, d2, cpu_seconds, threads)."""
+    import torch
+
+    import oracle
+
+    best = None
+    cpu_s = 0.0
+    N = data_t.shape[0]
+    host = torch.empty((min(chunk, N), data_t.shape[1]), dtype=torch.float32, pin_memory=True)
+    for lo in range(0, N, chunk):
+        hi = min(N, lo + chunk)
+        host[: hi - lo].copy_(data_t[lo:hi])
+        rows = host[: hi - lo].numpy()
+        t0 = time.perf_counter()
+        part = oracle.knn(rows, queries_np, k, oracle.ED, id_base=lo)
+        best = part if best is None else oracle.merge_topk([best, part], k)
+        cpu_s += time.perf_counter() - t0
+    return best[0], best[1], cpu_s, oracle.max_threads()
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, ws, rank, local):
+    if rank != 0:
+        return
+    import torch
+
+    import oracle
+    import synth
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    oracle.build()
+    data = synth.random_walks_torch(args.n, args.len, device=dev)
+    qpool = synth.query_mix_torch(data, args.warmup + args.steps, seed=synth.QUERY_SEED).cpu().numpy()
+    times = []
+    threads = oracle.max_threads()
+    for step in range(args.warmup + args.steps):
+        _, _, cpu_s, threads = oracle_sample(data, qpool[step:step + 1], args.k)
+        if step >= args.warmup:
+            times.append(cpu_s)
+    total = sum(times)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_QPS, "dtype": "f64",
+        "data": DATA_DESC,
+        "config": {"workload": f"{args.n} x {args.len} fp32 random walks, ED, k={args.k}",
+                   "queries_per_step": 1, "l2": "inputs larger than L2 (host memory)"},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} timed queries (1 per step), FP64 brute force over all "
+                                   f"{args.n} series; device-to-host chunk copies excluded"},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- GPU arm
+def run_messi(args, ws, rank, local):
+    import torch
+
+    import paper_2110_07519_gb300 as m
+    import synth
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    B, K, W = args.batch, args.steps, args.warmup
+
+    data = synth.random_walks_torch(args.n, args.len, seed=synth.DATASET_SEED + rank, device=dev)
+    torch.cuda.synchronize()
+    ix = m.messi_build(data, 16, 256)
+    info = m.messi_index_get_info(ix)
+    build_gbps = args.n * args.len * 4 / (info["build_ms"] * 1e-3) / 1e9
+    qpool = synth.query_mix_torch(data, (W + K) * B, seed=synth.QUERY_SEED + rank)
+    ids = torch.empty((B, args.k), dtype=torch.int64, device=dev)
+    dists = torch.empty((B, args.k), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    m.messi_set_profiling(ix, True)
+    for s in range(W):
+        m.messi_query(ix, qpool[s * B:(s + 1) * B], k=args.k, ids=ids, dists=dists)
+    m.messi_check(ix)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = ClockSampler(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    scan_ms, scan_launches, launches, lat = 0.0, 0, 0, []
+    survivors, refined = 0, 0
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(W, W + K):
+        m.messi_query(ix, qpool[s * B:(s + 1) * B], k=args.k, ids=ids, dists=dists)
+        st = m.messi_query_stats(ix)
+        scan_ms += st["scan_ms"]
+        scan_launches += st["scan_launches"]
+        launches += st["kernel_launches"]
+        survivors += st["lb_survivors"]
+        refined += st["refined"]
+        lat += [st["query_ms_p50"], st["query_ms_p99"]]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    m.messi_check(ix)
+    if pg:
+        t = torch.tensor([elapsed_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = ws * B * K / (elapsed_ms * 1e-3)
+
+    # per-query latency percentiles over the timed queries (separate pass so the
+    # percentile covers every query, not per-step summaries)
+    m.messi_query(ix, qpool[W * B:(W + K) * B], k=args.k)
+    st_all = m.messi_query_stats(ix)
+    m.messi_set_profiling(ix, False)
+
+    # roofline of the dominant kernel (the iSAX lower-bound scan)
+    scan_avg_s = scan_ms * 1e-3 / max(scan_launches, 1)
+    algo_bytes = 16.0 * args.n
+    achieved = algo_bytes / scan_avg_s / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    traffic = profiled_traffic(args.n)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if not args.no_e2e:
+        hq = qpool[W * B:(W + K) * B].cpu().pin_memory().numpy()
+        hids = torch.empty((B, args.k), dtype=torch.int64).pin_memory().numpy()
+        hd = torch.empty((B, args.k), dtype=torch.float32).pin_memory().numpy()
+        m.messi_query(ix, hq[:B], k=args.k, ids=hids, dists=hd)
+        t0 = time.perf_counter()
+        for s in range(K):
+            m.messi_query(ix, hq[s * B:(s + 1) * B], k=args.k, ids=hids, dists=hd)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": ws * B * K / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": B * args.len * 4,
+               "d2h_bytes_per_step": B * args.k * 12}
+
+    # FP64 oracle on a bounded sample: the CPU baseline and a parity spot check
+    cpu = None
+    parity = None
+    if rank == 0 and not args.no_cpu_baseline and args.cpu_sample > 0:
+        qs = qpool[W * B:W * B + args.cpu_sample].cpu().numpy()
+        r_ids, r_d2, cpu_s, threads = oracle_sample(data, qs, args.k)
+        g_ids, g_d = m.messi_query(ix, qs, k=args.k)
+        rel = np.abs(g_d.astype(np.float64) - np.sqrt(r_d2)) / np.maximum(np.sqrt(r_d2), 1e-30)
+        parity = {"ids_equal": bool(np.array_equal(g_ids, r_ids)), "max_rel_err": float(rel.max()),
+                  "queries": int(args.cpu_sample)}
+        cpu = {"value": args.cpu_sample / cpu_s, "unit": "queries/s", "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_sample} queries of the timed mix, FP64 brute force over all {args.n} "
+                         f"series (1M-row chunks copied to the host; copy time excluded)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value / PAPER_QPS, "dtype": "f32", "data": DATA_DESC,
+            "config": {"workload": f"{args.n} x {args.len} fp32 random walks, ED, k={args.k}, 16 segments, "
+                                   f"8-bit SAX, plain per-query path",
+                       "queries_per_step": B, "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (16 B iSAX word per series streamed per query)"},
+            "p50_ms": st_all["query_ms_p50"], "p99_ms": st_all["query_ms_p99"],
+            "build_gbps": build_gbps, "build_ms": info["build_ms"],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_lb_scan",
+                         "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
+                         "avg_launch_ms": scan_avg_s * 1e3},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "parity_sample": parity,
+            "counters": {"lb_survivors_per_query": survivors / (B * K), "refined_per_query": refined / (B * K)},
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank, local)
+    else:
+        run_messi(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

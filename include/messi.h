@@ -1,0 +1,184 @@
+/*
+ * messi.h -- C ABI of the GB300 exact k-NN engine over an in-memory iSAX
+ * index (MESSI, arXiv 2110.07519).
+ *
+ * Problem (Sec. 2.1, "Similarity Search"): given a collection of N series of
+ * length len and a query series of the same length, return the k series with
+ * the smallest Euclidean distance (ED) or Dynamic Time Warping distance under
+ * a Sakoe-Chiba window (DTW, Sec. 3.4).  The answer is exact: ids and
+ * distances equal a brute-force scan (Theorem 2, Sec. 4), with ties between
+ * equal distances broken by the lowest original id.
+ *
+ * Conventions for every call:
+ *   - Returns a messi_status; nothing throws.  On failure messi_last_error()
+ *     gives a thread-local message.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is stream-ordered; a call returns once its work
+ *     is queued, except where its comment says it synchronises.
+ *   - Pointers named "device or host" may point to either; host pointers
+ *     are detected with cudaPointerGetAttributes and staged through device
+ *     buffers inside the call, which then synchronises `stream` before it
+ *     returns so the host outputs are valid.
+ *   - Series are row-major float32 [n][len].  Output ids are int64 original
+ *     0-based row indices; dists are float32 distances (square roots).
+ *   - Device-side faults of a kernel (a bounded wait that ran out, an
+ *     invalid query value) are recorded in a status word of the index and
+ *     reported by messi_check().
+ *
+ * Limits: 1 <= len <= 4096 with len % segments == 0 and m = len / segments
+ * a power of two >= 4; 1 <= segments <= 16; cardinality a power of two in
+ * [2, 256]; 1 <= n < 2^32 - 1; 1 <= k <= min(n, 1024); window < len.
+ */
+#ifndef MESSI_H
+#define MESSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct messi_index messi_index;
+typedef struct messi_server messi_server;
+typedef void *messi_stream; /* cudaStream_t */
+
+typedef enum { MESSI_ED = 0, MESSI_DTW = 1 } messi_dist;
+
+typedef enum {
+    MESSI_OK = 0,
+    MESSI_EINVAL = 1,   /* an argument is outside the documented limits       */
+    MESSI_ENOMEM = 2,   /* device or pinned-host allocation failed            */
+    MESSI_ECUDA = 3,    /* a CUDA runtime call failed                         */
+    MESSI_ETIMEOUT = 4, /* a device-side bounded wait ran out                 */
+    MESSI_EBUSY = 5,    /* result not ready yet (server poll) / queue full    */
+    MESSI_ETIES = 6     /* more near-ties than the exact tie resolver holds   */
+} messi_status;
+
+/* Build options.  Zero-initialised fields take their defaults. */
+typedef struct {
+    uint32_t leaf_capacity; /* max series per leaf before it splits; default
+                               2000 (Sec. 5.2, "Parameter Tuning") */
+    uint32_t reserved[7];
+} messi_config;
+
+/* Counters of the most recent messi_query / messi_query_batched call. */
+typedef struct {
+    uint64_t queries;
+    uint64_t lb_evaluated;    /* series whose iSAX lower bound was computed   */
+    uint64_t lb_survivors;    /* series that passed the iSAX lower bound      */
+    uint64_t lbk_survivors;   /* DTW: series that passed LB_Keogh             */
+    uint64_t seeded;          /* series refined unconditionally in seed leaves */
+    uint64_t refined;         /* real distances computed to the end           */
+    uint64_t abandoned;       /* real distances abandoned early               */
+    uint64_t bsf_updates;     /* improvements of the k-th best distance       */
+    uint64_t tie_rechecks;    /* FP64 recomputations of near-tied candidates  */
+    uint64_t kernel_launches; /* kernels this call queued                     */
+    uint64_t scan_launches;   /* lower-bound scan launches (profiling mode)   */
+    double scan_ms;           /* summed scan durations, CUDA events (profiling) */
+    double query_ms_p50;      /* per-query device latency (profiling mode)    */
+    double query_ms_p99;
+    uint64_t reserved[6];
+} messi_stats;
+
+typedef struct {
+    uint64_t n_series;
+    uint32_t len, segments, cardinality, leaf_capacity;
+    uint64_t n_leaves;
+    uint64_t max_leaf_size;
+    uint64_t device_bytes;    /* bytes of device memory the index holds       */
+    double build_ms;          /* device time of the last build                */
+} messi_index_info;
+
+/* ---------------------------------------------------------------- build --
+ * Index construction (Sec. 3.2, Algorithms 1-4): every series is summarised
+ * by PAA and SAX (Sec. 2.2), the interleaved iSAX words are radix-sorted, and
+ * the sorted run is cut into leaves of at most leaf_capacity series by
+ * splitting on one iSAX bit at a time (the root has one child per value of
+ * the first bit of each segment).  The raw series are copied into leaf order.
+ *
+ * series      device or host, n*len float32; copied, so the caller may free it
+ *             after the call returns.  Must be finite.
+ * cfg         may be NULL.
+ * out         receives the index; release with messi_free.
+ * Synchronises `stream`.  Returns EINVAL for invalid sizes or non-finite
+ * values, ENOMEM when the device cannot hold the index. */
+messi_status messi_build(const float *series, uint64_t n, uint32_t len, uint32_t segments,
+                         uint32_t cardinality, const messi_config *cfg, messi_stream stream,
+                         messi_index **out);
+
+/* Release every device allocation of the index.  NULL is a no-op. */
+void messi_free(messi_index *ix);
+
+messi_status messi_index_get_info(const messi_index *ix, messi_index_info *out);
+
+/* ---------------------------------------------------------------- query --
+ * Exact k-NN (Algorithm 5 for ED, Sec. 3.4 for DTW; k-NN as a sorted array
+ * of the k best, Sec. 5.4), one query after another as in the paper's
+ * protocol (Sec. 5.1).  Per query: summarise the query (its PAA, or the PAA
+ * of its LB_Keogh envelope for DTW), seed the best-so-far from the query's
+ * own leaf (approxSearch, Sec. 3.1), stream every iSAX word through the
+ * lower bound, compact the survivors, refine them with ED (Algorithm 9) or
+ * LB_Keogh-filtered DTW (Algorithm 10), and resolve near-ties in FP64.
+ *
+ * queries     device or host, nq*len float32.
+ * window      DTW Sakoe-Chiba reach r in points (ignored for ED); r < len.
+ * ids, dists  device or host, nq*k each, row q sorted by (dist, id).
+ * A query holding a non-finite value yields ids -1 and dists NaN for its row
+ * and a MESSI_EINVAL status in messi_check(). */
+messi_status messi_query(const messi_index *ix, const float *queries, uint32_t nq, uint32_t k,
+                         messi_dist dist, uint32_t window, int64_t *ids, float *dists,
+                         messi_stream stream);
+
+/* Batched form: up to `batch` queries share one pass over the iSAX words in a
+ * persistent fused lower-bound-then-refine kernel (no counterpart in the
+ * paper, which answers queries one at a time).  Same arguments and results
+ * as messi_query; batch = 0 picks the tuned default. */
+messi_status messi_query_batched(const messi_index *ix, const float *queries, uint32_t nq,
+                                 uint32_t k, messi_dist dist, uint32_t window, uint32_t batch,
+                                 int64_t *ids, float *dists, messi_stream stream);
+
+/* Lower bounds of one query against every series, in original id order:
+ * lb2[i] = squared iSAX mindist (ED, Property 1 in Sec. 4) or squared
+ * envelope mindist (DTW, Sec. 3.4) as the query kernels use it (each term
+ * rounded down, so lb2[i] never exceeds the exact bound).
+ * query device or host len floats; lb2 device or host n floats. */
+messi_status messi_lower_bounds(const messi_index *ix, const float *query, messi_dist dist,
+                                uint32_t window, float *lb2, messi_stream stream);
+
+/* Counters of the last query call.  Synchronises the index's last stream. */
+messi_status messi_query_stats(const messi_index *ix, messi_stats *out);
+
+/* Profiling mode: record CUDA events around every scan launch and every
+ * query, reported by messi_query_stats.  Off by default. */
+messi_status messi_set_profiling(messi_index *ix, int enable);
+
+/* Synchronise `stream` and report (then clear) the device status word. */
+messi_status messi_check(const messi_index *ix, messi_stream stream);
+
+/* ------------------------------------------------------- summaries -------
+ * PAA + SAX of n series (Sec. 2.2; ConvertToiSAX in Algorithm 3) without
+ * building an index.  words receives n*16 bytes: byte s of word i is the
+ * symbol of segment s (0 = lowest region) for s < segments, 0 beyond.
+ * series, words: device or host. */
+messi_status messi_summarize(const float *series, uint64_t n, uint32_t len, uint32_t segments,
+                             uint32_t cardinality, uint8_t *words, messi_stream stream);
+
+/* Leaf layout of an index (for inspection and tests).  order: n uint32
+ * original ids in leaf order; leaf_off: n_leaves+1 uint64; leaf_depth:
+ * n_leaves uint8 (key prefix bits of each leaf).  Host pointers; any may be
+ * NULL.  Synchronises. */
+messi_status messi_index_layout(const messi_index *ix, uint32_t *order, uint64_t *leaf_off,
+                                uint8_t *leaf_depth);
+
+/* The FP64 breakpoints the library uses (Sec. 2.2: N(0,1) quantiles j/c,
+ * j = 1..c-1).  Host only, no GPU needed.  out: cardinality-1 doubles. */
+messi_status messi_breakpoints(uint32_t cardinality, double *out);
+
+/* Thread-local description of the last failure ("" when none). */
+const char *messi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MESSI_H */

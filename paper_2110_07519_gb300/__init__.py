@@ -1,0 +1,282 @@
+"""Python binding of the GB300 exact k-NN engine over an iSAX index (MESSI,
+arXiv 2110.07519).
+
+Argument marshalling only: every step of index construction and query
+answering runs in the CUDA kernels of ``libmessi.so`` (C ABI in
+``include/messi.h``).  PyTorch supplies device memory and streams; numpy
+arrays (host memory) are accepted too and staged by the library.  Importing
+this package fails loudly when the compiled library is missing -- there is no
+CPU fallback.
+
+Names mirror the C ABI: ``messi_build``, ``messi_query``, ... .
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmessi.so")
+
+MESSI_ED, MESSI_DTW = 0, 1
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY", 6: "ETIES"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(the CUDA library is required; there is no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P, _U32, _U64, _I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+
+
+class MessiConfig(ctypes.Structure):
+    _fields_ = [("leaf_capacity", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
+
+
+class MessiStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "queries", "lb_evaluated", "lb_survivors", "lbk_survivors", "seeded", "refined", "abandoned",
+        "bsf_updates", "tie_rechecks", "kernel_launches", "scan_launches")] + [
+        ("scan_ms", ctypes.c_double), ("query_ms_p50", ctypes.c_double), ("query_ms_p99", ctypes.c_double),
+        ("reserved", ctypes.c_uint64 * 6)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
+
+
+class MessiIndexInfo(ctypes.Structure):
+    _fields_ = [("n_series", ctypes.c_uint64), ("len", ctypes.c_uint32), ("segments", ctypes.c_uint32),
+                ("cardinality", ctypes.c_uint32), ("leaf_capacity", ctypes.c_uint32),
+                ("n_leaves", ctypes.c_uint64), ("max_leaf_size", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_SIGS = {
+    "messi_build": [_P, _U64, _U32, _U32, _U32, _P, _P, ctypes.POINTER(_P)],
+    "messi_free": [_P],
+    "messi_index_get_info": [_P, ctypes.POINTER(MessiIndexInfo)],
+    "messi_query": [_P, _P, _U32, _U32, _I, _U32, _P, _P, _P],
+    "messi_query_batched": [_P, _P, _U32, _U32, _I, _U32, _U32, _P, _P, _P],
+    "messi_lower_bounds": [_P, _P, _I, _U32, _P, _P],
+    "messi_query_stats": [_P, ctypes.POINTER(MessiStats)],
+    "messi_set_profiling": [_P, _I],
+    "messi_check": [_P, _P],
+    "messi_summarize": [_P, _U64, _U32, _U32, _U32, _P, _P],
+    "messi_index_layout": [_P, _P, _P, _P],
+    "messi_breakpoints": [_U32, _P],
+    "messi_last_error": [],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = ctypes.c_char_p if _name == "messi_last_error" else (None if _name == "messi_free" else _I)
+
+
+class MessiError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.messi_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise MessiError(st, where)
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+# ------------------------------------------------------------- marshalling
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, keepalive, is_cuda) of a torch tensor or numpy array."""
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), x, bool(x.is_cuda)
+    a = np.ascontiguousarray(x)
+    return ctypes.c_void_p(a.ctypes.data), a, False
+
+
+def _stream(stream, like=None):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if like is not None and _is_torch(like) and like.is_cuda:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream(like.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _f32(x):
+    if _is_torch(x):
+        import torch
+
+        return x if x.dtype == torch.float32 and x.is_contiguous() else x.to(torch.float32).contiguous()
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+@dataclass
+class Index:
+    handle: ctypes.c_void_p
+    n: int
+    len: int
+    segments: int
+    cardinality: int
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.messi_free(h)
+            self.handle = None
+
+    def free(self):
+        self.__del__()
+
+
+# ------------------------------------------------------------------- calls
+def messi_build(series, segments: int = 16, cardinality: int = 256, leaf_capacity: int = 0,
+                stream=None) -> Index:
+    series = _f32(series)
+    n, length = series.shape
+    p, keep, _ = _ptr(series)
+    cfg = MessiConfig()
+    cfg.leaf_capacity = leaf_capacity
+    out = ctypes.c_void_p()
+    _check(_lib.messi_build(p, n, length, segments, cardinality, ctypes.byref(cfg),
+                            _stream(stream, series), ctypes.byref(out)), "messi_build")
+    return Index(out, n, length, segments, cardinality)
+
+
+def _outputs(nq, k, on_cuda, device=None):
+    if on_cuda:
+        import torch
+
+        return (torch.empty((nq, k), dtype=torch.int64, device=device),
+                torch.empty((nq, k), dtype=torch.float32, device=device))
+    return np.empty((nq, k), dtype=np.int64), np.empty((nq, k), dtype=np.float32)
+
+
+def messi_query(index: Index, queries, k: int = 1, dist: int = MESSI_ED, window: int = 0,
+                ids=None, dists=None, stream=None):
+    """Exact k-NN of every query row; returns (ids int64 [nq,k], dists f32 [nq,k])."""
+    queries = _f32(queries)
+    if queries.ndim == 1:
+        queries = queries.reshape(1, -1)
+    nq = queries.shape[0]
+    qp, qkeep, qcuda = _ptr(queries)
+    if ids is None or dists is None:
+        ids, dists = _outputs(nq, k, qcuda, queries.device if qcuda else None)
+    ip, ikeep, _ = _ptr(ids)
+    dp, dkeep, _ = _ptr(dists)
+    _check(_lib.messi_query(index.handle, qp, nq, k, dist, window, ip, dp, _stream(stream, queries)),
+           "messi_query")
+    return ids, dists
+
+
+def messi_query_batched(index: Index, queries, k: int = 1, dist: int = MESSI_ED, window: int = 0,
+                        batch: int = 0, ids=None, dists=None, stream=None):
+    queries = _f32(queries)
+    if queries.ndim == 1:
+        queries = queries.reshape(1, -1)
+    nq = queries.shape[0]
+    qp, qkeep, qcuda = _ptr(queries)
+    if ids is None or dists is None:
+        ids, dists = _outputs(nq, k, qcuda, queries.device if qcuda else None)
+    ip, ikeep, _ = _ptr(ids)
+    dp, dkeep, _ = _ptr(dists)
+    _check(_lib.messi_query_batched(index.handle, qp, nq, k, dist, window, batch, ip, dp,
+                                    _stream(stream, queries)), "messi_query_batched")
+    return ids, dists
+
+
+def messi_lower_bounds(index: Index, query, dist: int = MESSI_ED, window: int = 0, out=None, stream=None):
+    query = _f32(query).reshape(-1)
+    qp, qkeep, qcuda = _ptr(query)
+    if out is None:
+        if qcuda:
+            import torch
+
+            out = torch.empty(index.n, dtype=torch.float32, device=query.device)
+        else:
+            out = np.empty(index.n, dtype=np.float32)
+    op, okeep, _ = _ptr(out)
+    _check(_lib.messi_lower_bounds(index.handle, qp, dist, window, op, _stream(stream, query)),
+           "messi_lower_bounds")
+    return out
+
+
+def messi_summarize(series, segments: int = 16, cardinality: int = 256, stream=None):
+    """iSAX words of every row: uint8 [n, 16] (byte s = symbol of segment s)."""
+    series = _f32(series)
+    n, length = series.shape
+    sp, skeep, scuda = _ptr(series)
+    if scuda:
+        import torch
+
+        out = torch.empty((n, 16), dtype=torch.uint8, device=series.device)
+    else:
+        out = np.empty((n, 16), dtype=np.uint8)
+    op, okeep, _ = _ptr(out)
+    _check(_lib.messi_summarize(sp, n, length, segments, cardinality, op, _stream(stream, series)),
+           "messi_summarize")
+    return out
+
+
+def messi_index_get_info(index: Index) -> dict:
+    info = MessiIndexInfo()
+    _check(_lib.messi_index_get_info(index.handle, ctypes.byref(info)), "messi_index_get_info")
+    return info.as_dict()
+
+
+def messi_index_layout(index: Index):
+    """(order uint32 [n], leaf_off uint64 [L+1], leaf_depth uint8 [L]) on the host."""
+    info = messi_index_get_info(index)
+    L = info["n_leaves"]
+    order = np.empty(index.n, dtype=np.uint32)
+    off = np.empty(L + 1, dtype=np.uint64)
+    depth = np.empty(L, dtype=np.uint8)
+    _check(_lib.messi_index_layout(index.handle, order.ctypes.data, off.ctypes.data, depth.ctypes.data),
+           "messi_index_layout")
+    return order, off, depth
+
+
+def messi_query_stats(index: Index) -> dict:
+    st = MessiStats()
+    _check(_lib.messi_query_stats(index.handle, ctypes.byref(st)), "messi_query_stats")
+    return st.as_dict()
+
+
+def messi_set_profiling(index: Index, enable: bool = True):
+    _check(_lib.messi_set_profiling(index.handle, 1 if enable else 0), "messi_set_profiling")
+
+
+def messi_check(index: Index, stream=None):
+    _check(_lib.messi_check(index.handle, _stream(stream)), "messi_check")
+
+
+def messi_breakpoints(cardinality: int) -> np.ndarray:
+    out = np.empty(cardinality - 1, dtype=np.float64)
+    _check(_lib.messi_breakpoints(cardinality, out.ctypes.data), "messi_breakpoints")
+    return out
+
+
+def messi_free(index: Index):
+    """Release the index's device memory now (also done when it is collected)."""
+    index.free()
+
+
+def messi_last_error() -> str:
+    return _lib.messi_last_error().decode(errors="replace")

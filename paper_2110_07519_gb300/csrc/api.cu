@@ -1,0 +1,635 @@
+// api.cu -- the C ABI declared in include/messi.h: argument checks, device
+// allocation, host<->device staging and the per-query kernel sequence.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "messi_internal.cuh"
+
+namespace messi {
+
+namespace {
+thread_local std::string g_last_error;
+
+bool is_pow2(unsigned v) { return v && !(v & (v - 1)); }
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+std::mutex g_attr_mu;
+std::vector<int> g_attr_done;
+
+void ensure_attributes()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (std::find(g_attr_done.begin(), g_attr_done.end(), dev) != g_attr_done.end()) return;
+    init_kernel_attributes();
+    g_attr_done.push_back(dev);
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Growable device buffer owned by the index (host staging of inputs/outputs).
+bool ensure_stage(messi_index *ix, size_t bytes)
+{
+    if (ix->stage_bytes >= bytes) return true;
+    if (ix->stage_block) cudaFree(ix->stage_block);
+    ix->stage_block = nullptr;
+    ix->stage_bytes = 0;
+    if (cudaMalloc(&ix->stage_block, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    ix->stage_bytes = bytes;
+    return true;
+}
+
+// Plain-path workspace: one query slot with survivor arrays of N entries.
+messi_status ensure_workspace(messi_index *ix)
+{
+    if (ix->ws_block) return MESSI_OK;
+    const size_t N = ix->N, len = ix->len;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t o_st = take(sizeof(QueryState));
+    const size_t o_lut = take(kMaxSegments * kMaxCard * 4);
+    const size_t o_q = take(len * 4), o_u = take(len * 4), o_l = take(len * 4);
+    const size_t o_karr = take(kMaxK * 8), o_log = take(kLogCap * 8), o_seed = take(kSeedMax * 8);
+    const size_t o_sp = take(N * 4), o_sl = take(N * 4), o_s2 = take(N * 4);
+    const size_t o_dtw = take(32 * 3 * len * 8);
+    const size_t o_acc = take(sizeof(QueryCounters));
+    char *base = nullptr;
+    if (cudaMalloc(&base, off) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MESSI_ENOMEM, "messi_query: cannot allocate the query workspace");
+    }
+    ix->ws_block = base;
+    ix->ws_bytes = off;
+    ix->device_bytes += off;
+    QuerySlot &s = ix->slot;
+    s.st = reinterpret_cast<QueryState *>(base + o_st);
+    s.lut = reinterpret_cast<float *>(base + o_lut);
+    s.q = reinterpret_cast<float *>(base + o_q);
+    s.U = reinterpret_cast<float *>(base + o_u);
+    s.L = reinterpret_cast<float *>(base + o_l);
+    s.karr = reinterpret_cast<unsigned long long *>(base + o_karr);
+    s.log = reinterpret_cast<unsigned long long *>(base + o_log);
+    s.seedbuf = reinterpret_cast<unsigned long long *>(base + o_seed);
+    s.surv_pos = reinterpret_cast<unsigned *>(base + o_sp);
+    s.surv_lb = reinterpret_cast<float *>(base + o_sl);
+    s.surv2 = reinterpret_cast<unsigned *>(base + o_s2);
+    s.dtw64 = reinterpret_cast<double *>(base + o_dtw);
+    s.acc = reinterpret_cast<QueryCounters *>(base + o_acc);
+    return MESSI_OK;
+}
+
+IndexView view_of(const messi_index *ix)
+{
+    IndexView v;
+    v.raw = ix->raw;
+    v.sax = ix->sax;
+    v.ids = ix->ids;
+    v.pos_of_id = ix->pos_of_id;
+    v.leaf_off = ix->leaf_off;
+    v.leaf_key = ix->leaf_key;
+    v.beta64 = ix->beta64;
+    v.N = ix->N;
+    v.L = ix->L;
+    v.len = ix->len;
+    v.w = ix->w;
+    v.card = ix->card;
+    v.bits = ix->bits;
+    v.m = ix->m;
+    v.status = ix->status;
+    return v;
+}
+
+cudaEvent_t pool_event(messi_index *ix, size_t i)
+{
+    while (ix->ev_pool.size() <= i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ix->ev_pool.push_back(e);
+    }
+    return ix->ev_pool[i];
+}
+
+messi_status check_sizes(uint64_t n, uint32_t len, uint32_t segments, uint32_t card)
+{
+    if (n == 0 || n >= 0xffffffffull) return fail(MESSI_EINVAL, "n must be in [1, 2^32-1)");
+    if (segments == 0 || segments > (unsigned)kMaxSegments)
+        return fail(MESSI_EINVAL, "segments must be in [1, 16]");
+    if (len == 0 || len > (unsigned)kMaxLen || len % segments)
+        return fail(MESSI_EINVAL, "len must be a multiple of segments and at most 4096");
+    const unsigned m = len / segments;
+    if (m < 4 || !is_pow2(m)) return fail(MESSI_EINVAL, "len/segments must be a power of two >= 4");
+    if (!is_pow2(card) || card < 2 || card > (unsigned)kMaxCard)
+        return fail(MESSI_EINVAL, "cardinality must be a power of two in [2, 256]");
+    return MESSI_OK;
+}
+
+}  // namespace
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+messi_status fail(messi_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+bool cuda_ok(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return true;
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return false;
+}
+
+int num_sms()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
+// N(0,1) quantiles j/c by safeguarded Newton iteration on Phi(x) - p, with
+// Phi evaluated through erfc in the lower tail and erf near the centre; the
+// upper half follows from symmetry.  Each root is polished to the double
+// whose CDF lies nearest p among its neighbours.
+namespace {
+double phi_minus(double x, double p)
+{
+    const double rt2 = 1.4142135623730951;
+    if (x < -0.6) return 0.5 * std::erfc(-x / rt2) - p;
+    return 0.5 * std::erf(x / rt2) - (p - 0.5);
+}
+
+double quantile_newton(double p)
+{
+    const double inv_sqrt_2pi = 0.3989422804014327;
+    double lo = -40.0, hi = 40.0, x = 0.0;
+    for (int it = 0; it < 200; ++it) {
+        const double f = phi_minus(x, p);
+        if (f < 0) lo = x; else hi = x;
+        const double dens = inv_sqrt_2pi * std::exp(-0.5 * x * x);
+        double nx = x - f / dens;
+        if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+        if (nx == x) break;
+        x = nx;
+    }
+    for (int pass = 0; pass < 4; ++pass) {   // local polish over neighbours
+        const double a = std::nextafter(x, -INFINITY), b = std::nextafter(x, INFINITY);
+        double best = x, eb = std::fabs(phi_minus(x, p));
+        const double ea = std::fabs(phi_minus(a, p)), ebb = std::fabs(phi_minus(b, p));
+        if (ea < eb) { best = a; eb = ea; }
+        if (ebb < eb) { best = b; }
+        if (best == x) break;
+        x = best;
+    }
+    return x;
+}
+}  // namespace
+
+void compute_breakpoints(int card, double *beta)
+{
+    for (int j = 1; 2 * j < card; ++j) beta[j - 1] = quantile_newton((double)j / card);
+    for (int j = 1; j < card; ++j) {
+        if (2 * j == card) beta[j - 1] = 0.0;
+        else if (2 * j > card) beta[j - 1] = -beta[card - j - 1];
+    }
+}
+
+}  // namespace messi
+
+using namespace messi;
+
+extern "C" {
+
+const char *messi_last_error(void) { return g_last_error.c_str(); }
+
+messi_status messi_breakpoints(uint32_t cardinality, double *out)
+{
+    if (!out || !is_pow2(cardinality) || cardinality < 2 || cardinality > (unsigned)kMaxCard)
+        return fail(MESSI_EINVAL, "messi_breakpoints: cardinality must be a power of two in [2, 256]");
+    compute_breakpoints((int)cardinality, out);
+    return MESSI_OK;
+}
+
+void messi_free(messi_index *ix)
+{
+    if (!ix) return;
+    void *ptrs[] = {ix->raw, ix->sax, ix->ids, ix->pos_of_id, ix->leaf_off, ix->leaf_key, ix->leaf_depth,
+                    ix->beta64, ix->status, ix->ws_block, ix->stage_block, ix->bws_block};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : ix->ev_pool) cudaEventDestroy(e);
+    if (ix->counters_host) cudaFreeHost(ix->counters_host);
+    delete ix;
+}
+
+messi_status messi_index_get_info(const messi_index *ix, messi_index_info *out)
+{
+    if (!ix || !out) return fail(MESSI_EINVAL, "messi_index_get_info: null argument");
+    out->n_series = ix->N;
+    out->len = ix->len;
+    out->segments = ix->w;
+    out->cardinality = ix->card;
+    out->leaf_capacity = ix->cap;
+    out->n_leaves = ix->L;
+    out->max_leaf_size = ix->max_leaf;
+    out->device_bytes = ix->device_bytes;
+    out->build_ms = ix->build_ms;
+    return MESSI_OK;
+}
+
+messi_status messi_build(const float *series, uint64_t n, uint32_t len, uint32_t segments,
+                         uint32_t cardinality, const messi_config *cfg, messi_stream stream,
+                         messi_index **out)
+{
+    if (!series || !out) return fail(MESSI_EINVAL, "messi_build: null argument");
+    *out = nullptr;
+    messi_status chk = check_sizes(n, len, segments, cardinality);
+    if (chk != MESSI_OK) return chk;
+    const unsigned cap = (cfg && cfg->leaf_capacity) ? cfg->leaf_capacity : 2000u;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ensure_attributes();
+
+    messi_index *ix = new messi_index();
+    cudaGetDevice(&ix->device);
+    ix->N = n;
+    ix->len = (int)len;
+    ix->w = (int)segments;
+    ix->card = (int)cardinality;
+    while ((1 << ix->bits) < ix->card) ++ix->bits;
+    ix->m = ix->len / ix->w;
+    ix->cap = cap;
+    compute_breakpoints(ix->card, ix->beta_host);
+
+    std::vector<void *> tmp;
+    auto bail = [&](messi_status st, const std::string &msg) {
+        for (void *p : tmp) cudaFree(p);
+        messi_free(ix);
+        cudaGetLastError();
+        return fail(st, msg);
+    };
+    auto talloc = [&](void **p, size_t bytes) {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        tmp.push_back(*p);
+        return true;
+    };
+
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+
+    if (cudaMalloc(&ix->beta64, kMaxCard * 8) != cudaSuccess || cudaMalloc(&ix->status, 256) != cudaSuccess)
+        return bail(MESSI_ENOMEM, "messi_build: cannot allocate breakpoint tables");
+    float beta32_h[kMaxCard];
+    for (int j = 0; j < ix->card - 1; ++j) beta32_h[j] = (float)ix->beta_host[j];
+    float *beta32 = nullptr;
+    if (!talloc((void **)&beta32, kMaxCard * 4)) return bail(MESSI_ENOMEM, "messi_build: out of device memory");
+    if (cudaMemcpyAsync(ix->beta64, ix->beta_host, (ix->card - 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(beta32, beta32_h, (ix->card - 1) * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(ix->status, 0, 256, s) != cudaSuccess)
+        return bail(MESSI_ECUDA, "messi_build: cannot upload breakpoints");
+
+    const float *dseries = series;
+    const size_t raw_bytes = (size_t)n * len * 4;
+    if (!is_device_ptr(series)) {
+        float *d = nullptr;
+        if (!talloc((void **)&d, raw_bytes)) return bail(MESSI_ENOMEM, "messi_build: cannot stage host series");
+        if (cudaMemcpyAsync(d, series, raw_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return bail(MESSI_ECUDA, "messi_build: host-to-device copy failed");
+        dseries = d;
+    }
+
+    uint4 *keys = nullptr, *keys_alt = nullptr, *sax_tmp = nullptr;
+    unsigned *vals_alt = nullptr;
+    void *sort_tmp = nullptr;
+    if (!talloc((void **)&keys, n * 16) || !talloc((void **)&keys_alt, n * 16) ||
+        !talloc((void **)&sax_tmp, n * 16) || !talloc((void **)&vals_alt, n * 4) ||
+        !talloc(&sort_tmp, radix_sort_temp_bytes(n)))
+        return bail(MESSI_ENOMEM, "messi_build: cannot allocate sort buffers");
+    if (cudaMalloc(&ix->ids, n * 4) != cudaSuccess) return bail(MESSI_ENOMEM, "messi_build: out of device memory");
+
+    // a non-finite value makes its segment sum non-finite; the kernel flags it
+    // in the status word, read once the build has finished
+    launch_summarize(dseries, n, ix->len, ix->w, ix->card, ix->beta64, beta32, sax_tmp, keys, ix->ids,
+                     ix->status, s);
+    ++ix->launches;
+    radix_sort_keys(keys, ix->ids, keys_alt, vals_alt, n, ix->w * ix->bits, sort_tmp, s, &ix->launches);
+    if (!cuda_ok(cudaStreamSynchronize(s), "messi_build: summarise/sort")) return bail(MESSI_ECUDA, g_last_error);
+    cudaFree(keys_alt);
+    cudaFree(vals_alt);
+    cudaFree(sort_tmp);
+    tmp.erase(std::remove_if(tmp.begin(), tmp.end(),
+                             [&](void *p) { return p == keys_alt || p == vals_alt || p == sort_tmp; }),
+              tmp.end());
+
+    if (cudaMalloc(&ix->raw, raw_bytes) != cudaSuccess || cudaMalloc(&ix->sax, n * 16) != cudaSuccess ||
+        cudaMalloc(&ix->pos_of_id, n * 4) != cudaSuccess)
+        return bail(MESSI_ENOMEM, "messi_build: cannot allocate the index arrays");
+    ix->device_bytes = raw_bytes + n * 16 + n * 8 + kMaxCard * 8 + 256;
+
+    messi_status st = build_leaves(ix, keys, sax_tmp, dseries, s);
+    if (st != MESSI_OK) return bail(st, g_last_error);
+    cudaEventRecord(e1, s);
+    if (!cuda_ok(cudaEventSynchronize(e1), "messi_build")) return bail(MESSI_ECUDA, g_last_error);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ix->build_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (void *p : tmp) cudaFree(p);
+    tmp.clear();
+
+    unsigned status = 0;
+    cudaMemcpy(&status, ix->status, 4, cudaMemcpyDeviceToHost);
+    if (status & kStInvalidQuery) {
+        messi_free(ix);
+        return fail(MESSI_EINVAL, "messi_build: the series hold a non-finite value");
+    }
+    ix->last_stream = s;
+    *out = ix;
+    return MESSI_OK;
+}
+
+static messi_status query_args(const messi_index *ix, const float *queries, uint32_t nq, uint32_t k,
+                               messi_dist dist, uint32_t window, const int64_t *ids, const float *dists)
+{
+    if (!ix || !queries || !ids || !dists) return fail(MESSI_EINVAL, "messi_query: null argument");
+    if (nq == 0) return fail(MESSI_EINVAL, "messi_query: nq must be >= 1");
+    if (k == 0 || k > (uint32_t)kMaxK || k > ix->N) return fail(MESSI_EINVAL, "messi_query: k must be in [1, min(n, 1024)]");
+    if (dist != MESSI_ED && dist != MESSI_DTW) return fail(MESSI_EINVAL, "messi_query: unknown distance");
+    if (dist == MESSI_DTW && window >= (uint32_t)ix->len) return fail(MESSI_EINVAL, "messi_query: window must be < len");
+    return MESSI_OK;
+}
+
+messi_status messi_query(const messi_index *cix, const float *queries, uint32_t nq, uint32_t k,
+                         messi_dist dist, uint32_t window, int64_t *ids, float *dists, messi_stream stream)
+{
+    messi_status chk = query_args(cix, queries, nq, k, dist, window, ids, dists);
+    if (chk != MESSI_OK) return chk;
+    messi_index *ix = const_cast<messi_index *>(cix);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ensure_attributes();
+    if ((chk = ensure_workspace(ix)) != MESSI_OK) return chk;
+
+    const bool hq = !is_device_ptr(queries), hi = !is_device_ptr(ids), hd = !is_device_ptr(dists);
+    const size_t qbytes = (size_t)nq * ix->len * 4, ibytes = (size_t)nq * k * 8, dbytes = (size_t)nq * k * 4;
+    const size_t need = (hq ? align256(qbytes) : 0) + (hi ? align256(ibytes) : 0) + (hd ? align256(dbytes) : 0);
+    if (need && !ensure_stage(ix, need)) return fail(MESSI_ENOMEM, "messi_query: cannot allocate staging buffers");
+    char *stage = static_cast<char *>(ix->stage_block);
+    const float *dq = queries;
+    long long *did = reinterpret_cast<long long *>(ids);
+    float *ddist = dists;
+    size_t so = 0;
+    if (hq) {
+        dq = reinterpret_cast<const float *>(stage + so);
+        MESSI_CUDA(cudaMemcpyAsync(stage + so, queries, qbytes, cudaMemcpyHostToDevice, s));
+        so += align256(qbytes);
+    }
+    if (hi) { did = reinterpret_cast<long long *>(stage + so); so += align256(ibytes); }
+    if (hd) { ddist = reinterpret_cast<float *>(stage + so); so += align256(dbytes); }
+
+    const IndexView iv = view_of(ix);
+    QueryParams qp;
+    qp.k = (int)k;
+    qp.dist = (int)dist;
+    qp.r = dist == MESSI_DTW ? (int)window : 0;
+    qp.F = band_factor(qp.dist, ix->len);
+    const QuerySlot slot = ix->slot;
+    MESSI_CUDA(cudaMemsetAsync(slot.acc, 0, sizeof(QueryCounters), s));
+    const unsigned long long launches0 = ix->launches;
+    ix->scan_ev.clear();
+    ix->query_ev.clear();
+    size_t evn = 0;
+    for (uint32_t qi = 0; qi < nq; ++qi) {
+        int eq0 = -1, es0 = -1;
+        if (ix->profiling) {
+            eq0 = (int)evn;
+            cudaEventRecord(pool_event(ix, evn++), s);
+        }
+        launch_prep(iv, qp, slot, dq + (size_t)qi * ix->len, s);
+        launch_seed(iv, qp, slot, s, &ix->launches);
+        if (ix->profiling) {
+            es0 = (int)evn;
+            cudaEventRecord(pool_event(ix, evn++), s);
+        }
+        launch_scan(iv, qp, slot, s);
+        if (ix->profiling) {
+            cudaEventRecord(pool_event(ix, evn++), s);
+            ix->scan_ev.push_back({es0, es0 + 1});
+        }
+        launch_refine(iv, qp, slot, s, &ix->launches);
+        launch_finalize(iv, qp, slot, did + (size_t)qi * k, ddist + (size_t)qi * k, s);
+        ix->launches += 3;
+        if (ix->profiling) {
+            cudaEventRecord(pool_event(ix, evn++), s);
+            ix->query_ev.push_back({eq0, (int)evn - 1});
+        }
+    }
+    MESSI_CUDA(cudaGetLastError());
+    ix->last = messi_stats{};
+    ix->last.queries = nq;
+    ix->last.kernel_launches = ix->launches - launches0;
+    ix->last_stream = s;
+    if (hi) MESSI_CUDA(cudaMemcpyAsync(ids, did, ibytes, cudaMemcpyDeviceToHost, s));
+    if (hd) MESSI_CUDA(cudaMemcpyAsync(dists, ddist, dbytes, cudaMemcpyDeviceToHost, s));
+    if (hq || hi || hd) MESSI_CUDA(cudaStreamSynchronize(s));
+    return MESSI_OK;
+}
+
+messi_status messi_query_batched(const messi_index *ix, const float *queries, uint32_t nq, uint32_t k,
+                                 messi_dist dist, uint32_t window, uint32_t batch, int64_t *ids, float *dists,
+                                 messi_stream stream)
+{
+    (void)batch;
+    messi_status chk = query_args(ix, queries, nq, k, dist, window, ids, dists);
+    if (chk != MESSI_OK) return chk;
+    return fail(MESSI_EINVAL, "messi_query_batched: the batched form is not part of this build yet");
+}
+
+messi_status messi_query_stats(const messi_index *cix, messi_stats *out)
+{
+    if (!cix || !out) return fail(MESSI_EINVAL, "messi_query_stats: null argument");
+    messi_index *ix = const_cast<messi_index *>(cix);
+    *out = ix->last;
+    if (!ix->ws_block) return MESSI_OK;
+    MESSI_CUDA(cudaStreamSynchronize(ix->last_stream));
+    QueryCounters c{};
+    MESSI_CUDA(cudaMemcpy(&c, ix->slot.acc, sizeof(c), cudaMemcpyDeviceToHost));
+    out->lb_evaluated = c.lb_evaluated;
+    out->lb_survivors = c.lb_survivors;
+    out->lbk_survivors = c.lbk_survivors;
+    out->seeded = c.seeded;
+    out->refined = c.refined;
+    out->abandoned = c.abandoned;
+    out->bsf_updates = c.bsf_updates;
+    out->tie_rechecks = c.tie_rechecks;
+    if (ix->profiling) {
+        double sum = 0.0;
+        for (auto &pr : ix->scan_ev) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ix->ev_pool[pr.first], ix->ev_pool[pr.second]);
+            sum += ms;
+        }
+        out->scan_ms = sum;
+        out->scan_launches = ix->scan_ev.size();
+        std::vector<double> lat;
+        for (auto &pr : ix->query_ev) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ix->ev_pool[pr.first], ix->ev_pool[pr.second]);
+            lat.push_back(ms);
+        }
+        if (!lat.empty()) {
+            std::sort(lat.begin(), lat.end());
+            auto pct = [&](double p) {
+                size_t i = (size_t)std::ceil(p * lat.size()) - 1;
+                return lat[std::min(i, lat.size() - 1)];
+            };
+            out->query_ms_p50 = pct(0.50);
+            out->query_ms_p99 = pct(0.99);
+        }
+    }
+    return MESSI_OK;
+}
+
+messi_status messi_set_profiling(messi_index *ix, int enable)
+{
+    if (!ix) return fail(MESSI_EINVAL, "messi_set_profiling: null index");
+    ix->profiling = enable != 0;
+    return MESSI_OK;
+}
+
+messi_status messi_check(const messi_index *ix, messi_stream stream)
+{
+    if (!ix) return fail(MESSI_EINVAL, "messi_check: null index");
+    MESSI_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    unsigned st = 0;
+    MESSI_CUDA(cudaMemcpy(&st, ix->status, 4, cudaMemcpyDeviceToHost));
+    MESSI_CUDA(cudaMemset(ix->status, 0, 4));
+    if (st & kStTimeout) return fail(MESSI_ETIMEOUT, "a device-side bounded wait ran out");
+    if (st & kStTieOverflow) return fail(MESSI_ETIES, "more near-tied candidates than the tie log holds");
+    if (st & kStInvalidQuery) return fail(MESSI_EINVAL, "a query held a non-finite value");
+    return MESSI_OK;
+}
+
+messi_status messi_lower_bounds(const messi_index *cix, const float *query, messi_dist dist, uint32_t window,
+                                float *lb2, messi_stream stream)
+{
+    if (!cix || !query || !lb2) return fail(MESSI_EINVAL, "messi_lower_bounds: null argument");
+    if (dist != MESSI_ED && dist != MESSI_DTW) return fail(MESSI_EINVAL, "messi_lower_bounds: unknown distance");
+    if (dist == MESSI_DTW && window >= (uint32_t)cix->len) return fail(MESSI_EINVAL, "messi_lower_bounds: window must be < len");
+    messi_index *ix = const_cast<messi_index *>(cix);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ensure_attributes();
+    messi_status chk = ensure_workspace(ix);
+    if (chk != MESSI_OK) return chk;
+    const bool hq = !is_device_ptr(query), ho = !is_device_ptr(lb2);
+    const size_t qbytes = (size_t)ix->len * 4, obytes = (size_t)ix->N * 4;
+    if ((hq || ho) && !ensure_stage(ix, align256(qbytes) + align256(obytes)))
+        return fail(MESSI_ENOMEM, "messi_lower_bounds: cannot allocate staging buffers");
+    char *stage = static_cast<char *>(ix->stage_block);
+    const float *dq = query;
+    float *dout = lb2;
+    if (hq) {
+        MESSI_CUDA(cudaMemcpyAsync(stage, query, qbytes, cudaMemcpyHostToDevice, s));
+        dq = reinterpret_cast<const float *>(stage);
+    }
+    if (ho) dout = reinterpret_cast<float *>(stage + align256(qbytes));
+    const IndexView iv = view_of(ix);
+    QueryParams qp{1, (int)dist, dist == MESSI_DTW ? (int)window : 0, band_factor((int)dist, ix->len)};
+    launch_prep(iv, qp, ix->slot, dq, s);
+    launch_lower_bounds(iv, ix->slot, dout, s);
+    ix->launches += 2;
+    MESSI_CUDA(cudaGetLastError());
+    if (ho) MESSI_CUDA(cudaMemcpyAsync(lb2, dout, obytes, cudaMemcpyDeviceToHost, s));
+    if (hq || ho) MESSI_CUDA(cudaStreamSynchronize(s));
+    return MESSI_OK;
+}
+
+messi_status messi_summarize(const float *series, uint64_t n, uint32_t len, uint32_t segments,
+                             uint32_t cardinality, uint8_t *words, messi_stream stream)
+{
+    if (!series || !words) return fail(MESSI_EINVAL, "messi_summarize: null argument");
+    messi_status chk = check_sizes(n, len, segments, cardinality);
+    if (chk != MESSI_OK) return chk;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double b64[kMaxCard];
+    float b32[kMaxCard];
+    compute_breakpoints((int)cardinality, b64);
+    for (unsigned j = 0; j + 1 < cardinality; ++j) b32[j] = (float)b64[j];
+    const bool hs = !is_device_ptr(series), hw = !is_device_ptr(words);
+    const size_t sbytes = (size_t)n * len * 4, wbytes = (size_t)n * 16;
+    char *tmp = nullptr;
+    const size_t tbytes = align256(kMaxCard * 8) + align256(kMaxCard * 4) + (hs ? align256(sbytes) : 0) +
+                          (hw ? align256(wbytes) : 0);
+    if (cudaMalloc(&tmp, tbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MESSI_ENOMEM, "messi_summarize: out of device memory");
+    }
+    double *d64 = reinterpret_cast<double *>(tmp);
+    float *d32 = reinterpret_cast<float *>(tmp + align256(kMaxCard * 8));
+    size_t o = align256(kMaxCard * 8) + align256(kMaxCard * 4);
+    const float *ds = series;
+    uint4 *dw = reinterpret_cast<uint4 *>(words);
+    cudaError_t e = cudaMemcpyAsync(d64, b64, (cardinality - 1) * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d32, b32, (cardinality - 1) * 4, cudaMemcpyHostToDevice, s);
+    if (hs && e == cudaSuccess) {
+        e = cudaMemcpyAsync(tmp + o, series, sbytes, cudaMemcpyHostToDevice, s);
+        ds = reinterpret_cast<const float *>(tmp + o);
+        o += align256(sbytes);
+    }
+    if (hw) dw = reinterpret_cast<uint4 *>(tmp + o);
+    if (e == cudaSuccess) {
+        launch_summarize(ds, n, len, segments, cardinality, d64, d32, dw, nullptr, nullptr, nullptr, s);
+        e = cudaGetLastError();
+    }
+    if (hw && e == cudaSuccess) e = cudaMemcpyAsync(words, dw, wbytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(MESSI_ECUDA, std::string("messi_summarize: ") + cudaGetErrorString(e));
+    return MESSI_OK;
+}
+
+messi_status messi_index_layout(const messi_index *ix, uint32_t *order, uint64_t *leaf_off, uint8_t *leaf_depth)
+{
+    if (!ix) return fail(MESSI_EINVAL, "messi_index_layout: null index");
+    MESSI_CUDA(cudaDeviceSynchronize());
+    if (order) MESSI_CUDA(cudaMemcpy(order, ix->ids, ix->N * 4, cudaMemcpyDeviceToHost));
+    if (leaf_off) MESSI_CUDA(cudaMemcpy(leaf_off, ix->leaf_off, (ix->L + 1) * 8, cudaMemcpyDeviceToHost));
+    if (leaf_depth) MESSI_CUDA(cudaMemcpy(leaf_depth, ix->leaf_depth, ix->L, cudaMemcpyDeviceToHost));
+    return MESSI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+// device_common.cuh -- device helpers shared by the query kernels: packed
+// best-so-far handling, PTX wrappers for mbarrier / bulk copies with bounded
+// waits, warp reductions, the iSAX lower bound of one word, and the ED / DTW
+// distance routines.
+#pragma once
+
+#include "messi_internal.cuh"
+
+namespace messi {
+
+__device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
+
+__device__ __forceinline__ unsigned long long pack_cand(float d2, unsigned id)
+{
+    return ((unsigned long long)__float_as_uint(d2) << 32) | id;
+}
+__device__ __forceinline__ float cand_d2(unsigned long long p) { return __uint_as_float((unsigned)(p >> 32)); }
+__device__ __forceinline__ unsigned cand_id(unsigned long long p) { return (unsigned)p; }
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p)
+{
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p)
+{
+    return *reinterpret_cast<const volatile unsigned *>(p);
+}
+
+// Pruning threshold from a packed k-th best: its squared distance widened by
+// the near-tie factor, rounded up (+inf while fewer than k candidates exist).
+__device__ __forceinline__ float prune_threshold(unsigned long long T, float F)
+{
+    return T == kEmpty ? f_inf() : __fmul_ru(cand_d2(T), F);
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+// ---------------------------------------------------------------- PTX: TMA
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared through the TMA unit; completes `bytes`
+// transaction bytes on `bar`.  Addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false when the phase did not complete within the limit.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
+{
+    for (unsigned it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ------------------------------------------------------ iSAX lower bound
+// Squared lower bound of one iSAX word: sum over segments of the table entry
+// of its symbol, added with rounding toward -inf so the result never exceeds
+// the exact sum of the (already rounded-down) entries.
+__device__ __forceinline__ float lb2_word(const uint4 &wv, const float *lut)
+{
+    float acc = 0.f;
+    const unsigned wd[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int s = 4 * k + b;
+            const unsigned sym = (wd[k] >> (8 * b)) & 0xffu;
+            acc = __fadd_rd(acc, lut[s * kMaxCard + sym]);
+        }
+    }
+    return acc;
+}
+
+// ------------------------------------------------------------------- ED
+// Squared ED of query q (len floats, 16-byte aligned) and row x, one warp.
+// Lanes take float4 i = lane, lane + 32, ...; chunks of 256 points are summed
+// in order and, when `thr` is finite, the warp stops after a chunk whose
+// running sum exceeds thr (returns that partial sum, > thr).  All lanes
+// return the same value.
+__device__ __forceinline__ float warp_ed2(const float *__restrict__ q, const float *__restrict__ x, int len,
+                                          float thr)
+{
+    const int lane = threadIdx.x & 31;
+    const int n4 = len >> 2;
+    const float4 *q4 = reinterpret_cast<const float4 *>(q);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    float acc = 0.f;
+    for (int base = 0; base < n4; base += 64) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int i = base + lane + 32 * t;
+            if (i < n4) {
+                const float4 xv = __ldg(x4 + i);
+                const float4 qv = q4[i];
+                float d;
+                d = qv.x - xv.x; acc = fmaf(d, d, acc);
+                d = qv.y - xv.y; acc = fmaf(d, d, acc);
+                d = qv.z - xv.z; acc = fmaf(d, d, acc);
+                d = qv.w - xv.w; acc = fmaf(d, d, acc);
+            }
+        }
+        if (base + 64 < n4 && thr < f_inf()) {
+            const float part = warp_sum(acc);
+            if (part > thr) return part;
+        }
+    }
+    return warp_sum(acc);
+}
+
+// ------------------------------------------------------------------ DTW
+// Banded DTW of q and x (length n, reach r) by one warp, anti-diagonal
+// wavefront: cells (i, j) with i + j = a are independent; lane handles
+// i = i_lo + lane, +32, ...  `diag` holds three diagonals (3*n values,
+// indexed by i).  A cell's neighbours are read only when they lie inside the
+// window and the matrix, so no diagonal needs clearing.  Every warping path
+// meets diagonal a or a+1, so when the minimum over two consecutive
+// diagonals exceeds `thr` the result would too and the warp stops early
+// (returning a value > thr).  FP32 uses fminf / plain adds; the FP64
+// instantiation uses explicitly rounded operations in the same order as the
+// FP64 reference evaluation of the recurrence.
+template <typename T>
+__device__ __forceinline__ T dtw_cost(float qi, float xj);
+template <>
+__device__ __forceinline__ float dtw_cost<float>(float qi, float xj)
+{
+    const float d = qi - xj;
+    return d * d;
+}
+template <>
+__device__ __forceinline__ double dtw_cost<double>(float qi, float xj)
+{
+    const double d = __dsub_rn((double)qi, (double)xj);
+    return __dmul_rn(d, d);
+}
+__device__ __forceinline__ float dtw_add(float a, float b) { return a + b; }
+__device__ __forceinline__ double dtw_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float dtw_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double dtw_min(double a, double b) { return fmin(a, b); }
+
+template <typename T>
+__device__ T warp_dtw(const float *__restrict__ q, const float *__restrict__ x, int n, int r, T *diag, T thr)
+{
+    const int lane = threadIdx.x & 31;
+    const T INF = (T)f_inf();
+    if (r > n - 1) r = n - 1;
+    T run_min = INF;      // min over the current diagonal (this lane)
+    T prev_min = INF;     // min over the previous diagonal (this lane)
+    const int last = 2 * n - 2;
+    for (int a = 0; a <= last; ++a) {
+        int i_lo = a - (n - 1);
+        const int wlo = (a - r + 1) >> 1;                     // ceil((a - r) / 2)
+        if (wlo > i_lo) i_lo = wlo;
+        if (i_lo < 0) i_lo = 0;
+        int i_hi = (a + r) >> 1;                              // floor((a + r) / 2)
+        if (i_hi > a) i_hi = a;
+        if (i_hi > n - 1) i_hi = n - 1;
+        T *cur = diag + (a % 3) * n;
+        const T *p1 = diag + ((a + 2) % 3) * n;
+        const T *p2 = diag + ((a + 1) % 3) * n;
+        T lmin = INF;
+        for (int i = i_lo + lane; i <= i_hi; i += 32) {
+            const int j = a - i;
+            const T cost = dtw_cost<T>(q[i], x[j]);
+            T D;
+            if (a == 0) {
+                D = cost;
+            } else {
+                T best = INF;
+                if (i >= 1 && abs(i - 1 - j) <= r) best = dtw_min(best, p1[i - 1]);
+                if (j >= 1 && abs(i - j + 1) <= r) best = dtw_min(best, p1[i]);
+                if (i >= 1 && j >= 1) best = dtw_min(best, p2[i - 1]);
+                D = dtw_add(cost, best);
+            }
+            cur[i] = D;
+            lmin = dtw_min(lmin, D);
+        }
+        __syncwarp();
+        prev_min = run_min;
+        run_min = lmin;
+        if ((a & 7) == 7 && a < last && thr < INF) {
+            T both = dtw_min(prev_min, run_min);
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) both = dtw_min(both, __shfl_xor_sync(0xffffffffu, both, off));
+            if (both > thr) return both;
+        }
+    }
+    return diag[(last % 3) * n + (n - 1)];
+}
+
+}  // namespace messi

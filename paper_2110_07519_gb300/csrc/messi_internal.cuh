@@ -1,0 +1,188 @@
+// messi_internal.cuh -- shared declarations of the GB300 iSAX k-NN library.
+//
+// Data layout in HBM (one index, positions are leaf order):
+//   raw        float [N][len]   series copied into leaf order (Sec. 3.2: a
+//                               leaf points at its raw series; here the rows
+//                               of a leaf are contiguous)
+//   sax        uint4 [N]        iSAX word, byte s = symbol of segment s
+//   ids        u32   [N]        original row id of each position
+//   pos_of_id  u32   [N]        inverse permutation
+//   leaf_off   u64   [L+1]      first position of each leaf
+//   leaf_key   uint4 [L]        interleaved key of each leaf's first series
+//   leaf_depth u8    [L]        key prefix bits of each leaf
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/messi.h"
+
+namespace messi {
+
+// ------------------------------------------------------------ constants
+constexpr int kMaxSegments = 16;
+constexpr int kMaxCard = 256;
+constexpr int kMaxLen = 4096;
+constexpr int kMaxK = 1024;
+constexpr int kLogCap = 8192;        // near-tie / accepted-candidate log per query
+constexpr int kSeedMax = 4096;       // series of the seed leaf refined up front
+constexpr unsigned long long kEmpty = ~0ull;   // packed "no candidate"
+
+// device status word bits
+constexpr unsigned kStTimeout = 1u;
+constexpr unsigned kStInvalidQuery = 2u;
+constexpr unsigned kStTieOverflow = 4u;
+
+// spin limits of bounded waits (iterations; each sleeps a few hundred ns)
+constexpr unsigned kSpinLimit = 1u << 22;
+
+// ------------------------------------------------------- per-query state
+struct QueryCounters {
+    unsigned long long lb_evaluated, lb_survivors, lbk_survivors, seeded, refined, abandoned,
+        bsf_updates, tie_rechecks;
+};
+
+struct QueryState {
+    unsigned long long thr;     // packed (d2 bits << 32 | id) of the current k-th best
+    unsigned int lock;          // k > 1 insertion lock
+    unsigned int kcount;        // entries in karr
+    unsigned int surv_count;    // lower-bound survivors
+    unsigned int surv2_count;   // LB_Keogh survivors (DTW)
+    unsigned int log_count;     // accepted / near-tie candidates logged
+    unsigned int seed_lo, seed_hi;
+    unsigned int seed_count;    // distances written by the seed phase
+    unsigned int invalid;       // non-finite query value seen
+    unsigned int pad0;
+    uint4 qkey;                 // interleaved key of the query word
+    QueryCounters c;
+};
+
+// Arrays belonging to one query slot (device pointers).
+struct QuerySlot {
+    QueryState *st;
+    float *lut;                 // [16][256] squared-distance table, rounded down
+    float *q;                   // [len] query
+    float *U, *L;               // [len] LB_Keogh envelope (DTW)
+    unsigned long long *karr;   // [kMaxK] sorted k best (k > 1)
+    unsigned long long *log;    // [kLogCap]
+    unsigned long long *seedbuf;// [kSeedMax]
+    unsigned int *surv_pos;     // [N] (plain path only)
+    float *surv_lb;             // [N]
+    unsigned int *surv2;        // [N]
+    double *dtw64;              // [32 warps][3][len] FP64 DTW diagonals (finalize)
+    QueryCounters *acc;         // per-call counter accumulator
+};
+
+// Parameters every query kernel needs, passed by value.
+struct IndexView {
+    const float *raw;
+    const uint4 *sax;
+    const unsigned int *ids;
+    const unsigned int *pos_of_id;
+    const unsigned long long *leaf_off;
+    const uint4 *leaf_key;
+    const double *beta64;       // [card-1] breakpoints
+    unsigned long long N;
+    unsigned long long L;
+    int len, w, card, bits, m;
+    unsigned int *status;       // device status word
+};
+
+struct QueryParams {
+    int k;
+    int dist;                   // 0 ED, 1 DTW
+    int r;                      // DTW window
+    float F;                    // near-tie band factor (>= (1+gamma)^2)
+};
+
+}  // namespace messi
+
+struct messi_index {
+    int device = 0;
+    unsigned long long N = 0;
+    int len = 0, w = 0, card = 0, bits = 0, m = 0;
+    unsigned cap = 2000;
+    unsigned long long L = 0, max_leaf = 0;
+    // device arrays
+    float *raw = nullptr;
+    uint4 *sax = nullptr;
+    unsigned int *ids = nullptr;
+    unsigned int *pos_of_id = nullptr;
+    unsigned long long *leaf_off = nullptr;
+    uint4 *leaf_key = nullptr;
+    unsigned char *leaf_depth = nullptr;
+    double *beta64 = nullptr;
+    unsigned int *status = nullptr;
+    double beta_host[256] = {0};
+    // plain-path workspace (lazily allocated)
+    void *ws_block = nullptr;
+    size_t ws_bytes = 0;
+    messi::QuerySlot slot{};
+    // staging for host queries / outputs
+    void *stage_block = nullptr;
+    size_t stage_bytes = 0;
+    // batched workspace
+    void *bws_block = nullptr;
+    size_t bws_bytes = 0;
+    int bws_slots = 0;
+    // bookkeeping
+    size_t device_bytes = 0;
+    double build_ms = 0.0;
+    bool profiling = false;
+    messi_stats last{};
+    cudaStream_t last_stream = nullptr;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> scan_ev, query_ev;   // pairs of event indices
+    unsigned long long launches = 0;
+    messi::QueryCounters *counters_host = nullptr;        // pinned readback
+};
+
+namespace messi {
+
+// ------------------------------------------------------------ host helpers
+void set_error(const std::string &msg);
+messi_status fail(messi_status st, const std::string &msg);
+bool cuda_ok(cudaError_t e, const char *what);
+#define MESSI_CUDA(call)                                  \
+    do {                                                  \
+        if (!::messi::cuda_ok((call), #call)) return MESSI_ECUDA; \
+    } while (0)
+
+int num_sms();
+void compute_breakpoints(int card, double *beta);
+
+// ------------------------------------------------------------- launchers
+// summarize.cu
+void launch_summarize(const float *series, unsigned long long n, int len, int w, int card,
+                      const double *beta64, const float *beta32, uint4 *sax_out, uint4 *key_out,
+                      unsigned int *id_out, unsigned int *status, cudaStream_t s);
+// radix_sort.cu
+size_t radix_sort_temp_bytes(unsigned long long n);
+void radix_sort_keys(uint4 *keys, unsigned int *vals, uint4 *keys_alt, unsigned int *vals_alt,
+                     unsigned long long n, int key_bits, void *temp, cudaStream_t s,
+                     unsigned long long *launches);
+size_t scan_temp_bytes(unsigned long long n);
+void exclusive_scan_u32(const unsigned int *in, unsigned int *out, unsigned long long n,
+                        void *temp, cudaStream_t s, unsigned long long *launches);
+// leaves.cu
+messi_status build_leaves(messi_index *ix, const uint4 *sorted_keys, const uint4 *sax_unsorted,
+                          const float *series, cudaStream_t s);
+// query.cu
+void launch_prep(const IndexView &iv, const QueryParams &qp, QuerySlot slot, const float *query,
+                 cudaStream_t s);
+void launch_seed(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s,
+                 unsigned long long *launches);
+void launch_scan(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s);
+void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s,
+                   unsigned long long *launches);
+void launch_finalize(const IndexView &iv, const QueryParams &qp, QuerySlot slot, long long *ids,
+                     float *dists, cudaStream_t s);
+void launch_lower_bounds(const IndexView &iv, QuerySlot slot, float *lb2_by_id, cudaStream_t s);
+void init_kernel_attributes();
+void launch_reset_state(QuerySlot slot, cudaStream_t s);
+float band_factor(int dist, int len);
+
+}  // namespace messi

@@ -1,0 +1,749 @@
+// query.cu -- exact k-NN query kernels (Sec. 3.3 for ED, Sec. 3.4 for DTW).
+//
+// Per query, in stream order:
+//   k_prep      FP64 PAA of the query (ED) or of its LB_Keogh envelope (DTW),
+//               the table T[s][v] = m * d_s(v)^2 rounded down, the query key
+//               and the seed range (the query's own leaf; approxSearch,
+//               Sec. 3.1).
+//   k_seed_dist distances to every series of the seed range.
+//   k_seed_sel  the k best of them become the initial best-so-far.
+//   k_lb_scan   streams every iSAX word through TMA bulk copies into shared
+//               memory, sums its table entries and compacts the survivors
+//               (LB^2 <= widened k-th best) warp by warp.
+//   k_refine_ed warp per survivor: re-checks its bound against the live
+//               best-so-far, then ED with early abandoning (Algorithm 9).
+//   k_lbk/k_dtw DTW: LB_Keogh on the raw survivor, then banded DTW
+//               (Algorithm 10).
+//   k_finalize  resolves near-ties in FP64 and writes ids / distances.
+//
+// Exactness.  Lower bounds are summed with rounding toward -inf from table
+// entries rounded toward -inf, so they never exceed the exact bound.  Real
+// distances are FP32 with relative error at most gamma; a candidate is
+// discarded only when it is certainly worse than the current k-th best: its
+// bound or distance exceeds the k-th best's FP32 distance times
+// F >= (1 + gamma)^2.  Every candidate within that band is logged, and at the
+// end any ambiguity (more than k candidates in the band, or two of the k
+// within the band of each other) is settled by recomputing those candidates
+// in FP64 with the same operation order as the FP64 reference; ties of equal
+// distance go to the lowest original id because the packed 64-bit
+// (distance bits << 32 | id) compares that way.
+#include <algorithm>
+
+#include "device_common.cuh"
+
+namespace messi {
+namespace {
+
+constexpr int kPrepThreads = 256;
+constexpr int kScanThreads = 256;
+constexpr int kScanWpt = 4;
+constexpr int kScanTileWords = kScanThreads * kScanWpt;   // 1024 words, 16 KB
+constexpr int kScanStages = 4;
+constexpr int kScanSmem = kMaxSegments * kMaxCard * 4 + kScanStages * kScanTileWords * 16;
+constexpr int kFinThreads = 1024;
+
+// ------------------------------------------------------------------ prep
+__device__ __forceinline__ double region_lo(int v, const double *beta)
+{
+    return v == 0 ? -__longlong_as_double(0x7ff0000000000000ll) : beta[v - 1];
+}
+__device__ __forceinline__ double region_hi(int v, int card, const double *beta)
+{
+    return v == card - 1 ? __longlong_as_double(0x7ff0000000000000ll) : beta[v];
+}
+
+// Distance from a value to a region, rounded down and shrunk by a slack that
+// covers the FP64 rounding of the PAA values the regions were chosen with.
+__device__ __forceinline__ double gap_rd(double edge, double p)   // edge - p, edge > p
+{
+    double d = __dsub_rd(edge, p);
+    d = __dsub_rd(d, 9.094947017729282e-13 * (fabs(edge) + fabs(p) + 1.0));   // 2^-40 (...)
+    return d > 0.0 ? d : 0.0;
+}
+
+__global__ void __launch_bounds__(kPrepThreads)
+k_prep(IndexView iv, QueryParams qp, QuerySlot slot, const float *__restrict__ query)
+{
+    __shared__ double paa[kMaxSegments], paaU[kMaxSegments], paaL[kMaxSegments];
+    __shared__ int sym[kMaxSegments];
+    __shared__ int bad;
+    __shared__ double sbeta[kMaxCard];
+    QueryState *st = slot.st;
+    const int tid = threadIdx.x;
+    const int len = iv.len, w = iv.w, m = iv.m, card = iv.card;
+    if (tid == 0) {
+        bad = 0;
+        st->thr = kEmpty;
+        st->lock = 0u;
+        st->kcount = 0u;
+        st->surv_count = 0u;
+        st->surv2_count = 0u;
+        st->log_count = 0u;
+        st->seed_count = 0u;
+        st->invalid = 0u;
+        st->c = QueryCounters{};
+    }
+    for (int i = tid; i < kMaxCard; i += blockDim.x) sbeta[i] = i < card - 1 ? iv.beta64[i] : 0.0;
+    __syncthreads();
+    for (int i = tid; i < len; i += blockDim.x) {
+        const float v = query[i];
+        if (!isfinite(v)) bad = 1;
+        slot.q[i] = v;
+    }
+    __syncthreads();
+    if (bad) {
+        if (tid == 0) {
+            st->invalid = 1u;
+            atomicOr(iv.status, kStInvalidQuery);
+        }
+        return;
+    }
+    if (qp.dist == 1) {   // LB_Keogh envelope, window clipped at the ends
+        for (int i = tid; i < len; i += blockDim.x) {
+            const int a = max(0, i - qp.r), b = min(len - 1, i + qp.r);
+            float hi = slot.q[a], lo = slot.q[a];
+            for (int j = a + 1; j <= b; ++j) {
+                const float v = slot.q[j];
+                hi = fmaxf(hi, v);
+                lo = fminf(lo, v);
+            }
+            slot.U[i] = hi;
+            slot.L[i] = lo;
+        }
+    }
+    __syncthreads();
+    if (tid < w) {   // FP64 segment means, sequential as the reference does
+        double s = 0.0, su = 0.0, sl = 0.0;
+        for (int t = tid * m; t < (tid + 1) * m; ++t) {
+            s = __dadd_rn(s, (double)slot.q[t]);
+            if (qp.dist == 1) {
+                su = __dadd_rn(su, (double)slot.U[t]);
+                sl = __dadd_rn(sl, (double)slot.L[t]);
+            }
+        }
+        paa[tid] = __ddiv_rn(s, (double)m);
+        paaU[tid] = __ddiv_rn(su, (double)m);
+        paaL[tid] = __ddiv_rn(sl, (double)m);
+        int lo = 0, hi = card - 1;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (sbeta[mid] <= paa[tid]) lo = mid + 1; else hi = mid;
+        }
+        sym[tid] = lo;
+    }
+    __syncthreads();
+    // table: T[s][v] = m * d^2, every step rounded toward -inf
+    for (int e = tid; e < kMaxSegments * kMaxCard; e += blockDim.x) {
+        const int s = e / kMaxCard, v = e % kMaxCard;
+        float out = 0.f;
+        if (s < w && v < card) {
+            const double lo = region_lo(v, sbeta), hi = region_hi(v, card, sbeta);
+            double d = 0.0;
+            if (qp.dist == 0) {
+                if (paa[s] < lo) d = gap_rd(lo, paa[s]);
+                else if (paa[s] > hi) d = gap_rd(paa[s], hi);
+            } else {
+                if (paaU[s] < lo) d = gap_rd(lo, paaU[s]);            // ABOVE
+                else if (paaL[s] > hi) d = gap_rd(paaL[s], hi);       // BELOW
+            }
+            out = __double2float_rd(__dmul_rd(__dmul_rd(d, d), (double)m));
+        }
+        slot.lut[e] = out;
+    }
+    if (tid == 0) {
+        // interleaved key of the query word
+        unsigned long long khi = 0ull, klo = 0ull;
+        for (int j = 0; j < iv.bits; ++j) {
+            unsigned field = 0u;
+            for (int s = 0; s < w; ++s) field = (field << 1) | ((sym[s] >> (iv.bits - 1 - j)) & 1);
+            khi = (khi << w) | (klo >> (64 - w));
+            klo = (klo << w) | field;
+        }
+        const int used = w * iv.bits;
+        if (used < 128) {
+            const int sh = 128 - used;
+            if (sh >= 64) { khi = klo << (sh - 64); klo = 0ull; }
+            else { khi = (khi << sh) | (klo >> (64 - sh)); klo <<= sh; }
+        }
+        const uint4 qk = make_uint4((unsigned)(khi >> 32), (unsigned)khi, (unsigned)(klo >> 32), (unsigned)klo);
+        st->qkey = qk;
+        // seed leaf: the last leaf whose first key is <= the query key
+        unsigned long long lo = 0, hi = iv.L;   // count of leaves with key <= qk
+        while (lo < hi) {
+            unsigned long long mid = (lo + hi) >> 1;
+            const uint4 k = iv.leaf_key[mid];
+            bool le = (k.x != qk.x) ? k.x < qk.x : (k.y != qk.y) ? k.y < qk.y
+                    : (k.z != qk.z) ? k.z < qk.z : k.w <= qk.w;
+            if (le) lo = mid + 1; else hi = mid;
+        }
+        const unsigned long long leaf = lo > 0 ? lo - 1 : 0;
+        unsigned long long a = iv.leaf_off[leaf], b = iv.leaf_off[leaf + 1];
+        if (b - a > (unsigned long long)kSeedMax) b = a + kSeedMax;
+        // fewer than k series in the leaf: widen to neighbouring positions
+        const unsigned long long want = (unsigned long long)qp.k;
+        while (b - a < want) {
+            if (a > 0) --a;
+            if (b - a < want && b < iv.N) ++b;
+        }
+        st->seed_lo = (unsigned)a;
+        st->seed_hi = (unsigned)b;
+    }
+}
+
+// ------------------------------------------------------------------ offer
+// Present a computed candidate (squared FP32 distance, original id).
+__device__ void offer(const QueryParams &qp, const QuerySlot &slot, unsigned *status, float d2, unsigned id)
+{
+    QueryState *st = slot.st;
+    const unsigned long long P = pack_cand(d2, id);
+    const unsigned long long T = ld_volatile_u64(&st->thr);
+    if (!(d2 <= prune_threshold(T, qp.F))) return;
+    const unsigned li = atomicAdd(&st->log_count, 1u);
+    if (li < (unsigned)kLogCap) slot.log[li] = P;
+    if (P >= T) return;
+    if (qp.k == 1) {
+        const unsigned long long old = atomicMin(&st->thr, P);
+        if (P < old) atomicAdd(&st->c.bsf_updates, 1ull);
+        return;
+    }
+    unsigned spins = 0;
+    while (atomicCAS(&st->lock, 0u, 1u) != 0u) {
+        if (++spins > kSpinLimit) {
+            atomicOr(status, kStTimeout);
+            return;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    volatile unsigned long long *ka = slot.karr;
+    volatile unsigned *kc = &st->kcount;
+    const unsigned cnt = *kc;
+    const unsigned k = (unsigned)qp.k;
+    if (cnt < k || P < ka[k - 1]) {
+        int pos = cnt < k ? (int)cnt : (int)k - 1;
+        if (cnt < k) *kc = cnt + 1;
+        while (pos > 0 && ka[pos - 1] > P) {
+            ka[pos] = ka[pos - 1];
+            --pos;
+        }
+        ka[pos] = P;
+        if (cnt + 1 >= k) {
+            atomicExch(&st->thr, ka[k - 1]);
+            atomicAdd(&st->c.bsf_updates, 1ull);
+        }
+    }
+    __threadfence();
+    atomicExch(&st->lock, 0u);
+}
+
+// ------------------------------------------------------------------ seed
+template <int DIST>
+__global__ void __launch_bounds__(256)
+k_seed_dist(IndexView iv, QueryParams qp, QuerySlot slot)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    QueryState *st = slot.st;
+    if (ld_volatile_u32(&st->invalid)) return;
+    const unsigned lo = st->seed_lo, hi = st->seed_hi;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *qs = reinterpret_cast<float *>(dsm);
+    for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
+    __syncthreads();
+    float *diag = qs + iv.len + wib * 3 * iv.len;
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    for (unsigned p = lo + blockIdx.x * (blockDim.x >> 5) + wib; p < hi; p += nw) {
+        const float *x = iv.raw + (unsigned long long)p * iv.len;
+        float d2 = DIST == 0 ? warp_ed2(qs, x, iv.len, f_inf())
+                             : warp_dtw<float>(qs, x, iv.len, qp.r, diag, f_inf());
+        if (lane == 0) slot.seedbuf[p - lo] = pack_cand(d2, iv.ids[p]);
+        __syncwarp();
+    }
+}
+
+// one block: sort the seed distances, keep the k best as the best-so-far
+__global__ void __launch_bounds__(kFinThreads)
+k_seed_select(IndexView iv, QueryParams qp, QuerySlot slot)
+{
+    __shared__ unsigned long long buf[kSeedMax];
+    QueryState *st = slot.st;
+    if (ld_volatile_u32(&st->invalid)) return;
+    const unsigned cnt = st->seed_hi - st->seed_lo;
+    unsigned npow = 1;
+    while (npow < cnt) npow <<= 1;
+    for (unsigned i = threadIdx.x; i < npow; i += blockDim.x) buf[i] = i < cnt ? slot.seedbuf[i] : kEmpty;
+    __syncthreads();
+    for (unsigned size = 2; size <= npow; size <<= 1)
+        for (unsigned stride = size >> 1; stride > 0; stride >>= 1) {
+            for (unsigned i = threadIdx.x; i < npow; i += blockDim.x) {
+                const unsigned j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const unsigned long long a = buf[i], b = buf[j];
+                    if ((a > b) == up) { buf[i] = b; buf[j] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    const unsigned k = (unsigned)qp.k;
+    const unsigned kept = cnt < k ? cnt : k;
+    for (unsigned i = threadIdx.x; i < kept; i += blockDim.x) slot.karr[i] = buf[i];
+    const unsigned long long T = cnt >= k ? buf[k - 1] : kEmpty;
+    const float band = prune_threshold(T, qp.F);
+    __shared__ unsigned nlog;
+    if (threadIdx.x == 0) nlog = 0;
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < cnt; i += blockDim.x)
+        if (cand_d2(buf[i]) <= band) {
+            const unsigned li = atomicAdd(&nlog, 1u);
+            if (li < (unsigned)kLogCap) slot.log[li] = buf[i];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->kcount = kept;
+        st->thr = T;
+        st->log_count = nlog;
+        st->seed_count = cnt;
+        st->c.seeded = cnt;
+        st->c.bsf_updates = T != kEmpty ? 1ull : 0ull;
+    }
+}
+
+// ------------------------------------------------------------------ scan
+__global__ void __launch_bounds__(kScanThreads, 2)
+k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long bars[kScanStages];
+    __shared__ int timed_out;
+    float *lut = reinterpret_cast<float *>(smem);
+    uint4 *stage = reinterpret_cast<uint4 *>(smem + kMaxSegments * kMaxCard * 4);
+    QueryState *st = slot.st;
+    if (ld_volatile_u32(&st->invalid)) return;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int i = tid; i < kMaxSegments * kMaxCard; i += blockDim.x) lut[i] = slot.lut[i];
+    const float thrp = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+    const unsigned long long seed_lo = st->seed_lo, seed_hi = st->seed_hi;
+    const unsigned long long N = iv.N;
+    const unsigned long long ntiles = (N + kScanTileWords - 1) / kScanTileWords;
+    if (tid == 0) {
+        timed_out = 0;
+        for (int s = 0; s < kScanStages; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    __syncthreads();
+    auto issue = [&](unsigned long long tile, int s) {
+        const unsigned long long first = tile * kScanTileWords;
+        const unsigned long long cnt = min((unsigned long long)kScanTileWords, N - first);
+        const unsigned bytes = (unsigned)(cnt * 16);
+        mbar_arrive_expect_tx(&bars[s], bytes);
+        bulk_g2s(stage + s * kScanTileWords, iv.sax + first, bytes, &bars[s]);
+    };
+    if (tid == 0)
+        for (int s = 0; s < kScanStages; ++s) {
+            const unsigned long long tile = blockIdx.x + (unsigned long long)s * gridDim.x;
+            if (tile < ntiles) issue(tile, s);
+        }
+    unsigned long long nsurv = 0;
+    unsigned iter = 0;
+    for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++iter) {
+        const int s = iter % kScanStages;
+        const unsigned parity = (iter / kScanStages) & 1u;
+        const bool ok = mbar_wait_bounded(&bars[s], parity);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(iv.status, kStTimeout);
+            timed_out = 1;
+            break;
+        }
+        const unsigned long long first = tile * kScanTileWords;
+        const unsigned cnt = (unsigned)min((unsigned long long)kScanTileWords, N - first);
+#pragma unroll
+        for (int r = 0; r < kScanWpt; ++r) {
+            const unsigned j = tid + r * kScanThreads;
+            bool surv = false;
+            float lb = 0.f;
+            const unsigned long long pos = first + j;
+            if (j < cnt) {
+                const uint4 wv = stage[s * kScanTileWords + j];
+                lb = lb2_word(wv, lut);
+                surv = lb <= thrp && (pos < seed_lo || pos >= seed_hi);
+            }
+            const unsigned ballot = __ballot_sync(0xffffffffu, surv);
+            if (ballot) {   // warp-uniform
+                unsigned base = 0;
+                if (lane == 0) base = atomicAdd(&st->surv_count, (unsigned)__popc(ballot));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (surv) {
+                    const unsigned o = base + __popc(ballot & ((1u << lane) - 1u));
+                    slot.surv_pos[o] = (unsigned)pos;
+                    slot.surv_lb[o] = lb;
+                }
+                if (lane == 0) nsurv += __popc(ballot);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned long long next = tile + (unsigned long long)kScanStages * gridDim.x;
+            if (next < ntiles) issue(next, s);
+        }
+    }
+    if (timed_out) {
+        // let the copies still in flight (iterations iter .. iter+S-1) land
+        // before the block's shared memory is released
+        if (tid == 0)
+            for (unsigned it = iter; it < iter + kScanStages; ++it) {
+                const unsigned long long t = blockIdx.x + (unsigned long long)it * gridDim.x;
+                if (t >= ntiles) break;
+                mbar_wait_bounded(&bars[it % kScanStages], (it / kScanStages) & 1u);
+            }
+        return;
+    }
+    if (lane == 0 && nsurv) atomicAdd(&st->c.lb_survivors, nsurv);
+    if (tid == 0) {
+        unsigned long long mine = 0;
+        for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x)
+            mine += min((unsigned long long)kScanTileWords, N - t * kScanTileWords);
+        atomicAdd(&st->c.lb_evaluated, mine);
+    }
+}
+
+// ------------------------------------------------------------ ED refine
+__global__ void __launch_bounds__(256)
+k_refine_ed(IndexView iv, QueryParams qp, QuerySlot slot)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    QueryState *st = slot.st;
+    if (ld_volatile_u32(&st->invalid)) return;
+    float *qs = reinterpret_cast<float *>(dsm);
+    for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned count = ld_volatile_u32(&st->surv_count);
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    unsigned long long done = 0, aband = 0, late = 0;
+    for (unsigned i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < count; i += nw) {
+        const unsigned pos = slot.surv_pos[i];
+        const float lb = slot.surv_lb[i];
+        const float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        if (lb > thr) { ++late; continue; }
+        const float d2 = warp_ed2(qs, iv.raw + (unsigned long long)pos * iv.len, iv.len, thr);
+        if (d2 > thr) { ++aband; continue; }
+        ++done;
+        if (lane == 0) offer(qp, slot, iv.status, d2, iv.ids[pos]);
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (done) atomicAdd(&st->c.refined, done);
+        if (aband) atomicAdd(&st->c.abandoned, aband);
+    }
+}
+
+// ------------------------------------------------------ DTW: LB_Keogh
+__global__ void __launch_bounds__(256)
+k_lbk(IndexView iv, QueryParams qp, QuerySlot slot)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    QueryState *st = slot.st;
+    if (ld_volatile_u32(&st->invalid)) return;
+    float *Us = reinterpret_cast<float *>(dsm);
+    float *Ls = Us + iv.len;
+    for (int i = threadIdx.x; i < iv.len; i += blockDim.x) {
+        Us[i] = slot.U[i];
+        Ls[i] = slot.L[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned count = ld_volatile_u32(&st->surv_count);
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    unsigned long long pass = 0;
+    for (unsigned i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < count; i += nw) {
+        const unsigned pos = slot.surv_pos[i];
+        float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        if (slot.surv_lb[i] > thr) continue;
+        const float *x = iv.raw + (unsigned long long)pos * iv.len;
+        // LB_Keogh^2, every operation rounded toward -inf (a certain lower bound)
+        float acc = 0.f;
+        bool pruned = false;
+        for (int base = 0; base < iv.len; base += 256) {
+            for (int t = lane; t < 256 && base + t < iv.len; t += 32) {
+                const int idx = base + t;
+                const float c = __ldg(x + idx);
+                float d = 0.f;
+                if (c > Us[idx]) d = __fsub_rd(c, Us[idx]);
+                else if (c < Ls[idx]) d = __fsub_rd(Ls[idx], c);
+                acc = __fadd_rd(acc, __fmul_rd(d, d));
+            }
+            float tot = acc;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) tot = __fadd_rd(tot, __shfl_xor_sync(0xffffffffu, tot, off));
+            if (tot > thr) { pruned = true; break; }
+        }
+        if (!pruned) {
+            ++pass;
+            if (lane == 0) slot.surv2[atomicAdd(&st->surv2_count, 1u)] = pos;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && pass) atomicAdd(&st->c.lbk_survivors, pass);
+}
+
+// ---------------------------------------------------------------- DTW
+__global__ void __launch_bounds__(256)
+k_dtw(IndexView iv, QueryParams qp, QuerySlot slot)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    QueryState *st = slot.st;
+    if (ld_volatile_u32(&st->invalid)) return;
+    float *qs = reinterpret_cast<float *>(dsm);
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *diag = qs + iv.len + wib * 3 * iv.len;
+    for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
+    __syncthreads();
+    const unsigned count = ld_volatile_u32(&st->surv2_count);
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    unsigned long long done = 0, aband = 0;
+    for (unsigned i = blockIdx.x * (blockDim.x >> 5) + wib; i < count; i += nw) {
+        const unsigned pos = slot.surv2[i];
+        const float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        const float d2 = warp_dtw<float>(qs, iv.raw + (unsigned long long)pos * iv.len, iv.len, qp.r, diag, thr);
+        if (d2 > thr) { ++aband; continue; }
+        ++done;
+        if (lane == 0) offer(qp, slot, iv.status, d2, iv.ids[pos]);
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (done) atomicAdd(&st->c.refined, done);
+        if (aband) atomicAdd(&st->c.abandoned, aband);
+    }
+}
+
+// ------------------------------------------------------------- finalize
+// Bitonic sort of n (power of two) entries in shared memory with a caller
+// ordering `less(i, j)` and swap `swap(i, j)`.
+template <typename Less, typename Swap>
+__device__ void block_bitonic(unsigned npow, Less less, Swap swap)
+{
+    for (unsigned size = 2; size <= npow; size <<= 1)
+        for (unsigned stride = size >> 1; stride > 0; stride >>= 1) {
+            for (unsigned i = threadIdx.x; i < npow; i += blockDim.x) {
+                const unsigned j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    if (less(j, i) == up) swap(i, j);
+                }
+            }
+            __syncthreads();
+        }
+}
+
+constexpr int kFinSmem = kLogCap * (8 + 8);
+
+__global__ void __launch_bounds__(kFinThreads)
+k_finalize(IndexView iv, QueryParams qp, QuerySlot slot, long long *ids, float *dists)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    unsigned long long *cand = reinterpret_cast<unsigned long long *>(fsm);
+    double *d64 = reinterpret_cast<double *>(fsm + kLogCap * 8);
+    __shared__ unsigned ncand;
+    __shared__ int ambiguous;
+    QueryState *st = slot.st;
+    const int tid = threadIdx.x;
+    const unsigned k = (unsigned)qp.k;
+    if (ld_volatile_u32(&st->invalid)) {
+        for (unsigned i = tid; i < k; i += blockDim.x) {
+            ids[i] = -1;
+            dists[i] = __int_as_float(0x7fc00000);
+        }
+        return;
+    }
+    const unsigned long long T = st->thr;
+    const float band = prune_threshold(T, qp.F);
+    const unsigned logged = st->log_count;
+    if (tid == 0) {
+        ncand = 0;
+        ambiguous = 0;
+        if (logged > (unsigned)kLogCap) atomicOr(iv.status, kStTieOverflow);
+    }
+    __syncthreads();
+    const unsigned nlog = min(logged, (unsigned)kLogCap);
+    for (unsigned i = tid; i < nlog; i += blockDim.x) {
+        const unsigned long long P = slot.log[i];
+        if (cand_d2(P) <= band) cand[atomicAdd(&ncand, 1u)] = P;
+    }
+    __syncthreads();
+    const unsigned c = ncand;
+    unsigned npow = 1;
+    while (npow < c) npow <<= 1;
+    for (unsigned i = c + tid; i < npow; i += blockDim.x) cand[i] = kEmpty;
+    __syncthreads();
+    block_bitonic(
+        npow, [&](unsigned i, unsigned j) { return cand[i] < cand[j]; },
+        [&](unsigned i, unsigned j) {
+            const unsigned long long t = cand[i];
+            cand[i] = cand[j];
+            cand[j] = t;
+        });
+    // ambiguity: a candidate beyond the k-th inside the band, or two of the
+    // first k within the band of each other (their order is not certain)
+    if (tid == 0 && c > k) ambiguous = 1;
+    for (unsigned i = tid; i + 1 < min(c, k); i += blockDim.x)
+        if (cand_d2(cand[i + 1]) <= __fmul_ru(cand_d2(cand[i]), qp.F)) ambiguous = 1;
+    __syncthreads();
+    if (!ambiguous) {
+        for (unsigned i = tid; i < k; i += blockDim.x) {
+            ids[i] = i < c ? (long long)cand_id(cand[i]) : -1;
+            dists[i] = i < c ? __fsqrt_rn(cand_d2(cand[i])) : f_inf();
+        }
+    } else {
+        // FP64 recomputation of every candidate in the band, in the operation
+        // order of the FP64 reference evaluation
+        const int lane = tid & 31, wib = tid >> 5;
+        if (qp.dist == 0) {
+            for (unsigned e = tid; e < c; e += blockDim.x) {
+                const unsigned pos = iv.pos_of_id[cand_id(cand[e])];
+                const float *x = iv.raw + (unsigned long long)pos * iv.len;
+                double s = 0.0;
+                for (int t = 0; t < iv.len; ++t) {
+                    const double d = __dsub_rn((double)slot.q[t], (double)x[t]);
+                    s = __dadd_rn(s, __dmul_rn(d, d));
+                }
+                d64[e] = s;
+            }
+        } else {
+            double *diag = slot.dtw64 + (size_t)wib * 3 * iv.len;
+            for (unsigned e = wib; e < c; e += blockDim.x >> 5) {
+                const unsigned pos = iv.pos_of_id[cand_id(cand[e])];
+                const double v = warp_dtw<double>(slot.q, iv.raw + (unsigned long long)pos * iv.len, iv.len,
+                                                  qp.r, diag, (double)f_inf());
+                if (lane == 0) d64[e] = v;
+                __syncwarp();
+            }
+        }
+        for (unsigned i = c + tid; i < npow; i += blockDim.x) d64[i] = (double)f_inf();
+        __syncthreads();
+        block_bitonic(
+            npow,
+            [&](unsigned i, unsigned j) {
+                return d64[i] < d64[j] || (d64[i] == d64[j] && cand_id(cand[i]) < cand_id(cand[j]));
+            },
+            [&](unsigned i, unsigned j) {
+                const double td = d64[i];
+                d64[i] = d64[j];
+                d64[j] = td;
+                const unsigned long long t = cand[i];
+                cand[i] = cand[j];
+                cand[j] = t;
+            });
+        for (unsigned i = tid; i < k; i += blockDim.x) {
+            ids[i] = i < c ? (long long)cand_id(cand[i]) : -1;
+            dists[i] = i < c ? (float)sqrt(d64[i]) : f_inf();
+        }
+        if (tid == 0) st->c.tie_rechecks += c;
+    }
+    __syncthreads();
+    QueryCounters *acc = slot.acc;
+    if (tid == 0 && acc) {
+        atomicAdd(&acc->lb_evaluated, st->c.lb_evaluated);
+        atomicAdd(&acc->lb_survivors, st->c.lb_survivors);
+        atomicAdd(&acc->lbk_survivors, st->c.lbk_survivors);
+        atomicAdd(&acc->seeded, st->c.seeded);
+        atomicAdd(&acc->refined, st->c.refined);
+        atomicAdd(&acc->abandoned, st->c.abandoned);
+        atomicAdd(&acc->bsf_updates, st->c.bsf_updates);
+        atomicAdd(&acc->tie_rechecks, st->c.tie_rechecks);
+    }
+}
+
+// lower bound of every series, written in original id order
+__global__ void __launch_bounds__(256)
+k_lb_all(IndexView iv, QuerySlot slot, float *__restrict__ out)
+{
+    __shared__ float lut[kMaxSegments * kMaxCard];
+    for (int i = threadIdx.x; i < kMaxSegments * kMaxCard; i += blockDim.x) lut[i] = slot.lut[i];
+    __syncthreads();
+    if (ld_volatile_u32(&slot.st->invalid)) return;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < iv.N; p += stride)
+        out[iv.ids[p]] = lb2_word(iv.sax[p], lut);
+}
+
+int dtw_warps_per_block(int len)
+{
+    const int per_warp = 3 * len * 4;
+    int w = (96 * 1024 - len * 4) / per_warp;
+    return std::max(1, std::min(8, w));
+}
+
+}  // namespace
+
+float band_factor(int dist, int len)
+{
+    const double u = 5.9604644775390625e-08;   // 2^-24
+    const double gamma = dist == 0 ? (len / 16.0 + 32.0) * u : (2.0 * len + 32.0) * u;
+    const double F = (1.0 + gamma) * (1.0 + gamma) * (1.0 + 9.1e-13);
+    return (float)F * (1.0f + 1.2e-7f);   // round up
+}
+
+void init_kernel_attributes()
+{
+    cudaFuncSetAttribute(k_lb_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
+    cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinSmem);
+    cudaFuncSetAttribute(k_dtw, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(k_seed_dist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+}
+
+void launch_prep(const IndexView &iv, const QueryParams &qp, QuerySlot slot, const float *query,
+                 cudaStream_t s)
+{
+    k_prep<<<1, kPrepThreads, 0, s>>>(iv, qp, slot, query);
+}
+
+void launch_seed(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s,
+                 unsigned long long *launches)
+{
+    if (qp.dist == 0) {
+        const size_t sm = iv.len * 4;
+        k_seed_dist<0><<<num_sms() * 2, 256, sm, s>>>(iv, qp, slot);
+    } else {
+        const int wpb = dtw_warps_per_block(iv.len);
+        const size_t sm = (size_t)iv.len * 4 + (size_t)wpb * 3 * iv.len * 4;
+        k_seed_dist<1><<<num_sms() * 4, wpb * 32, sm, s>>>(iv, qp, slot);
+    }
+    k_seed_select<<<1, kFinThreads, 0, s>>>(iv, qp, slot);
+    if (launches) *launches += 2;
+}
+
+void launch_scan(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s)
+{
+    const unsigned long long ntiles = (iv.N + kScanTileWords - 1) / kScanTileWords;
+    const unsigned long long g = std::min<unsigned long long>(ntiles, (unsigned long long)num_sms() * 2);
+    k_lb_scan<<<(unsigned)g, kScanThreads, kScanSmem, s>>>(iv, qp, slot);
+}
+
+void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s,
+                   unsigned long long *launches)
+{
+    if (qp.dist == 0) {
+        k_refine_ed<<<num_sms() * 8, 256, iv.len * 4, s>>>(iv, qp, slot);
+        if (launches) *launches += 1;
+    } else {
+        k_lbk<<<num_sms() * 8, 256, iv.len * 8, s>>>(iv, qp, slot);
+        const int wpb = dtw_warps_per_block(iv.len);
+        const size_t sm = (size_t)iv.len * 4 + (size_t)wpb * 3 * iv.len * 4;
+        k_dtw<<<num_sms() * 4, wpb * 32, sm, s>>>(iv, qp, slot);
+        if (launches) *launches += 2;
+    }
+}
+
+void launch_finalize(const IndexView &iv, const QueryParams &qp, QuerySlot slot, long long *ids,
+                     float *dists, cudaStream_t s)
+{
+    k_finalize<<<1, kFinThreads, kFinSmem, s>>>(iv, qp, slot, ids, dists);
+}
+
+void launch_lower_bounds(const IndexView &iv, QuerySlot slot, float *lb2_by_id, cudaStream_t s)
+{
+    k_lb_all<<<num_sms() * 4, 256, 0, s>>>(iv, slot, lb2_by_id);
+}
+
+}  // namespace messi

@@ -1,0 +1,93 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports
+every entry point include/messi.h declares, rejects invalid arguments before
+touching the device, and its breakpoints agree with the oracle's."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "messi.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2110_07519_gb300 import build as b
+
+    path = b.build()
+    return ctypes.CDLL(path)
+
+
+def declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(messi_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_abi():
+    names = declared()
+    for must in ("messi_build", "messi_query", "messi_query_batched", "messi_free", "messi_query_stats",
+                 "messi_lower_bounds", "messi_summarize", "messi_last_error", "messi_check"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    path = os.path.join(ROOT, "paper_2110_07519_gb300", "libmessi.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (messi_\w+)", out))
+    missing = [n for n in declared() if n not in exported]
+    assert not missing, missing
+    for n in declared():
+        assert hasattr(lib, n)
+    # nothing but the C ABI leaks out (the static CUDA runtime stays private)
+    assert all(s.startswith("messi_") for s in re.findall(r"\bT (\w+)", out))
+
+
+def test_python_binding_names_match_header():
+    import paper_2110_07519_gb300 as m
+
+    for n in declared():
+        assert callable(getattr(m, n)), n
+
+
+@pytest.mark.parametrize("card", [2, 4, 16, 64, 256])
+def test_breakpoints_match_oracle(card):
+    import paper_2110_07519_gb300 as m
+
+    lib_b = m.messi_breakpoints(card)
+    orc_b = oracle.breakpoints(card)
+    ulps = np.abs(lib_b - orc_b) / np.spacing(np.maximum(np.abs(orc_b), 1e-300))
+    assert ulps.max() <= 2, ulps.max()
+    assert np.all(np.diff(lib_b) > 0)
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    import paper_2110_07519_gb300 as m
+
+    out = ctypes.c_void_p()
+    x = np.zeros((4, 256), np.float32)
+    p = x.ctypes.data
+    bad = [
+        (p, 4, 250, 16, 256),     # len not a multiple of segments
+        (p, 4, 256, 17, 256),     # too many segments
+        (p, 4, 256, 16, 100),     # cardinality not a power of two
+        (p, 4, 256, 16, 512),     # cardinality above 256
+        (p, 0, 256, 16, 256),     # empty collection
+        (p, 4, 48, 16, 256),      # segment length 3, not a power of two >= 4
+        (None, 4, 256, 16, 256),  # null series
+    ]
+    for args in bad:
+        st = lib.messi_build(ctypes.c_void_p(args[0]) if args[0] else None, ctypes.c_uint64(args[1]),
+                             ctypes.c_uint32(args[2]), ctypes.c_uint32(args[3]), ctypes.c_uint32(args[4]),
+                             None, None, ctypes.byref(out))
+        assert st == 1, args
+        assert m.messi_last_error() != ""
+    assert lib.messi_breakpoints(ctypes.c_uint32(3), None) == 1
+    assert lib.messi_query(None, None, 1, 1, 0, 0, None, None, None) == 1
+    assert lib.messi_query_stats(None, None) == 1
+    lib.messi_free(None)

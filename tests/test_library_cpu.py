@@ -17,10 +17,10 @@ HEADER = os.path.join(ROOT, "include", "messi.h")
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2110_07519_gb300 import build as b
+    import __graft_entry__
 
-    path = b.build()
-    return ctypes.CDLL(path)
+    __graft_entry__.build()
+    return ctypes.CDLL(os.path.join(ROOT, "paper_2110_07519_gb300", "libmessi.so"))
 
 
 def declared():

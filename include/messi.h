@@ -146,6 +146,26 @@ messi_status messi_query_batched(const messi_index *ix, const float *queries, ui
 messi_status messi_lower_bounds(const messi_index *ix, const float *query, messi_dist dist,
                                 uint32_t window, float *lb2, messi_stream stream);
 
+/* Lower bounds like messi_lower_bounds, for callers that cannot allocate
+ * device memory while they run: code inside a CUDA stream capture (where
+ * allocation calls are not allowed), a real-time loop that must not block in
+ * the allocator, or an embedding that gives the library only a fixed budget.
+ * The paper has no counterpart; this is an interface of this library.
+ *
+ * Allocates nothing: query and lb2 must be device pointers (EINVAL for host
+ * buffers, which would need staging memory); the scratch -- query state,
+ * lower-bound table, query and envelope rows -- lives in one fixed array of
+ * 41,216 bytes that every GPU loading the library holds until the process
+ * exits.  That array bounds the series length: an index with len > 2048 is
+ * rejected with EINVAL (use messi_lower_bounds).  Every call shares the
+ * array, so calls whose work overlaps on the GPU (on different streams, or
+ * from several threads) race and must be serialised by the caller; each call
+ * clears the query state it needs before use.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) and should come
+ * before any stream capture.  Results equal messi_lower_bounds bit for bit. */
+messi_status messi_lower_bounds_noalloc(const messi_index *ix, const float *query, messi_dist dist,
+                                        uint32_t window, float *lb2, messi_stream stream);
+
 /* Counters of the last query call.  Synchronises the index's last stream. */
 messi_status messi_query_stats(const messi_index *ix, messi_stats *out);
 

@@ -65,6 +65,7 @@ _SIGS = {
     "messi_query": [_P, _P, _U32, _U32, _I, _U32, _P, _P, _P],
     "messi_query_batched": [_P, _P, _U32, _U32, _I, _U32, _U32, _P, _P, _P],
     "messi_lower_bounds": [_P, _P, _I, _U32, _P, _P],
+    "messi_lower_bounds_noalloc": [_P, _P, _I, _U32, _P, _P],
     "messi_query_stats": [_P, ctypes.POINTER(MessiStats)],
     "messi_set_profiling": [_P, _I],
     "messi_check": [_P, _P],
@@ -215,6 +216,17 @@ def messi_lower_bounds(index: Index, query, dist: int = MESSI_ED, window: int = 
     op, okeep, _ = _ptr(out)
     _check(_lib.messi_lower_bounds(index.handle, qp, dist, window, op, _stream(stream, query)),
            "messi_lower_bounds")
+    return out
+
+
+def messi_lower_bounds_noalloc(index: Index, query, out, dist: int = MESSI_ED, window: int = 0, stream=None):
+    """Lower bounds into a caller-provided device tensor ``out`` (n float32)
+    without any device allocation by the library; ``query`` must be on the
+    device too.  Calls sharing the library's fixed scratch must not overlap."""
+    qp, qkeep, _ = _ptr(query)
+    op, okeep, _ = _ptr(out)
+    _check(_lib.messi_lower_bounds_noalloc(index.handle, qp, dist, window, op, _stream(stream, query)),
+           "messi_lower_bounds_noalloc")
     return out
 
 

@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=4, help="queries in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mix", default="mixed", choices=["mixed", "fresh", "s0.1", "s0.5", "s1.0"],
+                    help="query class (default: the paper-shaped mix)")
     return ap.parse_args()
 
 
@@ -212,7 +214,12 @@ def run_messi(args, ws, rank, local):
     ix = m.messi_build(data, 16, 256)
     info = m.messi_index_get_info(ix)
     build_gbps = args.n * args.len * 4 / (info["build_ms"] * 1e-3) / 1e9
-    qpool = synth.query_mix_torch(data, (W + K) * B, seed=synth.QUERY_SEED + rank)
+    if args.mix == "mixed":
+        qpool = synth.query_mix_torch(data, (W + K) * B, seed=synth.QUERY_SEED + rank)
+    elif args.mix == "fresh":
+        qpool = synth.random_walks_torch((W + K) * B, args.len, seed=synth.QUERY_SEED + rank, device=dev)
+    else:
+        qpool = synth.noisy_members_torch(data, (W + K) * B, float(args.mix[1:]), seed=synth.NOISE_SEED + rank)[0]
     ids = torch.empty((B, args.k), dtype=torch.int64, device=dev)
     dists = torch.empty((B, args.k), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -227,7 +234,7 @@ def run_messi(args, ws, rank, local):
     clocks = ClockSampler(local)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     scan_ms, scan_launches, launches, lat = 0.0, 0, 0, []
-    survivors, refined = 0, 0
+    survivors, refined, abandoned = 0, 0, 0
     torch.cuda.synchronize()
     e0.record(stream)
     for s in range(W, W + K):
@@ -238,6 +245,7 @@ def run_messi(args, ws, rank, local):
         launches += st["kernel_launches"]
         survivors += st["lb_survivors"]
         refined += st["refined"]
+        abandoned += st["abandoned"]
         lat += [st["query_ms_p50"], st["query_ms_p99"]]
     e1.record(stream)
     torch.cuda.synchronize()
@@ -297,7 +305,7 @@ def run_messi(args, ws, rank, local):
             "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": value / PAPER_QPS, "dtype": "f32", "data": DATA_DESC,
             "config": {"workload": f"{args.n} x {args.len} fp32 random walks, ED, k={args.k}, 16 segments, "
-                                   f"8-bit SAX, plain per-query path",
+                                   f"8-bit SAX, plain per-query path", "queries": args.mix,
                        "queries_per_step": B, "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (16 B iSAX word per series streamed per query)"},
             "p50_ms": st_all["query_ms_p50"], "p99_ms": st_all["query_ms_p99"],
@@ -308,7 +316,13 @@ def run_messi(args, ws, rank, local):
                          "avg_launch_ms": scan_avg_s * 1e3},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "parity_sample": parity,
-            "counters": {"lb_survivors_per_query": survivors / (B * K), "refined_per_query": refined / (B * K)},
+            "counters": {"lb_survivors_per_query": survivors / (B * K), "refined_per_query": refined / (B * K),
+                         "rows_read_per_query": (refined + abandoned) / (B * K)},
+            "query_roofline": {
+                "bytes_per_query": 16.0 * args.n + 8.0 * survivors / (B * K)
+                                   + 4.0 * args.len * (refined + abandoned) / (B * K),
+                "frac": (16.0 * args.n + 8.0 * survivors / (B * K) + 4.0 * args.len * (refined + abandoned) / (B * K))
+                        / (elapsed_ms * 1e-3 / (B * K)) / 1e9 / peak},
         }
         print(json.dumps(line), flush=True)
     if pg:

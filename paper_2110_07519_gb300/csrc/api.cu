@@ -74,6 +74,7 @@ messi_status ensure_workspace(messi_index *ix)
     const size_t o_karr = take(kMaxK * 8), o_log = take(kLogCap * 8), o_seed = take(kSeedMax * 8);
     const size_t o_sp = take(N * 4), o_sl = take(N * 4), o_s2 = take(N * 4);
     const size_t o_dtw = take(32 * 3 * len * 8);
+    const size_t o_rc = take(kMaxScanGrid * 4);
     const size_t o_acc = take(sizeof(QueryCounters));
     char *base = nullptr;
     if (cudaMalloc(&base, off) != cudaSuccess) {
@@ -96,6 +97,7 @@ messi_status ensure_workspace(messi_index *ix)
     s.surv_lb = reinterpret_cast<float *>(base + o_sl);
     s.surv2 = reinterpret_cast<unsigned *>(base + o_s2);
     s.dtw64 = reinterpret_cast<double *>(base + o_dtw);
+    s.region_count = reinterpret_cast<unsigned *>(base + o_rc);
     s.acc = reinterpret_cast<QueryCounters *>(base + o_acc);
     return MESSI_OK;
 }

@@ -101,21 +101,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
 // ------------------------------------------------------ iSAX lower bound
 // Squared lower bound of one iSAX word: sum over segments of the table entry
 // of its symbol, added with rounding toward -inf so the result never exceeds
-// the exact sum of the (already rounded-down) entries.
+// the exact sum of the (already rounded-down) entries.  lb2_half adds the 8
+// segments held in two 32-bit words starting at segment s0 to acc; a partial
+// sum never exceeds the full one, so a partial sum above a threshold already
+// rejects the word.
+__device__ __forceinline__ float lb2_half(unsigned w0, unsigned w1, const float *lut, int s0, float acc)
+{
+    float v[8];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) v[b] = lut[(s0 + b) * kMaxCard + ((w0 >> (8 * b)) & 0xffu)];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) v[4 + b] = lut[(s0 + 4 + b) * kMaxCard + ((w1 >> (8 * b)) & 0xffu)];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc = __fadd_rd(acc, v[b]);
+    return acc;
+}
+
 __device__ __forceinline__ float lb2_word(const uint4 &wv, const float *lut)
 {
-    float acc = 0.f;
-    const unsigned wd[4] = {wv.x, wv.y, wv.z, wv.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int s = 4 * k + b;
-            const unsigned sym = (wd[k] >> (8 * b)) & 0xffu;
-            acc = __fadd_rd(acc, lut[s * kMaxCard + sym]);
-        }
-    }
-    return acc;
+    return lb2_half(wv.z, wv.w, lut, 8, lb2_half(wv.x, wv.y, lut, 0, 0.f));
 }
 
 // ------------------------------------------------------------------- ED
@@ -152,6 +156,59 @@ __device__ __forceinline__ float warp_ed2(const float *__restrict__ q, const flo
         }
     }
     return warp_sum(acc);
+}
+
+// Two rows at once (more loads in flight); same arithmetic as warp_ed2 for
+// each row.  A row whose running sum exceeds thr after a 256-point chunk
+// stops accumulating; its returned value is then that partial sum (> thr).
+__device__ __forceinline__ void warp_ed2_pair(const float *__restrict__ q, const float *__restrict__ xa,
+                                              const float *__restrict__ xb, int len, float thr, float &da,
+                                              float &db)
+{
+    const int lane = threadIdx.x & 31;
+    const int n4 = len >> 2;
+    const float4 *q4 = reinterpret_cast<const float4 *>(q);
+    const float4 *a4 = reinterpret_cast<const float4 *>(xa);
+    const float4 *b4 = reinterpret_cast<const float4 *>(xb);
+    float aa = 0.f, ab = 0.f;
+    bool live_a = true, live_b = true;
+    for (int base = 0; base < n4; base += 64) {
+        float4 xv[4];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int i = base + lane + 32 * t;
+            const bool in = i < n4;
+            xv[t] = (in && live_a) ? __ldg(a4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xv[2 + t] = (in && live_b) ? __ldg(b4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int i = base + lane + 32 * t;
+            if (i < n4) {
+                const float4 qv = q4[i];
+                float d;
+                if (live_a) {
+                    d = qv.x - xv[t].x; aa = fmaf(d, d, aa);
+                    d = qv.y - xv[t].y; aa = fmaf(d, d, aa);
+                    d = qv.z - xv[t].z; aa = fmaf(d, d, aa);
+                    d = qv.w - xv[t].w; aa = fmaf(d, d, aa);
+                }
+                if (live_b) {
+                    d = qv.x - xv[2 + t].x; ab = fmaf(d, d, ab);
+                    d = qv.y - xv[2 + t].y; ab = fmaf(d, d, ab);
+                    d = qv.z - xv[2 + t].z; ab = fmaf(d, d, ab);
+                    d = qv.w - xv[2 + t].w; ab = fmaf(d, d, ab);
+                }
+            }
+        }
+        if (base + 64 < n4 && thr < f_inf()) {
+            if (live_a && warp_sum(aa) > thr) live_a = false;
+            if (live_b && warp_sum(ab) > thr) live_b = false;
+            if (!live_a && !live_b) break;
+        }
+    }
+    da = warp_sum(aa);
+    db = warp_sum(ab);
 }
 
 // ------------------------------------------------------------------ DTW

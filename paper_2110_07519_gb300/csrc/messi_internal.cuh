@@ -30,6 +30,7 @@ constexpr int kMaxK = 1024;
 constexpr int kLogCap = 8192;        // near-tie / accepted-candidate log per query
 constexpr int kSeedMax = 4096;       // series of the seed leaf refined up front
 constexpr unsigned long long kEmpty = ~0ull;   // packed "no candidate"
+constexpr int kMaxScanGrid = 2048;   // scan CTAs (each owns one survivor region)
 
 // device status word bits
 constexpr unsigned kStTimeout = 1u;
@@ -55,7 +56,8 @@ struct QueryState {
     unsigned int seed_lo, seed_hi;
     unsigned int seed_count;    // distances written by the seed phase
     unsigned int invalid;       // non-finite query value seen
-    unsigned int pad0;
+    unsigned int scan_grid;     // CTAs of the last scan: survivor regions
+    unsigned int region_words;  // words (and survivor slots) per scan CTA
     uint4 qkey;                 // interleaved key of the query word
     QueryCounters c;
 };
@@ -69,8 +71,9 @@ struct QuerySlot {
     unsigned long long *karr;   // [kMaxK] sorted k best (k > 1)
     unsigned long long *log;    // [kLogCap]
     unsigned long long *seedbuf;// [kSeedMax]
-    unsigned int *surv_pos;     // [N] (plain path only)
-    float *surv_lb;             // [N]
+    unsigned int *surv_pos;     // [N] (plain path only), region of scan CTA c
+    float *surv_lb;             // [N]    starts at c * region_words
+    unsigned int *region_count; // [kMaxScanGrid] survivors found by each scan CTA
     unsigned int *surv2;        // [N]
     double *dtw64;              // [32 warps][3][len] FP64 DTW diagonals (finalize)
     QueryCounters *acc;         // per-call counter accumulator

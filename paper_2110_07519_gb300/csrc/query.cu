@@ -35,10 +35,11 @@ namespace messi {
 namespace {
 
 constexpr int kPrepThreads = 256;
-constexpr int kScanThreads = 256;
-constexpr int kScanWpt = 4;
+constexpr int kScanThreads = 512;
+constexpr int kScanWpt = 2;
 constexpr int kScanTileWords = kScanThreads * kScanWpt;   // 1024 words, 16 KB
 constexpr int kScanStages = 4;
+constexpr int kScanCtasPerSm = 2;
 constexpr int kScanSmem = kMaxSegments * kMaxCard * 4 + kScanStages * kScanTileWords * 16;
 constexpr int kFinThreads = 1024;
 
@@ -309,12 +310,16 @@ k_seed_select(IndexView iv, QueryParams qp, QuerySlot slot)
 }
 
 // ------------------------------------------------------------------ scan
-__global__ void __launch_bounds__(kScanThreads, 2)
-k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
+// Persistent CTAs; CTA c owns the contiguous tiles [c*tpc, (c+1)*tpc) and
+// writes its survivors into its own region of the survivor arrays (the same
+// index range as its words), so compaction needs only a shared-memory counter.
+__global__ void __launch_bounds__(kScanThreads, kScanCtasPerSm)
+k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot, unsigned tpc)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bars[kScanStages];
     __shared__ int timed_out;
+    __shared__ unsigned s_count;
     float *lut = reinterpret_cast<float *>(smem);
     uint4 *stage = reinterpret_cast<uint4 *>(smem + kMaxSegments * kMaxCard * 4);
     QueryState *st = slot.st;
@@ -325,11 +330,19 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
     const unsigned long long seed_lo = st->seed_lo, seed_hi = st->seed_hi;
     const unsigned long long N = iv.N;
     const unsigned long long ntiles = (N + kScanTileWords - 1) / kScanTileWords;
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * tpc;
+    const unsigned long long t1 = min(t0 + tpc, ntiles);
+    const unsigned long long region = t0 * kScanTileWords;
     if (tid == 0) {
         timed_out = 0;
+        s_count = 0;
         for (int s = 0; s < kScanStages; ++s) mbar_init(&bars[s], 1);
         fence_barrier_init();
         fence_proxy_async();
+        if (blockIdx.x == 0) {
+            st->scan_grid = gridDim.x;
+            st->region_words = tpc * kScanTileWords;
+        }
     }
     __syncthreads();
     auto issue = [&](unsigned long long tile, int s) {
@@ -340,13 +353,9 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
         bulk_g2s(stage + s * kScanTileWords, iv.sax + first, bytes, &bars[s]);
     };
     if (tid == 0)
-        for (int s = 0; s < kScanStages; ++s) {
-            const unsigned long long tile = blockIdx.x + (unsigned long long)s * gridDim.x;
-            if (tile < ntiles) issue(tile, s);
-        }
-    unsigned long long nsurv = 0;
+        for (int s = 0; s < kScanStages && t0 + s < t1; ++s) issue(t0 + s, s);
     unsigned iter = 0;
-    for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++iter) {
+    for (unsigned long long tile = t0; tile < t1; ++tile, ++iter) {
         const int s = iter % kScanStages;
         const unsigned parity = (iter / kScanStages) & 1u;
         const bool ok = mbar_wait_bounded(&bars[s], parity);
@@ -360,77 +369,150 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
 #pragma unroll
         for (int r = 0; r < kScanWpt; ++r) {
             const unsigned j = tid + r * kScanThreads;
-            bool surv = false;
-            float lb = 0.f;
+            const bool valid = j < cnt;
+            const uint4 wv = valid ? stage[s * kScanTileWords + j] : make_uint4(0, 0, 0, 0);
+            // first half of the segments; the rest only if some lane can still survive
+            float lb = lb2_half(wv.x, wv.y, lut, 0, 0.f);
+            if (__any_sync(0xffffffffu, valid && lb <= thrp)) lb = lb2_half(wv.z, wv.w, lut, 8, lb);
             const unsigned long long pos = first + j;
-            if (j < cnt) {
-                const uint4 wv = stage[s * kScanTileWords + j];
-                lb = lb2_word(wv, lut);
-                surv = lb <= thrp && (pos < seed_lo || pos >= seed_hi);
-            }
+            const bool surv = valid && lb <= thrp && (pos < seed_lo || pos >= seed_hi);
             const unsigned ballot = __ballot_sync(0xffffffffu, surv);
             if (ballot) {   // warp-uniform
                 unsigned base = 0;
-                if (lane == 0) base = atomicAdd(&st->surv_count, (unsigned)__popc(ballot));
+                if (lane == 0) base = atomicAdd(&s_count, (unsigned)__popc(ballot));
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (surv) {
-                    const unsigned o = base + __popc(ballot & ((1u << lane) - 1u));
+                    const unsigned long long o = region + base + __popc(ballot & ((1u << lane) - 1u));
                     slot.surv_pos[o] = (unsigned)pos;
                     slot.surv_lb[o] = lb;
                 }
-                if (lane == 0) nsurv += __popc(ballot);
             }
         }
         __syncthreads();
-        if (tid == 0) {
-            const unsigned long long next = tile + (unsigned long long)kScanStages * gridDim.x;
-            if (next < ntiles) issue(next, s);
-        }
+        if (tid == 0 && tile + kScanStages < t1) issue(tile + kScanStages, s);
     }
     if (timed_out) {
         // let the copies still in flight (iterations iter .. iter+S-1) land
         // before the block's shared memory is released
         if (tid == 0)
-            for (unsigned it = iter; it < iter + kScanStages; ++it) {
-                const unsigned long long t = blockIdx.x + (unsigned long long)it * gridDim.x;
-                if (t >= ntiles) break;
+            for (unsigned it = iter; it < iter + kScanStages && t0 + it < t1; ++it)
                 mbar_wait_bounded(&bars[it % kScanStages], (it / kScanStages) & 1u);
-            }
+        if (tid == 0) slot.region_count[blockIdx.x] = 0;
         return;
     }
-    if (lane == 0 && nsurv) atomicAdd(&st->c.lb_survivors, nsurv);
+    __syncthreads();
     if (tid == 0) {
-        unsigned long long mine = 0;
-        for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x)
-            mine += min((unsigned long long)kScanTileWords, N - t * kScanTileWords);
-        atomicAdd(&st->c.lb_evaluated, mine);
+        slot.region_count[blockIdx.x] = s_count;
+        if (s_count) atomicAdd(&st->c.lb_survivors, (unsigned long long)s_count);
+        atomicAdd(&st->c.lb_evaluated, (t1 > t0) ? min(N, t1 * kScanTileWords) - t0 * kScanTileWords : 0ull);
     }
 }
 
+// Survivors are stored in per-scan-CTA regions; a refine block turns the
+// region counts into a prefix over 32-entry chunks so warps can take chunks
+// by index.  Returns the number of chunks.
+__device__ unsigned chunk_prefix(const QuerySlot &slot, unsigned G, unsigned *prefix, unsigned *counts)
+{
+    __shared__ unsigned part[32];
+    const unsigned per = (G + blockDim.x - 1) / blockDim.x;
+    const unsigned lo = threadIdx.x * per, hi = min(lo + per, G);
+    unsigned sum = 0;
+    for (unsigned c = lo; c < hi; ++c) {
+        const unsigned n = slot.region_count[c];
+        counts[c] = n;
+        sum += (n + 31) >> 5;
+    }
+    // block-wide exclusive scan of the per-thread sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned inc = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) part[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        unsigned v = lane < nw ? part[lane] : 0u;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += y;
+        }
+        if (lane < nw) part[lane] = v;
+    }
+    __syncthreads();
+    unsigned run = (warp ? part[warp - 1] : 0u) + inc - sum;
+    for (unsigned c = lo; c < hi; ++c) {
+        prefix[c] = run;
+        run += (counts[c] + 31) >> 5;
+    }
+    if (threadIdx.x == blockDim.x - 1) prefix[G] = run;
+    __syncthreads();
+    return prefix[G];
+}
+
+// region holding chunk `ch`: the last c with prefix[c] <= ch
+__device__ __forceinline__ unsigned region_of(unsigned ch, const unsigned *prefix, unsigned G)
+{
+    unsigned lo = 0, hi = G;
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (prefix[mid] <= ch) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // ------------------------------------------------------------ ED refine
+// A warp takes 32 survivors at a time: one coalesced read of their positions
+// and bounds, one read of the live best-so-far, a ballot of those whose bound
+// is still within it; then real distances for those, two rows in flight.
 __global__ void __launch_bounds__(256)
 k_refine_ed(IndexView iv, QueryParams qp, QuerySlot slot)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ unsigned prefix[kMaxScanGrid + 1];
+    __shared__ unsigned counts[kMaxScanGrid];
     QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
     float *qs = reinterpret_cast<float *>(dsm);
     for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
-    __syncthreads();
+    const unsigned G = st->scan_grid;
+    const unsigned long long RW = st->region_words;
+    const unsigned nchunks = chunk_prefix(slot, G, prefix, counts);
     const int lane = threadIdx.x & 31;
-    const unsigned count = ld_volatile_u32(&st->surv_count);
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
-    unsigned long long done = 0, aband = 0, late = 0;
-    for (unsigned i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < count; i += nw) {
-        const unsigned pos = slot.surv_pos[i];
-        const float lb = slot.surv_lb[i];
-        const float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
-        if (lb > thr) { ++late; continue; }
-        const float d2 = warp_ed2(qs, iv.raw + (unsigned long long)pos * iv.len, iv.len, thr);
-        if (d2 > thr) { ++aband; continue; }
-        ++done;
-        if (lane == 0) offer(qp, slot, iv.status, d2, iv.ids[pos]);
-        __syncwarp();
+    unsigned long long done = 0, aband = 0;
+    for (unsigned ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += nw) {
+        const unsigned r = region_of(ch, prefix, G);
+        const unsigned within = (ch - prefix[r]) * 32 + lane;
+        const bool valid = within < counts[r];
+        const unsigned long long i = r * RW + within;
+        const unsigned pos = valid ? slot.surv_pos[i] : 0u;
+        const float lb = valid ? slot.surv_lb[i] : f_inf();
+        float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        unsigned mask = __ballot_sync(0xffffffffu, valid && lb <= thr);
+        while (mask) {
+            const int a = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int b = mask ? __ffs(mask) - 1 : -1;
+            if (b >= 0) mask &= mask - 1;
+            const unsigned pa = __shfl_sync(0xffffffffu, pos, a);
+            const unsigned pb = __shfl_sync(0xffffffffu, pos, b >= 0 ? b : a);
+            float da, db;
+            warp_ed2_pair(qs, iv.raw + (unsigned long long)pa * iv.len, iv.raw + (unsigned long long)pb * iv.len,
+                          iv.len, thr, da, db);
+            if (da <= thr) { ++done; if (lane == 0) offer(qp, slot, iv.status, da, iv.ids[pa]); }
+            else ++aband;
+            if (b >= 0) {
+                if (db <= thr) { ++done; if (lane == 0) offer(qp, slot, iv.status, db, iv.ids[pb]); }
+                else ++aband;
+            }
+            __syncwarp();
+            thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+            mask &= __ballot_sync(0xffffffffu, lb <= thr);
+        }
     }
     if (lane == 0) {
         if (done) atomicAdd(&st->c.refined, done);
@@ -443,6 +525,8 @@ __global__ void __launch_bounds__(256)
 k_lbk(IndexView iv, QueryParams qp, QuerySlot slot)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ unsigned prefix[kMaxScanGrid + 1];
+    __shared__ unsigned counts[kMaxScanGrid];
     QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
     float *Us = reinterpret_cast<float *>(dsm);
@@ -451,38 +535,62 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot)
         Us[i] = slot.U[i];
         Ls[i] = slot.L[i];
     }
-    __syncthreads();
+    const unsigned G = st->scan_grid;
+    const unsigned long long RW = st->region_words;
+    const unsigned nchunks = chunk_prefix(slot, G, prefix, counts);
     const int lane = threadIdx.x & 31;
-    const unsigned count = ld_volatile_u32(&st->surv_count);
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
     unsigned long long pass = 0;
-    for (unsigned i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < count; i += nw) {
-        const unsigned pos = slot.surv_pos[i];
-        float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
-        if (slot.surv_lb[i] > thr) continue;
-        const float *x = iv.raw + (unsigned long long)pos * iv.len;
-        // LB_Keogh^2, every operation rounded toward -inf (a certain lower bound)
-        float acc = 0.f;
-        bool pruned = false;
-        for (int base = 0; base < iv.len; base += 256) {
-            for (int t = lane; t < 256 && base + t < iv.len; t += 32) {
-                const int idx = base + t;
-                const float c = __ldg(x + idx);
-                float d = 0.f;
-                if (c > Us[idx]) d = __fsub_rd(c, Us[idx]);
-                else if (c < Ls[idx]) d = __fsub_rd(Ls[idx], c);
-                acc = __fadd_rd(acc, __fmul_rd(d, d));
-            }
-            float tot = acc;
+    unsigned pend = 0, npend = 0;          // passing positions, one per lane, flushed by 32
+    for (unsigned ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += nw) {
+        const unsigned r = region_of(ch, prefix, G);
+        const unsigned within = (ch - prefix[r]) * 32 + lane;
+        const bool valid = within < counts[r];
+        const unsigned long long i = r * RW + within;
+        const unsigned pos = valid ? slot.surv_pos[i] : 0u;
+        const float lb = valid ? slot.surv_lb[i] : f_inf();
+        const float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        unsigned mask = __ballot_sync(0xffffffffu, valid && lb <= thr);
+        while (mask) {
+            const int a = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const unsigned pa = __shfl_sync(0xffffffffu, pos, a);
+            const float *x = iv.raw + (unsigned long long)pa * iv.len;
+            // LB_Keogh^2, every operation rounded toward -inf (a certain lower bound)
+            float acc = 0.f;
+            bool pruned = false;
+            for (int base = 0; base < iv.len; base += 256) {
+                for (int t = lane; t < 256 && base + t < iv.len; t += 32) {
+                    const int idx = base + t;
+                    const float c = __ldg(x + idx);
+                    float d = 0.f;
+                    if (c > Us[idx]) d = __fsub_rd(c, Us[idx]);
+                    else if (c < Ls[idx]) d = __fsub_rd(Ls[idx], c);
+                    acc = __fadd_rd(acc, __fmul_rd(d, d));
+                }
+                float tot = acc;
 #pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) tot = __fadd_rd(tot, __shfl_xor_sync(0xffffffffu, tot, off));
-            if (tot > thr) { pruned = true; break; }
+                for (int off = 16; off >= 1; off >>= 1) tot = __fadd_rd(tot, __shfl_xor_sync(0xffffffffu, tot, off));
+                if (tot > thr) { pruned = true; break; }
+            }
+            if (!pruned) {
+                ++pass;
+                if (lane == (int)npend) pend = pa;
+                if (++npend == 32) {
+                    unsigned o = 0;
+                    if (lane == 0) o = atomicAdd(&st->surv2_count, 32u);
+                    o = __shfl_sync(0xffffffffu, o, 0);
+                    slot.surv2[o + lane] = pend;
+                    npend = 0;
+                }
+            }
         }
-        if (!pruned) {
-            ++pass;
-            if (lane == 0) slot.surv2[atomicAdd(&st->surv2_count, 1u)] = pos;
-        }
-        __syncwarp();
+    }
+    if (npend) {
+        unsigned o = 0;
+        if (lane == 0) o = atomicAdd(&st->surv2_count, npend);
+        o = __shfl_sync(0xffffffffu, o, 0);
+        if ((unsigned)lane < npend) slot.surv2[o + lane] = pend;
     }
     if (lane == 0 && pass) atomicAdd(&st->c.lbk_survivors, pass);
 }
@@ -716,8 +824,11 @@ void launch_seed(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cud
 void launch_scan(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s)
 {
     const unsigned long long ntiles = (iv.N + kScanTileWords - 1) / kScanTileWords;
-    const unsigned long long g = std::min<unsigned long long>(ntiles, (unsigned long long)num_sms() * 2);
-    k_lb_scan<<<(unsigned)g, kScanThreads, kScanSmem, s>>>(iv, qp, slot);
+    unsigned long long g = std::min<unsigned long long>(ntiles, (unsigned long long)num_sms() * kScanCtasPerSm);
+    g = std::min<unsigned long long>(g, kMaxScanGrid);
+    const unsigned long long tpc = (ntiles + g - 1) / g;
+    g = (ntiles + tpc - 1) / tpc;
+    k_lb_scan<<<(unsigned)g, kScanThreads, kScanSmem, s>>>(iv, qp, slot, (unsigned)tpc);
 }
 
 void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s,

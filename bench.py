@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=4, help="queries in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--form", default="both", choices=["both", "plain", "batched"])
     ap.add_argument("--mix", default="mixed", choices=["mixed", "fresh", "s0.1", "s0.5", "s1.0"],
                     help="query class (default: the paper-shaped mix)")
     return ap.parse_args()
@@ -193,6 +194,57 @@ def run_reference(args, ws, rank, local):
 
 
 # -------------------------------------------------------------- GPU arm
+def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists):
+    """W warm-up and K timed steps of one query form; per-step stats."""
+    import torch
+
+    def step(qs):
+        if form == "plain":
+            m.messi_query(ix, qs, k=k, ids=ids, dists=dists)
+        else:
+            m.messi_query_batched(ix, qs, k=k, batch=B, ids=ids, dists=dists)
+
+    m.messi_set_profiling(ix, True)
+    for s in range(W):
+        step(qpool[s * B:(s + 1) * B])
+    m.messi_check(ix)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = ClockSampler(dev.index or 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    agg = {"kern_ms": 0.0, "kern_launches": 0, "launches": 0, "survivors": 0, "rows": 0, "lat": []}
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(W, W + K):
+        step(qpool[s * B:(s + 1) * B])
+        st = m.messi_query_stats(ix)
+        agg["kern_ms"] += st["scan_ms"]
+        agg["kern_launches"] += st["scan_launches"]
+        agg["launches"] += st["kernel_launches"]
+        agg["survivors"] += st["lb_survivors"]
+        agg["rows"] += st["refined"] + st["abandoned"]
+        agg["lat"] += [st["query_ms_p50"], st["query_ms_p99"]]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    m.messi_check(ix)
+    if pg:
+        t = torch.tensor([elapsed_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    # per-query latency percentiles over every timed query in one call
+    if form == "plain":
+        m.messi_query(ix, qpool[W * B:(W + K) * B], k=k)
+    else:
+        m.messi_query_batched(ix, qpool[W * B:(W + K) * B], k=k, batch=B)
+    st_all = m.messi_query_stats(ix)
+    m.messi_set_profiling(ix, False)
+    agg.update(elapsed_ms=elapsed_ms, clocks=clk, p50=st_all["query_ms_p50"], p99=st_all["query_ms_p99"])
+    return agg
+
+
 def run_messi(args, ws, rank, local):
     import torch
 
@@ -223,53 +275,32 @@ def run_messi(args, ws, rank, local):
     ids = torch.empty((B, args.k), dtype=torch.int64, device=dev)
     dists = torch.empty((B, args.k), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    m.messi_set_profiling(ix, True)
-    for s in range(W):
-        m.messi_query(ix, qpool[s * B:(s + 1) * B], k=args.k, ids=ids, dists=dists)
-    m.messi_check(ix)
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    clocks = ClockSampler(local)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    scan_ms, scan_launches, launches, lat = 0.0, 0, 0, []
-    survivors, refined, abandoned = 0, 0, 0
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for s in range(W, W + K):
-        m.messi_query(ix, qpool[s * B:(s + 1) * B], k=args.k, ids=ids, dists=dists)
-        st = m.messi_query_stats(ix)
-        scan_ms += st["scan_ms"]
-        scan_launches += st["scan_launches"]
-        launches += st["kernel_launches"]
-        survivors += st["lb_survivors"]
-        refined += st["refined"]
-        abandoned += st["abandoned"]
-        lat += [st["query_ms_p50"], st["query_ms_p99"]]
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    elapsed_ms = e0.elapsed_time(e1)
-    m.messi_check(ix)
-    if pg:
-        t = torch.tensor([elapsed_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = ws * B * K / (elapsed_ms * 1e-3)
-
-    # per-query latency percentiles over the timed queries (separate pass so the
-    # percentile covers every query, not per-step summaries)
-    m.messi_query(ix, qpool[W * B:(W + K) * B], k=args.k)
-    st_all = m.messi_query_stats(ix)
-    m.messi_set_profiling(ix, False)
-
-    # roofline of the dominant kernel (the iSAX lower-bound scan)
-    scan_avg_s = scan_ms * 1e-3 / max(scan_launches, 1)
-    algo_bytes = 16.0 * args.n
-    achieved = algo_bytes / scan_avg_s / 1e9
     peak, peak_kind = measured_peak_hbm()
-    traffic = profiled_traffic(args.n)
+
+    forms = {}
+    for form in (["plain", "batched"] if args.form == "both" else [args.form]):
+        r = time_form(m, ix, qpool, form, B, K, W, args.k, stream, pg, dev, ids, dists)
+        nqt = B * K
+        kern_avg_s = r["kern_ms"] * 1e-3 / max(r["kern_launches"], 1)
+        if form == "plain":
+            kernel, algo = "k_lb_scan", 16.0 * args.n
+        else:
+            kernel = "k_fused_ed"
+            algo = 16.0 * args.n + 4.0 * args.len * r["rows"] / max(r["kern_launches"], 1)
+        q_bytes = 16.0 * args.n + 8.0 * r["survivors"] / nqt + 4.0 * args.len * r["rows"] / nqt
+        forms[form] = {
+            "value": ws * nqt / (r["elapsed_ms"] * 1e-3), "ms_per_step": r["elapsed_ms"] / K,
+            "p50_ms": r["p50"], "p99_ms": r["p99"], "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "roofline": {"bound": "hbm", "achieved": algo / kern_avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": algo / kern_avg_s / 1e9 / peak, "kernel": kernel, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": algo, "avg_launch_ms": kern_avg_s * 1e3},
+            "counters": {"lb_survivors_per_query": r["survivors"] / nqt, "rows_read_per_query": r["rows"] / nqt},
+            "query_roofline_frac": q_bytes / (r["elapsed_ms"] * 1e-3 / nqt) / 1e9 / peak,
+        }
+    head_form = max(forms, key=lambda f: forms[f]["value"])
+    head = forms[head_form]
+    traffic = profiled_traffic(args.n) if head["roofline"]["kernel"] == "k_lb_scan" else None
+    head["roofline"]["traffic"] = traffic
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     e2e = None
@@ -277,13 +308,15 @@ def run_messi(args, ws, rank, local):
         hq = qpool[W * B:(W + K) * B].cpu().pin_memory().numpy()
         hids = torch.empty((B, args.k), dtype=torch.int64).pin_memory().numpy()
         hd = torch.empty((B, args.k), dtype=torch.float32).pin_memory().numpy()
-        m.messi_query(ix, hq[:B], k=args.k, ids=hids, dists=hd)
+        call = (lambda q: m.messi_query(ix, q, k=args.k, ids=hids, dists=hd)) if head_form == "plain" else \
+            (lambda q: m.messi_query_batched(ix, q, k=args.k, batch=B, ids=hids, dists=hd))
+        call(hq[:B])
         t0 = time.perf_counter()
         for s in range(K):
-            m.messi_query(ix, hq[s * B:(s + 1) * B], k=args.k, ids=hids, dists=hd)
+            call(hq[s * B:(s + 1) * B])
         e2e_s = time.perf_counter() - t0
         e2e = {"value": ws * B * K / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": B * args.len * 4,
-               "d2h_bytes_per_step": B * args.k * 12}
+               "d2h_bytes_per_step": B * args.k * 12, "form": head_form}
 
     # FP64 oracle on a bounded sample: the CPU baseline and a parity spot check
     cpu = None
@@ -291,38 +324,29 @@ def run_messi(args, ws, rank, local):
     if rank == 0 and not args.no_cpu_baseline and args.cpu_sample > 0:
         qs = qpool[W * B:W * B + args.cpu_sample].cpu().numpy()
         r_ids, r_d2, cpu_s, threads = oracle_sample(data, qs, args.k)
-        g_ids, g_d = m.messi_query(ix, qs, k=args.k)
-        rel = np.abs(g_d.astype(np.float64) - np.sqrt(r_d2)) / np.maximum(np.sqrt(r_d2), 1e-30)
-        parity = {"ids_equal": bool(np.array_equal(g_ids, r_ids)), "max_rel_err": float(rel.max()),
-                  "queries": int(args.cpu_sample)}
+        parity = {"queries": int(args.cpu_sample)}
+        for form in forms:
+            fn = m.messi_query if form == "plain" else m.messi_query_batched
+            g_ids, g_d = fn(ix, qs, k=args.k)
+            rel = np.abs(g_d.astype(np.float64) - np.sqrt(r_d2)) / np.maximum(np.sqrt(r_d2), 1e-30)
+            parity[form] = {"ids_equal": bool(np.array_equal(g_ids, r_ids)), "max_rel_err": float(rel.max())}
         cpu = {"value": args.cpu_sample / cpu_s, "unit": "queries/s", "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_sample} queries of the timed mix, FP64 brute force over all {args.n} "
                          f"series (1M-row chunks copied to the host; copy time excluded)"}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": K, "warmup": W,
-            "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": value / PAPER_QPS, "dtype": "f32", "data": DATA_DESC,
+            "metric": METRIC, "value": head["value"], "unit": "queries/s", "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": head["value"] / PAPER_QPS, "dtype": "f32", "data": DATA_DESC,
             "config": {"workload": f"{args.n} x {args.len} fp32 random walks, ED, k={args.k}, 16 segments, "
-                                   f"8-bit SAX, plain per-query path", "queries": args.mix,
+                                   f"8-bit SAX", "form": head_form, "queries": args.mix,
                        "queries_per_step": B, "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (16 B iSAX word per series streamed per query)"},
-            "p50_ms": st_all["query_ms_p50"], "p99_ms": st_all["query_ms_p99"],
+            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
             "build_gbps": build_gbps, "build_ms": info["build_ms"],
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_lb_scan",
-                         "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
-                         "avg_launch_ms": scan_avg_s * 1e3},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "parity_sample": parity,
-            "counters": {"lb_survivors_per_query": survivors / (B * K), "refined_per_query": refined / (B * K),
-                         "rows_read_per_query": (refined + abandoned) / (B * K)},
-            "query_roofline": {
-                "bytes_per_query": 16.0 * args.n + 8.0 * survivors / (B * K)
-                                   + 4.0 * args.len * (refined + abandoned) / (B * K),
-                "frac": (16.0 * args.n + 8.0 * survivors / (B * K) + 4.0 * args.len * (refined + abandoned) / (B * K))
-                        / (elapsed_ms * 1e-3 / (B * K)) / 1e9 / peak},
+            "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": head["gpu_launches"],
+            "clocks": head["clocks"], "parity_sample": parity, "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if pg:

@@ -102,6 +102,55 @@ messi_status ensure_workspace(messi_index *ix)
     return MESSI_OK;
 }
 
+// Batched workspace: B query slots (no survivor arrays: the fused kernel keeps
+// survivors in shared memory), their device-side descriptor array, the work
+// counter and the call's counter accumulator.
+messi_status ensure_batch_workspace(messi_index *ix, unsigned B)
+{
+    if (ix->bws_block && (unsigned)ix->bws_slots >= B) return MESSI_OK;
+    if (ix->bws_block) {
+        cudaFree(ix->bws_block);
+        ix->device_bytes -= ix->bws_bytes;
+        ix->bws_block = nullptr;
+        ix->bws_slots = 0;
+    }
+    const size_t len = ix->len;
+    const size_t per = align256(sizeof(QueryState)) + align256(kMaxSegments * kMaxCard * 4) + 3 * align256(len * 4) +
+                       align256(kMaxK * 8) + align256(kLogCap * 8) + align256(kSeedMax * 8);
+    const size_t head = align256(B * sizeof(QuerySlot)) + align256(64) + align256(sizeof(QueryCounters));
+    char *base = nullptr;
+    if (cudaMalloc(&base, head + per * B) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate the batch workspace");
+    }
+    ix->bws_block = base;
+    ix->bws_bytes = head + per * B;
+    ix->bws_slots = (int)B;
+    ix->device_bytes += ix->bws_bytes;
+    ix->bslots_dev = reinterpret_cast<QuerySlot *>(base);
+    ix->bcounter = reinterpret_cast<unsigned *>(base + align256(B * sizeof(QuerySlot)));
+    ix->bacc = reinterpret_cast<QueryCounters *>(base + align256(B * sizeof(QuerySlot)) + align256(64));
+    std::vector<QuerySlot> host(B);
+    char *p = base + head;
+    for (unsigned b = 0; b < B; ++b) {
+        QuerySlot &q = host[b];
+        q = QuerySlot{};
+        q.st = reinterpret_cast<QueryState *>(p); p += align256(sizeof(QueryState));
+        q.lut = reinterpret_cast<float *>(p); p += align256(kMaxSegments * kMaxCard * 4);
+        q.q = reinterpret_cast<float *>(p); p += align256(len * 4);
+        q.U = reinterpret_cast<float *>(p); p += align256(len * 4);
+        q.L = reinterpret_cast<float *>(p); p += align256(len * 4);
+        q.karr = reinterpret_cast<unsigned long long *>(p); p += align256(kMaxK * 8);
+        q.log = reinterpret_cast<unsigned long long *>(p); p += align256(kLogCap * 8);
+        q.seedbuf = reinterpret_cast<unsigned long long *>(p); p += align256(kSeedMax * 8);
+        q.acc = ix->bacc;
+    }
+    if (!cuda_ok(cudaMemcpy(ix->bslots_dev, host.data(), B * sizeof(QuerySlot), cudaMemcpyHostToDevice),
+                 "messi_query_batched: slot table upload"))
+        return MESSI_ECUDA;
+    return MESSI_OK;
+}
+
 IndexView view_of(const messi_index *ix)
 {
     IndexView v;
@@ -465,20 +514,84 @@ messi_status messi_query(const messi_index *cix, const float *queries, uint32_t 
     ix->last.queries = nq;
     ix->last.kernel_launches = ix->launches - launches0;
     ix->last_stream = s;
+    ix->last_batched = false;
     if (hi) MESSI_CUDA(cudaMemcpyAsync(ids, did, ibytes, cudaMemcpyDeviceToHost, s));
     if (hd) MESSI_CUDA(cudaMemcpyAsync(dists, ddist, dbytes, cudaMemcpyDeviceToHost, s));
     if (hq || hi || hd) MESSI_CUDA(cudaStreamSynchronize(s));
     return MESSI_OK;
 }
 
-messi_status messi_query_batched(const messi_index *ix, const float *queries, uint32_t nq, uint32_t k,
+messi_status messi_query_batched(const messi_index *cix, const float *queries, uint32_t nq, uint32_t k,
                                  messi_dist dist, uint32_t window, uint32_t batch, int64_t *ids, float *dists,
                                  messi_stream stream)
 {
-    (void)batch;
-    messi_status chk = query_args(ix, queries, nq, k, dist, window, ids, dists);
+    messi_status chk = query_args(cix, queries, nq, k, dist, window, ids, dists);
     if (chk != MESSI_OK) return chk;
-    return fail(MESSI_EINVAL, "messi_query_batched: the batched form is not part of this build yet");
+    // DTW queries take the per-query kernels (the fused batch kernel is ED)
+    if (dist == MESSI_DTW) return messi_query(cix, queries, nq, k, dist, window, ids, dists, stream);
+    messi_index *ix = const_cast<messi_index *>(cix);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ensure_attributes();
+    const unsigned B = std::min<unsigned>(batch ? batch : ix->tune_batch, nq);
+    if ((chk = ensure_batch_workspace(ix, B)) != MESSI_OK) return chk;
+
+    const bool hq = !is_device_ptr(queries), hi = !is_device_ptr(ids), hd = !is_device_ptr(dists);
+    const size_t qbytes = (size_t)nq * ix->len * 4, ibytes = (size_t)nq * k * 8, dbytes = (size_t)nq * k * 4;
+    const size_t need = (hq ? align256(qbytes) : 0) + (hi ? align256(ibytes) : 0) + (hd ? align256(dbytes) : 0);
+    if (need && !ensure_stage(ix, need)) return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate staging buffers");
+    char *stage = static_cast<char *>(ix->stage_block);
+    const float *dq = queries;
+    long long *did = reinterpret_cast<long long *>(ids);
+    float *ddist = dists;
+    size_t so = 0;
+    if (hq) {
+        dq = reinterpret_cast<const float *>(stage + so);
+        MESSI_CUDA(cudaMemcpyAsync(stage + so, queries, qbytes, cudaMemcpyHostToDevice, s));
+        so += align256(qbytes);
+    }
+    if (hi) { did = reinterpret_cast<long long *>(stage + so); so += align256(ibytes); }
+    if (hd) { ddist = reinterpret_cast<float *>(stage + so); so += align256(dbytes); }
+
+    const IndexView iv = view_of(ix);
+    QueryParams qp;
+    qp.k = (int)k;
+    qp.dist = 0;
+    qp.r = 0;
+    qp.F = band_factor(0, ix->len);
+    MESSI_CUDA(cudaMemsetAsync(ix->bacc, 0, sizeof(QueryCounters), s));
+    const unsigned long long launches0 = ix->launches;
+    ix->scan_ev.clear();
+    ix->query_ev.clear();
+    size_t evn = 0;
+    for (uint32_t g = 0; g < nq; g += B) {
+        const unsigned nb = std::min<unsigned>(B, nq - g);
+        int eq0 = -1, es0 = -1;
+        cudaEvent_t f0 = nullptr, f1 = nullptr;
+        if (ix->profiling) {
+            eq0 = (int)evn;
+            cudaEventRecord(pool_event(ix, evn++), s);
+            es0 = (int)evn;
+            f0 = pool_event(ix, evn++);
+            f1 = pool_event(ix, evn++);
+        }
+        launch_batch(iv, qp, ix->bslots_dev, nb, dq + (size_t)g * ix->len, did + (size_t)g * k, ddist + (size_t)g * k,
+                     ix->tune_chunk_tiles, ix->tune_ctas_per_sm, ix->bcounter, s, &ix->launches, f0, f1);
+        if (ix->profiling) {
+            ix->scan_ev.push_back({es0, es0 + 1});
+            cudaEventRecord(pool_event(ix, evn++), s);
+            for (unsigned r = 0; r < nb; ++r) ix->query_ev.push_back({eq0, (int)evn - 1});
+        }
+    }
+    MESSI_CUDA(cudaGetLastError());
+    ix->last = messi_stats{};
+    ix->last.queries = nq;
+    ix->last.kernel_launches = ix->launches - launches0;
+    ix->last_stream = s;
+    ix->last_batched = true;
+    if (hi) MESSI_CUDA(cudaMemcpyAsync(ids, did, ibytes, cudaMemcpyDeviceToHost, s));
+    if (hd) MESSI_CUDA(cudaMemcpyAsync(dists, ddist, dbytes, cudaMemcpyDeviceToHost, s));
+    if (hq || hi || hd) MESSI_CUDA(cudaStreamSynchronize(s));
+    return MESSI_OK;
 }
 
 messi_status messi_query_stats(const messi_index *cix, messi_stats *out)
@@ -486,10 +599,11 @@ messi_status messi_query_stats(const messi_index *cix, messi_stats *out)
     if (!cix || !out) return fail(MESSI_EINVAL, "messi_query_stats: null argument");
     messi_index *ix = const_cast<messi_index *>(cix);
     *out = ix->last;
-    if (!ix->ws_block) return MESSI_OK;
+    const QueryCounters *acc = ix->last_batched ? ix->bacc : ix->slot.acc;
+    if (!acc) return MESSI_OK;
     MESSI_CUDA(cudaStreamSynchronize(ix->last_stream));
     QueryCounters c{};
-    MESSI_CUDA(cudaMemcpy(&c, ix->slot.acc, sizeof(c), cudaMemcpyDeviceToHost));
+    MESSI_CUDA(cudaMemcpy(&c, acc, sizeof(c), cudaMemcpyDeviceToHost));
     out->lb_evaluated = c.lb_evaluated;
     out->lb_survivors = c.lb_survivors;
     out->lbk_survivors = c.lbk_survivors;

@@ -131,6 +131,12 @@ struct messi_index {
     void *bws_block = nullptr;
     size_t bws_bytes = 0;
     int bws_slots = 0;
+    messi::QuerySlot *bslots_dev = nullptr;
+    unsigned *bcounter = nullptr;
+    messi::QueryCounters *bacc = nullptr;
+    bool last_batched = false;
+    // tuned shapes of the batched path
+    unsigned tune_batch = 64, tune_chunk_tiles = 32, tune_ctas_per_sm = 2;
     // bookkeeping
     size_t device_bytes = 0;
     double build_ms = 0.0;
@@ -185,6 +191,10 @@ void launch_finalize(const IndexView &iv, const QueryParams &qp, QuerySlot slot,
                      float *dists, cudaStream_t s);
 void launch_lower_bounds(const IndexView &iv, QuerySlot slot, float *lb2_by_id, cudaStream_t s);
 void init_kernel_attributes();
+void launch_batch(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
+                  const float *queries, long long *ids, float *dists, unsigned chunk_tiles, unsigned ctas_per_sm,
+                  unsigned *counter, cudaStream_t s, unsigned long long *launches, cudaEvent_t ev0 = nullptr,
+                  cudaEvent_t ev1 = nullptr);
 void launch_reset_state(QuerySlot slot, cudaStream_t s);
 float band_factor(int dist, int len);
 

@@ -62,8 +62,8 @@ __device__ __forceinline__ double gap_rd(double edge, double p)   // edge - p, e
     return d > 0.0 ? d : 0.0;
 }
 
-__global__ void __launch_bounds__(kPrepThreads)
-k_prep(IndexView iv, QueryParams qp, QuerySlot slot, const float *__restrict__ query)
+__device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot,
+                                          const float *__restrict__ query)
 {
     __shared__ double paa[kMaxSegments], paaU[kMaxSegments], paaL[kMaxSegments];
     __shared__ int sym[kMaxSegments];
@@ -191,6 +191,19 @@ k_prep(IndexView iv, QueryParams qp, QuerySlot slot, const float *__restrict__ q
     }
 }
 
+__global__ void __launch_bounds__(kPrepThreads)
+k_prep(IndexView iv, QueryParams qp, QuerySlot slot, const float *__restrict__ query)
+{
+    prep_body(iv, qp, slot, query);
+}
+
+// one block per query of a batch
+__global__ void __launch_bounds__(kPrepThreads)
+k_prep_batch(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, const float *__restrict__ queries)
+{
+    prep_body(iv, qp, slots[blockIdx.x], queries + (size_t)blockIdx.x * iv.len);
+}
+
 // ------------------------------------------------------------------ offer
 // Present a computed candidate (squared FP32 distance, original id).
 __device__ void offer(const QueryParams &qp, const QuerySlot &slot, unsigned *status, float d2, unsigned id)
@@ -239,8 +252,8 @@ __device__ void offer(const QueryParams &qp, const QuerySlot &slot, unsigned *st
 
 // ------------------------------------------------------------------ seed
 template <int DIST>
-__global__ void __launch_bounds__(256)
-k_seed_dist(IndexView iv, QueryParams qp, QuerySlot slot)
+__device__ __forceinline__ void seed_dist_body(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot,
+                                               unsigned part, unsigned nparts)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     QueryState *st = slot.st;
@@ -251,8 +264,8 @@ k_seed_dist(IndexView iv, QueryParams qp, QuerySlot slot)
     for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
     __syncthreads();
     float *diag = qs + iv.len + wib * 3 * iv.len;
-    const unsigned nw = gridDim.x * (blockDim.x >> 5);
-    for (unsigned p = lo + blockIdx.x * (blockDim.x >> 5) + wib; p < hi; p += nw) {
+    const unsigned nw = nparts * (blockDim.x >> 5);
+    for (unsigned p = lo + part * (blockDim.x >> 5) + wib; p < hi; p += nw) {
         const float *x = iv.raw + (unsigned long long)p * iv.len;
         float d2 = DIST == 0 ? warp_ed2(qs, x, iv.len, f_inf())
                              : warp_dtw<float>(qs, x, iv.len, qp.r, diag, f_inf());
@@ -261,9 +274,23 @@ k_seed_dist(IndexView iv, QueryParams qp, QuerySlot slot)
     }
 }
 
+template <int DIST>
+__global__ void __launch_bounds__(256)
+k_seed_dist(IndexView iv, QueryParams qp, QuerySlot slot)
+{
+    seed_dist_body<DIST>(iv, qp, slot, blockIdx.x, gridDim.x);
+}
+
+// blockIdx.y selects the query of the batch
+template <int DIST>
+__global__ void __launch_bounds__(256)
+k_seed_dist_batch(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots)
+{
+    seed_dist_body<DIST>(iv, qp, slots[blockIdx.y], blockIdx.x, gridDim.x);
+}
+
 // one block: sort the seed distances, keep the k best as the best-so-far
-__global__ void __launch_bounds__(kFinThreads)
-k_seed_select(IndexView iv, QueryParams qp, QuerySlot slot)
+__device__ __forceinline__ void seed_select_body(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot)
 {
     __shared__ unsigned long long buf[kSeedMax];
     QueryState *st = slot.st;
@@ -307,6 +334,18 @@ k_seed_select(IndexView iv, QueryParams qp, QuerySlot slot)
         st->c.seeded = cnt;
         st->c.bsf_updates = T != kEmpty ? 1ull : 0ull;
     }
+}
+
+__global__ void __launch_bounds__(kFinThreads)
+k_seed_select(IndexView iv, QueryParams qp, QuerySlot slot)
+{
+    seed_select_body(iv, qp, slot);
+}
+
+__global__ void __launch_bounds__(kFinThreads)
+k_seed_select_batch(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots)
+{
+    seed_select_body(iv, qp, slots[blockIdx.x]);
 }
 
 // ------------------------------------------------------------------ scan
@@ -625,6 +664,161 @@ k_dtw(IndexView iv, QueryParams qp, QuerySlot slot)
     }
 }
 
+// ------------------------------------------------- batched fused (ED)
+// One launch answers the lower-bound + refine part of a batch of queries.
+// Work items are (chunk of consecutive scan tiles, query) pairs handed out by
+// an atomic counter in chunk-major order, so all queries of a batch visit a
+// chunk close in time and its iSAX words come from HBM once and from L2 after.
+// Per item: the query's table and vector go to shared memory, the chunk's
+// words stream through TMA bulk copies, each tile's survivors (bound <= the
+// query's live best-so-far) are compacted in shared memory and refined right
+// away by the block's warps, so later tiles prune against the improved bound.
+constexpr int kFuThreads = 256;
+constexpr int kFuWpt = kScanTileWords / kFuThreads;    // 4 words per thread per tile
+constexpr int kFuStages = 4;
+constexpr int kFuSmemFixed = kMaxSegments * kMaxCard * 4 + kFuStages * kScanTileWords * 16 +
+                             kScanTileWords * 8;        // table + stages + survivor list
+
+__global__ void __launch_bounds__(kFuThreads, 2)
+k_fused_ed(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, unsigned B, unsigned chunk_tiles,
+           unsigned *__restrict__ counter)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long bars[kFuStages];
+    __shared__ unsigned s_item, s_n;
+    __shared__ float s_thr;
+    __shared__ int s_fail;
+    float *lut = reinterpret_cast<float *>(smem);
+    uint4 *stage = reinterpret_cast<uint4 *>(smem + kMaxSegments * kMaxCard * 4);
+    unsigned *list_pos = reinterpret_cast<unsigned *>(smem + kMaxSegments * kMaxCard * 4 +
+                                                      kFuStages * kScanTileWords * 16);
+    float *list_lb = reinterpret_cast<float *>(list_pos + kScanTileWords);
+    float *qs = list_lb + kScanTileWords;
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    const unsigned long long N = iv.N;
+    const unsigned long long ntiles = (N + kScanTileWords - 1) / kScanTileWords;
+    const unsigned long long nchunks = (ntiles + chunk_tiles - 1) / chunk_tiles;
+    const unsigned long long nitems = nchunks * B;
+    if (tid == 0) {
+        s_fail = 0;
+        for (int s = 0; s < kFuStages; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    __syncthreads();
+    unsigned uses[kFuStages] = {0, 0, 0, 0};   // completed phases per stage (thread-uniform)
+    while (true) {
+        if (tid == 0) s_item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const unsigned long long item = s_item;
+        if (item >= nitems || s_fail) break;
+        const unsigned b = (unsigned)(item % B);
+        const unsigned long long c = item / B;
+        const QuerySlot slot = slots[b];
+        QueryState *st = slot.st;
+        if (ld_volatile_u32(&st->invalid)) {   // uniform: every thread takes this branch
+            __syncthreads();
+            continue;
+        }
+        for (int i = tid; i < kMaxSegments * kMaxCard; i += blockDim.x) lut[i] = slot.lut[i];
+        for (int i = tid; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
+        const unsigned long long seed_lo = st->seed_lo, seed_hi = st->seed_hi;
+        const unsigned long long t0 = c * chunk_tiles, t1 = min(t0 + chunk_tiles, ntiles);
+        const unsigned nt = (unsigned)(t1 - t0);
+        auto issue = [&](unsigned long long tile, int sidx) {
+            const unsigned long long first = tile * kScanTileWords;
+            const unsigned long long cnt = min((unsigned long long)kScanTileWords, N - first);
+            const unsigned bytes = (unsigned)(cnt * 16);
+            mbar_arrive_expect_tx(&bars[sidx], bytes);
+            bulk_g2s(stage + sidx * kScanTileWords, iv.sax + first, bytes, &bars[sidx]);
+        };
+        if (tid == 0)
+            for (unsigned t = 0; t < nt && t < (unsigned)kFuStages; ++t) issue(t0 + t, (int)t);
+        __syncthreads();
+        unsigned long long evals = 0, nsurv = 0, done = 0, aband = 0;
+        for (unsigned t = 0; t < nt; ++t) {
+            const int sidx = t % kFuStages;
+            const bool ok = mbar_wait_bounded(&bars[sidx], uses[sidx] & 1u);
+            if (tid == 0) {
+                s_n = 0;
+                s_thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+            }
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicOr(iv.status, kStTimeout);
+                    s_fail = 1;
+                }
+                // let copies still in flight land before leaving
+                if (tid == 0)
+                    for (unsigned u = t; u < nt && u < t + kFuStages; ++u)
+                        mbar_wait_bounded(&bars[u % kFuStages], (uses[u % kFuStages] + (u - t) / kFuStages) & 1u);
+                return;
+            }
+            ++uses[sidx];
+            const float thr = s_thr;
+            const unsigned long long first = (t0 + t) * kScanTileWords;
+            const unsigned cnt = (unsigned)min((unsigned long long)kScanTileWords, N - first);
+            evals += cnt;
+#pragma unroll
+            for (int r = 0; r < kFuWpt; ++r) {
+                const unsigned j = tid + r * kFuThreads;
+                const bool valid = j < cnt;
+                const uint4 wv = valid ? stage[sidx * kScanTileWords + j] : make_uint4(0, 0, 0, 0);
+                float lb = lb2_half(wv.x, wv.y, lut, 0, 0.f);
+                if (__any_sync(0xffffffffu, valid && lb <= thr)) lb = lb2_half(wv.z, wv.w, lut, 8, lb);
+                const unsigned long long pos = first + j;
+                const bool surv = valid && lb <= thr && (pos < seed_lo || pos >= seed_hi);
+                const unsigned ballot = __ballot_sync(0xffffffffu, surv);
+                if (ballot) {
+                    unsigned base = 0;
+                    if (lane == 0) base = atomicAdd(&s_n, (unsigned)__popc(ballot));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (surv) {
+                        const unsigned o = base + __popc(ballot & ((1u << lane) - 1u));
+                        list_pos[o] = (unsigned)pos;
+                        list_lb[o] = lb;
+                    }
+                }
+            }
+            __syncthreads();
+            // words of this stage are consumed: prefetch the tile kFuStages ahead
+            if (tid == 0 && t + kFuStages < nt) issue(t0 + t + kFuStages, sidx);
+            const unsigned n = s_n;
+            nsurv += n;
+            // refine this tile's survivors: warps take two at a time
+            for (unsigned e = 2 * wib; e < n; e += 2 * (kFuThreads / 32)) {
+                const float live = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+                const bool ua = list_lb[e] <= live;
+                const bool ub = e + 1 < n && list_lb[e + 1] <= live;
+                if (!ua && !ub) continue;
+                const unsigned pa = list_pos[e], pb = (e + 1 < n) ? list_pos[e + 1] : pa;
+                float da, db;
+                warp_ed2_pair(qs, iv.raw + (unsigned long long)(ua ? pa : pb) * iv.len,
+                              iv.raw + (unsigned long long)pb * iv.len, iv.len, live, da, db);
+                if (ua) {
+                    if (da <= live) { ++done; if (lane == 0) offer(qp, slot, iv.status, da, iv.ids[pa]); }
+                    else ++aband;
+                }
+                if (ub) {
+                    if (db <= live) { ++done; if (lane == 0) offer(qp, slot, iv.status, db, iv.ids[pb]); }
+                    else ++aband;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            atomicAdd(&st->c.lb_evaluated, evals);
+            if (nsurv) atomicAdd(&st->c.lb_survivors, nsurv);
+        }
+        if (lane == 0) {
+            if (done) atomicAdd(&st->c.refined, done);
+            if (aband) atomicAdd(&st->c.abandoned, aband);
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------- finalize
 // Bitonic sort of n (power of two) entries in shared memory with a caller
 // ordering `less(i, j)` and swap `swap(i, j)`.
@@ -646,8 +840,8 @@ __device__ void block_bitonic(unsigned npow, Less less, Swap swap)
 
 constexpr int kFinSmem = kLogCap * (8 + 8);
 
-__global__ void __launch_bounds__(kFinThreads)
-k_finalize(IndexView iv, QueryParams qp, QuerySlot slot, long long *ids, float *dists)
+__device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot,
+                                              long long *ids, float *dists)
 {
     extern __shared__ __align__(16) unsigned char fsm[];
     unsigned long long *cand = reinterpret_cast<unsigned long long *>(fsm);
@@ -762,6 +956,18 @@ k_finalize(IndexView iv, QueryParams qp, QuerySlot slot, long long *ids, float *
     }
 }
 
+__global__ void __launch_bounds__(kFinThreads)
+k_finalize(IndexView iv, QueryParams qp, QuerySlot slot, long long *ids, float *dists)
+{
+    finalize_body(iv, qp, slot, ids, dists);
+}
+
+__global__ void __launch_bounds__(kFinThreads)
+k_finalize_batch(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, long long *ids, float *dists)
+{
+    finalize_body(iv, qp, slots[blockIdx.x], ids + (size_t)blockIdx.x * qp.k, dists + (size_t)blockIdx.x * qp.k);
+}
+
 // lower bound of every series, written in original id order
 __global__ void __launch_bounds__(256)
 k_lb_all(IndexView iv, QuerySlot slot, float *__restrict__ out)
@@ -796,6 +1002,8 @@ void init_kernel_attributes()
 {
     cudaFuncSetAttribute(k_lb_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
     cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinSmem);
+    cudaFuncSetAttribute(k_finalize_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinSmem);
+    cudaFuncSetAttribute(k_fused_ed, cudaFuncAttributeMaxDynamicSharedMemorySize, kFuSmemFixed + kMaxLen * 4);
     cudaFuncSetAttribute(k_dtw, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     cudaFuncSetAttribute(k_seed_dist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
 }
@@ -850,6 +1058,23 @@ void launch_finalize(const IndexView &iv, const QueryParams &qp, QuerySlot slot,
                      float *dists, cudaStream_t s)
 {
     k_finalize<<<1, kFinThreads, kFinSmem, s>>>(iv, qp, slot, ids, dists);
+}
+
+void launch_batch(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
+                  const float *queries, long long *ids, float *dists, unsigned chunk_tiles, unsigned ctas_per_sm,
+                  unsigned *counter, cudaStream_t s, unsigned long long *launches, cudaEvent_t ev0,
+                  cudaEvent_t ev1)
+{
+    k_prep_batch<<<B, kPrepThreads, 0, s>>>(iv, qp, slots_dev, queries);
+    k_seed_dist_batch<0><<<dim3(8, B), 256, iv.len * 4, s>>>(iv, qp, slots_dev);
+    k_seed_select_batch<<<B, kFinThreads, 0, s>>>(iv, qp, slots_dev);
+    cudaMemsetAsync(counter, 0, 4, s);
+    const size_t sm = kFuSmemFixed + (size_t)iv.len * 4;
+    if (ev0) cudaEventRecord(ev0, s);
+    k_fused_ed<<<num_sms() * ctas_per_sm, kFuThreads, sm, s>>>(iv, qp, slots_dev, B, chunk_tiles, counter);
+    if (ev1) cudaEventRecord(ev1, s);
+    k_finalize_batch<<<B, kFinThreads, kFinSmem, s>>>(iv, qp, slots_dev, ids, dists);
+    if (launches) *launches += 5;
 }
 
 void launch_lower_bounds(const IndexView &iv, QuerySlot slot, float *lb2_by_id, cudaStream_t s)

@@ -1,0 +1,75 @@
+"""The batched persistent fused form (many queries per launch) against the
+FP64 oracle and against the per-query path: same ids, distances within
+1e-5 relative of FP64, for several batch shapes including ragged tails."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def m():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import paper_2110_07519_gb300 as mod
+
+    return mod
+
+
+@pytest.fixture(scope="module")
+def coll(m):
+    x = synth.random_walks(100_000, 256, seed=synth.DATASET_SEED)
+    ix = m.messi_build(torch.from_numpy(x).cuda(), 16, 256)
+    q = synth.query_mix(x, 70, seed=synth.QUERY_SEED + 100)
+    return x, ix, q
+
+
+def check(ids, d, ref_ids, ref_d2):
+    ids = ids.cpu().numpy() if hasattr(ids, "cpu") else ids
+    d = d.cpu().numpy() if hasattr(d, "cpu") else d
+    assert np.array_equal(ids, ref_ids), np.argwhere(ids != ref_ids)[:5]
+    ref = np.sqrt(ref_d2)
+    err = np.abs(d.astype(np.float64) - ref) / np.maximum(ref, 1e-30)
+    err[(ref == 0) & (d == 0)] = 0
+    assert err.max() <= RTOL
+
+
+@pytest.mark.parametrize("k", [1, 10])
+@pytest.mark.parametrize("batch", [1, 16, 64, 0])
+def test_batched_matches_oracle_and_plain(m, coll, k, batch):
+    x, ix, q = coll
+    qd = torch.from_numpy(q).cuda()
+    ids, d = m.messi_query_batched(ix, qd, k=k, batch=batch)
+    m.messi_check(ix)
+    ref = oracle.knn(x, q, k)
+    check(ids, d, *ref)
+    pids, pd = m.messi_query(ix, qd, k=k)
+    assert np.array_equal(ids.cpu().numpy(), pids.cpu().numpy())
+    st = m.messi_query_stats(ix)
+    assert st["queries"] == len(q)
+
+
+def test_batched_host_buffers_and_ties(m):
+    x = synth.random_walks(20_000, 128, seed=5)
+    x[19_999] = x[3]
+    x[10_000] = x[3]
+    ix = m.messi_build(torch.from_numpy(x).cuda(), 16, 256, leaf_capacity=200)
+    q = np.concatenate([x[[3, 10_000]], synth.query_mix(x, 9, seed=6)])
+    ids, d = m.messi_query_batched(ix, q, k=3, batch=4)        # numpy in and out
+    m.messi_check(ix)
+    check(ids, d, *oracle.knn(x, q, 3))
+    assert ids[0].tolist() == [3, 10_000, 19_999]
+
+
+def test_batched_dtw_takes_per_query_kernels(m, coll):
+    x, ix, q = coll
+    sub = x[:20_000]
+    iy = m.messi_build(torch.from_numpy(sub).cuda(), 16, 256)
+    ids, d = m.messi_query_batched(iy, torch.from_numpy(q[:6]).cuda(), k=2, dist=m.MESSI_DTW, window=12)
+    m.messi_check(iy)
+    check(ids, d, *oracle.knn(sub, q[:6], 2, oracle.DTW, 12))

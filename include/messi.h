@@ -130,10 +130,20 @@ messi_status messi_query(const messi_index *ix, const float *queries, uint32_t n
                          messi_dist dist, uint32_t window, int64_t *ids, float *dists,
                          messi_stream stream);
 
-/* Batched form: up to `batch` queries share one pass over the iSAX words in a
- * persistent fused lower-bound-then-refine kernel (no counterpart in the
- * paper, which answers queries one at a time).  Same arguments and results
- * as messi_query; batch = 0 picks the tuned default. */
+/* Batched form (no counterpart in the paper, which answers queries one at a
+ * time): up to `batch` queries per launch.  Same arguments and results as
+ * messi_query; batch = 0 picks the tuned default.  Two modes, chosen with
+ * messi_set_batch_mode:
+ *   MESSI_BATCH_TC_SCREEN (default): every (series, query) squared distance is
+ *     estimated as |x|^2 + |q|^2 - 2 q.x with f16 tensor-core MMAs (FP32
+ *     accumulation), widened by a rigorous per-pair error bound; pairs whose
+ *     lower end stays within the query's k-th best bound are recomputed
+ *     exactly in FP32.  Needs len % 16 == 0, len <= 256 and |values| <= 65000
+ *     (an f16 copy of the rows, 2*len bytes per series, is built on first
+ *     use); otherwise, or for DTW, the call takes the other kernels.
+ *   MESSI_BATCH_LB_REFINE: a persistent fused lower-bound-then-refine kernel
+ *     where the queries of a batch share each pass over the iSAX words.
+ * DTW queries are answered by the per-query kernels. */
 messi_status messi_query_batched(const messi_index *ix, const float *queries, uint32_t nq,
                                  uint32_t k, messi_dist dist, uint32_t window, uint32_t batch,
                                  int64_t *ids, float *dists, messi_stream stream);
@@ -168,6 +178,20 @@ messi_status messi_lower_bounds_noalloc(const messi_index *ix, const float *quer
 
 /* Counters of the last query call.  Synchronises the index's last stream. */
 messi_status messi_query_stats(const messi_index *ix, messi_stats *out);
+
+enum { MESSI_BATCH_LB_REFINE = 0, MESSI_BATCH_TC_SCREEN = 1 };
+messi_status messi_set_batch_mode(messi_index *ix, int mode);
+
+/* Diagnostic of the tensor-core operand layout used by the screen: one
+ * 128 x n x k f16 GEMM tile, D = A * B^T with FP32 accumulation, through the
+ * same tcgen05 instructions.  a_tile (128 x k) and b_tile (n x k) are f16 bit
+ * patterns already in the operand layout (8-row x 16-byte core matrices, see
+ * paper_2110_07519_gb300/csrc/tc.cuh); lbo / sbo are the descriptor's
+ * leading and stride byte offsets; d receives 128 x n floats, row-major.
+ * Host pointers; synchronises the device.  k a multiple of 16 <= 256, n a
+ * multiple of 32 <= 256.  The paper has no counterpart. */
+messi_status messi_debug_tc_gemm(const uint16_t *a_tile, const uint16_t *b_tile, uint32_t k, uint32_t n,
+                                 uint32_t lbo, uint32_t sbo, float *d);
 
 /* Profiling mode: record CUDA events around every scan launch and every
  * query, reported by messi_query_stats.  Off by default. */

@@ -22,6 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmessi.so")
 
 MESSI_ED, MESSI_DTW = 0, 1
+MESSI_BATCH_LB_REFINE, MESSI_BATCH_TC_SCREEN = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY", 6: "ETIES"}
 
 if not os.path.exists(LIB_PATH):
@@ -68,6 +69,8 @@ _SIGS = {
     "messi_lower_bounds_noalloc": [_P, _P, _I, _U32, _P, _P],
     "messi_query_stats": [_P, ctypes.POINTER(MessiStats)],
     "messi_set_profiling": [_P, _I],
+    "messi_set_batch_mode": [_P, _I],
+    "messi_debug_tc_gemm": [_P, _P, _U32, _U32, _U32, _U32, _P],
     "messi_check": [_P, _P],
     "messi_summarize": [_P, _U64, _U32, _U32, _U32, _P, _P],
     "messi_index_layout": [_P, _P, _P, _P],
@@ -273,6 +276,21 @@ def messi_query_stats(index: Index) -> dict:
 
 def messi_set_profiling(index: Index, enable: bool = True):
     _check(_lib.messi_set_profiling(index.handle, 1 if enable else 0), "messi_set_profiling")
+
+
+def messi_set_batch_mode(index: Index, mode: int):
+    _check(_lib.messi_set_batch_mode(index.handle, mode), "messi_set_batch_mode")
+
+
+def messi_debug_tc_gemm(a_tile: np.ndarray, b_tile: np.ndarray, k: int, n: int, lbo: int, sbo: int) -> np.ndarray:
+    """One 128 x n x k tensor-core tile, D = A B^T (operands as f16 bit patterns
+    already in the tensor-core layout); returns D as float32 [128, n]."""
+    a = np.ascontiguousarray(a_tile, dtype=np.uint16)
+    b = np.ascontiguousarray(b_tile, dtype=np.uint16)
+    d = np.empty((128, n), dtype=np.float32)
+    _check(_lib.messi_debug_tc_gemm(a.ctypes.data, b.ctypes.data, k, n, lbo, sbo, d.ctypes.data),
+           "messi_debug_tc_gemm")
+    return d
 
 
 def messi_check(index: Index, stream=None):

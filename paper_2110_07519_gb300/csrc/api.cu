@@ -151,6 +151,86 @@ messi_status ensure_batch_workspace(messi_index *ix, unsigned B)
     return MESSI_OK;
 }
 
+// f16 tile copy of the rows for the tensor-core screen (built on first use).
+messi_status ensure_screen_copy(messi_index *ix, cudaStream_t s)
+{
+    if (ix->screen_state != 0) return MESSI_OK;
+    if (ix->len % 16 || ix->len > (int)kTcMaxLenHost) {
+        ix->screen_state = -1;
+        return MESSI_OK;
+    }
+    const unsigned long long rows = (ix->N + 127) / 128 * 128;
+    char *p = nullptr;
+    const size_t b16 = align256(rows * ix->len * 2), bn = align256(rows * 4);
+    if (cudaMalloc(&p, b16 + 2 * bn + 256) != cudaSuccess) {
+        cudaGetLastError();
+        ix->screen_state = -1;   // no room: the batched path uses the lower-bound kernels
+        return MESSI_OK;
+    }
+    ix->screen16 = reinterpret_cast<__half *>(p);
+    ix->xn = reinterpret_cast<float *>(p + b16);
+    ix->xnorm = reinterpret_cast<float *>(p + b16 + bn);
+    unsigned *bad = reinterpret_cast<unsigned *>(p + b16 + 2 * bn);
+    MESSI_CUDA(cudaMemsetAsync(bad, 0, 4, s));
+    launch_make_screen_copy(ix->raw, ix->N, ix->len, ix->screen16, ix->xn, ix->xnorm, bad, s);
+    ++ix->launches;
+    unsigned hbad = 0;
+    MESSI_CUDA(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s));
+    MESSI_CUDA(cudaStreamSynchronize(s));
+    if (hbad) {
+        cudaFree(p);
+        ix->screen16 = nullptr;
+        ix->screen_state = -1;
+        return MESSI_OK;
+    }
+    ix->device_bytes += b16 + 2 * bn + 256;
+    ix->screen_state = 1;
+    return MESSI_OK;
+}
+
+struct TcWs {
+    __half *qtiles;
+    float *qconst;
+    unsigned *Ubits, *cand_count, *flags, *active, *cand_pos, *n_active;
+};
+
+TcWs tc_ws_view(messi_index *ix)
+{
+    const unsigned P = (ix->tcws_B + 127) / 128 * 128;
+    char *p = static_cast<char *>(ix->tcws_block);
+    TcWs w;
+    w.qtiles = reinterpret_cast<__half *>(p); p += align256((size_t)P * ix->len * 2);
+    w.qconst = reinterpret_cast<float *>(p); p += align256((size_t)P * 16);
+    w.Ubits = reinterpret_cast<unsigned *>(p); p += align256((size_t)P * 4);
+    w.cand_count = reinterpret_cast<unsigned *>(p); p += align256((size_t)P * 4);
+    w.flags = reinterpret_cast<unsigned *>(p); p += align256((size_t)P * 4);
+    w.active = reinterpret_cast<unsigned *>(p); p += align256((size_t)P * 4);
+    w.n_active = reinterpret_cast<unsigned *>(p); p += 256;
+    w.cand_pos = reinterpret_cast<unsigned *>(p);
+    return w;
+}
+
+messi_status ensure_tc_workspace(messi_index *ix, unsigned B)
+{
+    if (ix->tcws_block && ix->tcws_B >= B) return MESSI_OK;
+    if (ix->tcws_block) {
+        cudaFree(ix->tcws_block);
+        ix->device_bytes -= ix->tcws_bytes;
+        ix->tcws_block = nullptr;
+    }
+    const size_t P = (B + 127) / 128 * 128;
+    const size_t bytes = align256(P * ix->len * 2) + align256(P * 16) + 4 * align256(P * 4) + 256 + P * kTcCap * 4;
+    if (cudaMalloc(&ix->tcws_block, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ix->tcws_block = nullptr;
+        return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate the screening workspace");
+    }
+    ix->tcws_bytes = bytes;
+    ix->tcws_B = B;
+    ix->device_bytes += bytes;
+    return MESSI_OK;
+}
+
 IndexView view_of(const messi_index *ix)
 {
     IndexView v;
@@ -294,8 +374,9 @@ messi_status messi_breakpoints(uint32_t cardinality, double *out)
 void messi_free(messi_index *ix)
 {
     if (!ix) return;
-    void *ptrs[] = {ix->raw, ix->sax, ix->ids, ix->pos_of_id, ix->leaf_off, ix->leaf_key, ix->leaf_depth,
-                    ix->beta64, ix->status, ix->ws_block, ix->stage_block, ix->bws_block};
+    void *ptrs[] = {ix->raw,    ix->sax,      ix->ids,         ix->pos_of_id, ix->leaf_off,
+                    ix->leaf_key, ix->leaf_depth, ix->beta64,   ix->status,    ix->ws_block,
+                    ix->stage_block, ix->bws_block, ix->screen16, ix->tcws_block};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : ix->ev_pool) cudaEventDestroy(e);
@@ -563,7 +644,68 @@ messi_status messi_query_batched(const messi_index *cix, const float *queries, u
     ix->scan_ev.clear();
     ix->query_ev.clear();
     size_t evn = 0;
-    for (uint32_t g = 0; g < nq; g += B) {
+    bool use_tc = ix->batch_mode == 1;
+    if (use_tc && (chk = ensure_screen_copy(ix, s)) != MESSI_OK) return chk;
+    use_tc = use_tc && ix->screen_state == 1;
+    if (use_tc && (chk = ensure_tc_workspace(ix, B)) != MESSI_OK) return chk;
+    for (uint32_t g = 0; g < nq && use_tc; g += B) {
+        const unsigned nb = std::min<unsigned>(B, nq - g);
+        int eq0 = -1, es0 = -1;
+        if (ix->profiling) {
+            eq0 = (int)evn;
+            cudaEventRecord(pool_event(ix, evn++), s);
+        }
+        const TcWs w = tc_ws_view(ix);
+        launch_batch_seed(iv, qp, ix->bslots_dev, nb, dq + (size_t)g * ix->len, s, &ix->launches);
+        launch_tc_qprep(ix->bslots_dev, nb, ix->len, qp, w.qtiles, w.qconst, w.Ubits, w.cand_count, w.flags,
+                        w.active, s);
+        ++ix->launches;
+        unsigned more = 1;
+        for (int pass = 0; pass < 3 && more; ++pass) {
+            if (ix->profiling) {
+                es0 = (int)evn;
+                cudaEventRecord(pool_event(ix, evn++), s);
+            }
+            launch_tc_screen(ix->screen16, ix->xn, ix->xnorm, w.qtiles, w.qconst, w.Ubits, w.cand_count, w.cand_pos,
+                             w.active, kTcCap, ix->N, ix->len, nb, (int)k, ix->status, s);
+            if (ix->profiling) {
+                cudaEventRecord(pool_event(ix, evn++), s);
+                ix->scan_ev.push_back({es0, es0 + 1});
+            }
+            launch_tc_recheck(iv, qp, ix->bslots_dev, nb, w.cand_count, w.cand_pos, kTcCap, w.active, s);
+            MESSI_CUDA(cudaMemsetAsync(w.n_active, 0, 4, s));
+            launch_tc_next_pass(ix->bslots_dev, nb, qp, kTcCap, w.Ubits, w.cand_count, w.active, w.n_active, s);
+            ix->launches += 3;
+            MESSI_CUDA(cudaMemcpyAsync(&more, w.n_active, 4, cudaMemcpyDeviceToHost, s));
+            MESSI_CUDA(cudaStreamSynchronize(s));
+        }
+        launch_batch_finalize(iv, qp, ix->bslots_dev, nb, did + (size_t)g * k, ddist + (size_t)g * k, s, &ix->launches);
+        // queries the screen could not settle (values outside f16 range, or
+        // still overflowing after three passes): the per-query kernels
+        std::vector<unsigned> hflags(nb), hact(nb);
+        MESSI_CUDA(cudaMemcpyAsync(hflags.data(), w.flags, nb * 4, cudaMemcpyDeviceToHost, s));
+        MESSI_CUDA(cudaMemcpyAsync(hact.data(), w.active, nb * 4, cudaMemcpyDeviceToHost, s));
+        MESSI_CUDA(cudaStreamSynchronize(s));
+        for (unsigned b = 0; b < nb; ++b) {
+            if ((hflags[b] & 4u) || hact[b]) {
+                if ((chk = ensure_workspace(ix)) != MESSI_OK) return chk;
+                QueryParams q1 = qp;
+                const QuerySlot one = ix->slot;
+                MESSI_CUDA(cudaMemsetAsync(one.acc, 0, sizeof(QueryCounters), s));
+                launch_prep(iv, q1, one, dq + (size_t)(g + b) * ix->len, s);
+                launch_seed(iv, q1, one, s, &ix->launches);
+                launch_scan(iv, q1, one, s);
+                launch_refine(iv, q1, one, s, &ix->launches);
+                launch_finalize(iv, q1, one, did + (size_t)(g + b) * k, ddist + (size_t)(g + b) * k, s);
+                ix->launches += 3;
+            }
+        }
+        if (ix->profiling) {
+            cudaEventRecord(pool_event(ix, evn++), s);
+            for (unsigned r = 0; r < nb; ++r) ix->query_ev.push_back({eq0, (int)evn - 1});
+        }
+    }
+    for (uint32_t g = 0; g < nq && !use_tc; g += B) {
         const unsigned nb = std::min<unsigned>(B, nq - g);
         int eq0 = -1, es0 = -1;
         cudaEvent_t f0 = nullptr, f1 = nullptr;
@@ -637,6 +779,14 @@ messi_status messi_query_stats(const messi_index *cix, messi_stats *out)
             out->query_ms_p99 = pct(0.99);
         }
     }
+    return MESSI_OK;
+}
+
+messi_status messi_set_batch_mode(messi_index *ix, int mode)
+{
+    if (!ix || (mode != MESSI_BATCH_LB_REFINE && mode != MESSI_BATCH_TC_SCREEN))
+        return fail(MESSI_EINVAL, "messi_set_batch_mode: unknown mode");
+    ix->batch_mode = mode;
     return MESSI_OK;
 }
 

@@ -291,4 +291,59 @@ __device__ T warp_dtw(const float *__restrict__ q, const float *__restrict__ x, 
     return diag[(last % 3) * n + (n - 1)];
 }
 
+// ------------------------------------------------------------------ offer
+// Present a computed candidate (squared FP32 distance, original id) to a
+// query's best-so-far.  Candidates within the near-tie band of the current
+// k-th best are logged for the final FP64 resolution.  k = 1 keeps the best
+// as a packed 64-bit atomicMin; k > 1 inserts into a sorted k-array under a
+// lock with a bounded spin.  Offering the same row twice changes nothing
+// (its packed value is already in the array or no longer qualifies); the
+// log may then hold it twice, which the final step removes.
+static __device__ __noinline__ void offer(const QueryParams &qp, const QuerySlot &slot, unsigned *status, float d2,
+                                   unsigned id)
+{
+    QueryState *st = slot.st;
+    const unsigned long long P = pack_cand(d2, id);
+    const unsigned long long T = ld_volatile_u64(&st->thr);
+    if (!(d2 <= prune_threshold(T, qp.F))) return;
+    const unsigned li = atomicAdd(&st->log_count, 1u);
+    if (li < (unsigned)kLogCap) slot.log[li] = P;
+    if (P >= T) return;
+    if (qp.k == 1) {
+        const unsigned long long old = atomicMin(&st->thr, P);
+        if (P < old) atomicAdd(&st->c.bsf_updates, 1ull);
+        return;
+    }
+    unsigned spins = 0;
+    while (atomicCAS(&st->lock, 0u, 1u) != 0u) {
+        if (++spins > kSpinLimit) {
+            atomicOr(status, kStTimeout);
+            return;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    volatile unsigned long long *ka = slot.karr;
+    volatile unsigned *kc = &st->kcount;
+    const unsigned cnt = *kc;
+    const unsigned k = (unsigned)qp.k;
+    bool present = false;
+    for (unsigned i = 0; i < cnt && !present; ++i) present = ka[i] == P;
+    if (!present && (cnt < k || P < ka[k - 1])) {
+        int pos = cnt < k ? (int)cnt : (int)k - 1;
+        if (cnt < k) *kc = cnt + 1;
+        while (pos > 0 && ka[pos - 1] > P) {
+            ka[pos] = ka[pos - 1];
+            --pos;
+        }
+        ka[pos] = P;
+        if (cnt + 1 >= k) {
+            atomicExch(&st->thr, ka[k - 1]);
+            atomicAdd(&st->c.bsf_updates, 1ull);
+        }
+    }
+    __threadfence();
+    atomicExch(&st->lock, 0u);
+}
+
 }  // namespace messi

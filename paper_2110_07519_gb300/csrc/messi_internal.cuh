@@ -18,6 +18,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "../../include/messi.h"
 
 namespace messi {
@@ -137,6 +139,14 @@ struct messi_index {
     bool last_batched = false;
     // tuned shapes of the batched path
     unsigned tune_batch = 64, tune_chunk_tiles = 32, tune_ctas_per_sm = 2;
+    int batch_mode = 1;                 // 0: lower bound + FP32 refine, 1: tensor-core screen
+    // tensor-core screen: f16 tile copy of the rows, norms, per-batch buffers
+    __half *screen16 = nullptr;
+    float *xn = nullptr, *xnorm = nullptr;
+    int screen_state = 0;               // 0 not built, 1 ready, -1 unavailable (values outside f16 range)
+    void *tcws_block = nullptr;
+    size_t tcws_bytes = 0;
+    unsigned tcws_B = 0;
     // bookkeeping
     size_t device_bytes = 0;
     double build_ms = 0.0;
@@ -191,6 +201,29 @@ void launch_finalize(const IndexView &iv, const QueryParams &qp, QuerySlot slot,
                      float *dists, cudaStream_t s);
 void launch_lower_bounds(const IndexView &iv, QuerySlot slot, float *lb2_by_id, cudaStream_t s);
 void init_kernel_attributes();
+// screen.cu
+constexpr unsigned kTcCap = 4096;    // candidates per query per screening pass
+constexpr unsigned kTcMaxLenHost = 256;
+size_t screen_smem_bytes(int len);
+void init_screen_attributes();
+void launch_make_screen_copy(const float *raw, unsigned long long N, int len, __half *tiles, float *xn, float *xnorm,
+                             unsigned *bad, cudaStream_t s);
+void launch_tc_qprep(const QuerySlot *slots, unsigned B, int len, const QueryParams &qp, __half *qtiles,
+                     float *qconst, unsigned *Ubits, unsigned *cand_count, unsigned *flags, unsigned *active,
+                     cudaStream_t s);
+void launch_tc_next_pass(const QuerySlot *slots, unsigned B, const QueryParams &qp, unsigned cap, unsigned *Ubits,
+                         unsigned *cand_count, unsigned *active, unsigned *n_active, cudaStream_t s);
+void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm, const __half *qtiles,
+                      const float *qconst, unsigned *Ubits, unsigned *cand_count, unsigned *cand_pos,
+                      const unsigned *active, unsigned cap, unsigned long long N, int len, unsigned B, int k,
+                      unsigned *status, cudaStream_t s);
+void launch_tc_recheck(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots, unsigned B,
+                       const unsigned *cand_count, const unsigned *cand_pos, unsigned cap, const unsigned *active,
+                       cudaStream_t s);
+void launch_batch_seed(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
+                       const float *queries, cudaStream_t s, unsigned long long *launches);
+void launch_batch_finalize(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
+                           long long *ids, float *dists, cudaStream_t s, unsigned long long *launches);
 void launch_batch(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
                   const float *queries, long long *ids, float *dists, unsigned chunk_tiles, unsigned ctas_per_sm,
                   unsigned *counter, cudaStream_t s, unsigned long long *launches, cudaEvent_t ev0 = nullptr,

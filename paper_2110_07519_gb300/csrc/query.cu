@@ -204,52 +204,6 @@ k_prep_batch(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, 
     prep_body(iv, qp, slots[blockIdx.x], queries + (size_t)blockIdx.x * iv.len);
 }
 
-// ------------------------------------------------------------------ offer
-// Present a computed candidate (squared FP32 distance, original id).
-__device__ void offer(const QueryParams &qp, const QuerySlot &slot, unsigned *status, float d2, unsigned id)
-{
-    QueryState *st = slot.st;
-    const unsigned long long P = pack_cand(d2, id);
-    const unsigned long long T = ld_volatile_u64(&st->thr);
-    if (!(d2 <= prune_threshold(T, qp.F))) return;
-    const unsigned li = atomicAdd(&st->log_count, 1u);
-    if (li < (unsigned)kLogCap) slot.log[li] = P;
-    if (P >= T) return;
-    if (qp.k == 1) {
-        const unsigned long long old = atomicMin(&st->thr, P);
-        if (P < old) atomicAdd(&st->c.bsf_updates, 1ull);
-        return;
-    }
-    unsigned spins = 0;
-    while (atomicCAS(&st->lock, 0u, 1u) != 0u) {
-        if (++spins > kSpinLimit) {
-            atomicOr(status, kStTimeout);
-            return;
-        }
-        __nanosleep(64);
-    }
-    __threadfence();
-    volatile unsigned long long *ka = slot.karr;
-    volatile unsigned *kc = &st->kcount;
-    const unsigned cnt = *kc;
-    const unsigned k = (unsigned)qp.k;
-    if (cnt < k || P < ka[k - 1]) {
-        int pos = cnt < k ? (int)cnt : (int)k - 1;
-        if (cnt < k) *kc = cnt + 1;
-        while (pos > 0 && ka[pos - 1] > P) {
-            ka[pos] = ka[pos - 1];
-            --pos;
-        }
-        ka[pos] = P;
-        if (cnt + 1 >= k) {
-            atomicExch(&st->thr, ka[k - 1]);
-            atomicAdd(&st->c.bsf_updates, 1ull);
-        }
-    }
-    __threadfence();
-    atomicExch(&st->lock, 0u);
-}
-
 // ------------------------------------------------------------------ seed
 template <int DIST>
 __device__ __forceinline__ void seed_dist_body(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot,
@@ -885,23 +839,52 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
             cand[i] = cand[j];
             cand[j] = t;
         });
+    // the same row may have been offered more than once (screened batches
+    // re-offer rows); equal packed entries are the same row: keep one
+    __shared__ int dup;
+    if (tid == 0) dup = 0;
+    __syncthreads();
+    unsigned long long *mark = reinterpret_cast<unsigned long long *>(d64);
+    for (unsigned i = tid; i < npow; i += blockDim.x) mark[i] = (i > 0 && i < c && cand[i] == cand[i - 1]) ? 1ull : 0ull;
+    __syncthreads();
+    for (unsigned i = tid; i < npow; i += blockDim.x)
+        if (mark[i]) { cand[i] = kEmpty; dup = 1; }
+    __syncthreads();
+    unsigned c_eff = c;
+    if (dup) {
+        block_bitonic(
+            npow, [&](unsigned i, unsigned j) { return cand[i] < cand[j]; },
+            [&](unsigned i, unsigned j) {
+                const unsigned long long t = cand[i];
+                cand[i] = cand[j];
+                cand[j] = t;
+            });
+        __shared__ unsigned nuniq;
+        if (tid == 0) nuniq = 0;
+        __syncthreads();
+        for (unsigned i = tid; i < c; i += blockDim.x)
+            if (cand[i] != kEmpty) atomicAdd(&nuniq, 1u);
+        __syncthreads();
+        c_eff = nuniq;
+    }
+    const unsigned cu = c_eff;
     // ambiguity: a candidate beyond the k-th inside the band, or two of the
     // first k within the band of each other (their order is not certain)
-    if (tid == 0 && c > k) ambiguous = 1;
-    for (unsigned i = tid; i + 1 < min(c, k); i += blockDim.x)
+    if (tid == 0 && cu > k) ambiguous = 1;
+    for (unsigned i = tid; i + 1 < min(cu, k); i += blockDim.x)
         if (cand_d2(cand[i + 1]) <= __fmul_ru(cand_d2(cand[i]), qp.F)) ambiguous = 1;
     __syncthreads();
     if (!ambiguous) {
         for (unsigned i = tid; i < k; i += blockDim.x) {
-            ids[i] = i < c ? (long long)cand_id(cand[i]) : -1;
-            dists[i] = i < c ? __fsqrt_rn(cand_d2(cand[i])) : f_inf();
+            ids[i] = i < cu ? (long long)cand_id(cand[i]) : -1;
+            dists[i] = i < cu ? __fsqrt_rn(cand_d2(cand[i])) : f_inf();
         }
     } else {
         // FP64 recomputation of every candidate in the band, in the operation
         // order of the FP64 reference evaluation
         const int lane = tid & 31, wib = tid >> 5;
         if (qp.dist == 0) {
-            for (unsigned e = tid; e < c; e += blockDim.x) {
+            for (unsigned e = tid; e < cu; e += blockDim.x) {
                 const unsigned pos = iv.pos_of_id[cand_id(cand[e])];
                 const float *x = iv.raw + (unsigned long long)pos * iv.len;
                 double s = 0.0;
@@ -913,7 +896,7 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
             }
         } else {
             double *diag = slot.dtw64 + (size_t)wib * 3 * iv.len;
-            for (unsigned e = wib; e < c; e += blockDim.x >> 5) {
+            for (unsigned e = wib; e < cu; e += blockDim.x >> 5) {
                 const unsigned pos = iv.pos_of_id[cand_id(cand[e])];
                 const double v = warp_dtw<double>(slot.q, iv.raw + (unsigned long long)pos * iv.len, iv.len,
                                                   qp.r, diag, (double)f_inf());
@@ -921,7 +904,7 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
                 __syncwarp();
             }
         }
-        for (unsigned i = c + tid; i < npow; i += blockDim.x) d64[i] = (double)f_inf();
+        for (unsigned i = cu + tid; i < npow; i += blockDim.x) d64[i] = (double)f_inf();
         __syncthreads();
         block_bitonic(
             npow,
@@ -937,10 +920,10 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
                 cand[j] = t;
             });
         for (unsigned i = tid; i < k; i += blockDim.x) {
-            ids[i] = i < c ? (long long)cand_id(cand[i]) : -1;
-            dists[i] = i < c ? (float)sqrt(d64[i]) : f_inf();
+            ids[i] = i < cu ? (long long)cand_id(cand[i]) : -1;
+            dists[i] = i < cu ? (float)sqrt(d64[i]) : f_inf();
         }
-        if (tid == 0) st->c.tie_rechecks += c;
+        if (tid == 0) st->c.tie_rechecks += cu;
     }
     __syncthreads();
     QueryCounters *acc = slot.acc;
@@ -1004,6 +987,7 @@ void init_kernel_attributes()
     cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinSmem);
     cudaFuncSetAttribute(k_finalize_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinSmem);
     cudaFuncSetAttribute(k_fused_ed, cudaFuncAttributeMaxDynamicSharedMemorySize, kFuSmemFixed + kMaxLen * 4);
+    init_screen_attributes();
     cudaFuncSetAttribute(k_dtw, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     cudaFuncSetAttribute(k_seed_dist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
 }
@@ -1075,6 +1059,22 @@ void launch_batch(const IndexView &iv, const QueryParams &qp, const QuerySlot *s
     if (ev1) cudaEventRecord(ev1, s);
     k_finalize_batch<<<B, kFinThreads, kFinSmem, s>>>(iv, qp, slots_dev, ids, dists);
     if (launches) *launches += 5;
+}
+
+void launch_batch_seed(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
+                       const float *queries, cudaStream_t s, unsigned long long *launches)
+{
+    k_prep_batch<<<B, kPrepThreads, 0, s>>>(iv, qp, slots_dev, queries);
+    k_seed_dist_batch<0><<<dim3(8, B), 256, iv.len * 4, s>>>(iv, qp, slots_dev);
+    k_seed_select_batch<<<B, kFinThreads, 0, s>>>(iv, qp, slots_dev);
+    if (launches) *launches += 3;
+}
+
+void launch_batch_finalize(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
+                           long long *ids, float *dists, cudaStream_t s, unsigned long long *launches)
+{
+    k_finalize_batch<<<B, kFinThreads, kFinSmem, s>>>(iv, qp, slots_dev, ids, dists);
+    if (launches) *launches += 1;
 }
 
 void launch_lower_bounds(const IndexView &iv, QuerySlot slot, float *lb2_by_id, cudaStream_t s)

@@ -1,0 +1,531 @@
+// screen.cu -- tensor-core screening of a query batch (no counterpart in the
+// paper, which answers one query at a time).
+//
+// For a batch of queries, squared ED is estimated for every (series, query)
+// pair as  s = |x|^2 + |q|^2 - 2 q.x  with the dot products from tcgen05 MMAs
+// on f16 copies of both (FP32 accumulation in TMEM).  Each estimate is
+// widened by a rigorous bound eps(x, q) on its error:
+//   |q.x - c| <= (2^-10 + (len + 16) 2^-23) 1.002 |q||x|
+//               + 2^-24 sqrt(len) 1.002 (|q| + |x|)          (f16 rounding of
+//                 both operands incl. subnormals, FP32 accumulation)
+//   plus 4u (|x|^2 + |q|^2 + 2|q||x|) for the FP32 evaluation of s and the
+//   FP32 rounding of the norms (computed in FP64).
+// so s - eps <= true d^2 <= s + eps.  A pair is a candidate when
+// s - eps <= U_q, U_q an upper bound of the query's true k-th squared
+// distance; for k = 1 every s + eps also tightens U_q.  Candidates are then
+// recomputed exactly in FP32 and offered to the query's best-so-far, and the
+// usual FP64 near-tie resolution finishes the query.  A query whose candidate
+// list overflows is screened again with its tightened bound.
+//
+// Operand tiles (see tc.cuh): rows of the collection are copied once to f16 in
+// 128-row tiles already in the tensor-core layout, so one bulk copy loads a
+// tile; queries are laid out the same way, 128 per tile.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "tc.cuh"
+
+namespace messi {
+namespace {
+
+constexpr int kTcRows = 128;        // M: series per tile
+constexpr int kTcQ = 128;           // N: queries per tile
+constexpr int kTcThreads = 256;
+constexpr float kKappa = 2.4e-7f;   // 4u
+constexpr int kTcMaxLen = 256;      // operand tiles of 128 x len halves: 3 tiles must fit in shared memory
+
+__device__ __forceinline__ float tc_coef(int len)
+{
+    return 1.002f * (9.765625e-4f + (float)(len + 16) * 1.1920929e-7f);
+}
+
+// ------------------------------------------------------- screen copy
+// One warp per series: f16 copy in tile layout, FP64 squared norm -> xn (FP32,
+// nearest) and |x| rounded up.
+__global__ void __launch_bounds__(256)
+k_make_screen_copy(const float *__restrict__ raw, unsigned long long N, int len, __half *__restrict__ tiles,
+                   float *__restrict__ xn, float *__restrict__ xnorm, unsigned *__restrict__ bad)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long ntile_rows = ((N + kTcRows - 1) / kTcRows) * kTcRows;
+    for (unsigned long long row = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+         row < ntile_rows; row += nw) {
+        const unsigned long long tile = row / kTcRows;
+        const unsigned r = (unsigned)(row % kTcRows);
+        unsigned char *tbase = reinterpret_cast<unsigned char *>(tiles) + tile * (unsigned long long)kTcRows * len * 2;
+        double ss = 0.0;
+        for (int k0 = lane * 8; k0 < len; k0 += 256) {
+            float v[8];
+            if (row < N) {
+                const float4 *src = reinterpret_cast<const float4 *>(raw + row * (unsigned long long)len + k0);
+                const float4 a = __ldg(src), b = __ldg(src + 1);
+                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[i] = 0.f;
+            }
+            __align__(16) __half h[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (fabsf(v[i]) > 65000.f) atomicOr(bad, 1u);
+                h[i] = __float2half_rn(v[i]);
+                ss = __dadd_rn(ss, __dmul_rn((double)v[i], (double)v[i]));
+            }
+            *reinterpret_cast<uint4 *>(tbase + tc_offset(r, (unsigned)k0, (unsigned)len)) = *reinterpret_cast<uint4 *>(h);
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+        if (lane == 0) {
+            xn[row] = (float)ss;
+            xnorm[row] = __double2float_ru(sqrt(ss * (1.0 + 1e-12)));
+        }
+    }
+}
+
+// ------------------------------------------------------- query prep
+// One block per query: f16 copy into its query tile, |q|^2 and |q|, the
+// per-query epilogue constants and the initial bound U_q from the seed.
+__global__ void __launch_bounds__(256)
+k_tc_qprep(const QuerySlot *__restrict__ slots, unsigned B, int len, QueryParams qp, __half *__restrict__ qtiles,
+           float *__restrict__ qconst, unsigned *__restrict__ Ubits, unsigned *__restrict__ cand_count,
+           unsigned *__restrict__ flags, unsigned *__restrict__ active)
+{
+    __shared__ double part[8];
+    const unsigned b = blockIdx.x;        // padded up to a multiple of kTcQ
+    const unsigned tile = b / kTcQ, r = b % kTcQ;
+    unsigned char *tbase = reinterpret_cast<unsigned char *>(qtiles) + (unsigned long long)tile * kTcQ * len * 2;
+    const bool real = b < B;
+    const float *q = real ? slots[b].q : nullptr;
+    double ss = 0.0;
+    bool big = false;
+    for (int k0 = threadIdx.x * 8; k0 < len; k0 += blockDim.x * 8) {
+        __align__(16) __half h[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float v = real ? q[k0 + i] : 0.f;
+            big |= !(fabsf(v) <= 65000.f);
+            h[i] = __float2half_rn(v);
+            ss = __dadd_rn(ss, __dmul_rn((double)v, (double)v));
+        }
+        *reinterpret_cast<uint4 *>(tbase + tc_offset(r, (unsigned)k0, (unsigned)len)) = *reinterpret_cast<uint4 *>(h);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+    big = __any_sync(0xffffffffu, big);
+    if (lane == 0) part[warp] = ss;
+    __shared__ int sbig;
+    if (threadIdx.x == 0) sbig = 0;
+    __syncthreads();
+    if (big) sbig = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        const float qn = (float)t;
+        const float qnorm = __double2float_ru(sqrt(t * (1.0 + 1e-12)));
+        const float beta = 5.9604645e-8f * sqrtf((float)len) * 1.002f;
+        const float alpha = (qnorm * (2.f * tc_coef(len) + 2.f * kKappa) + beta) * (1.f + 1e-6f);
+        const float gamma = (beta * qnorm + kKappa * qn) * (1.f + 1e-6f);
+        qconst[4 * b + 0] = qn;
+        qconst[4 * b + 1] = alpha;
+        qconst[4 * b + 2] = gamma;
+        qconst[4 * b + 3] = 0.f;
+        unsigned f = 0;
+        float U = -1.f;                  // padded or unusable query: no candidates
+        if (real) {
+            QueryState *st = slots[b].st;
+            if (ld_volatile_u32(&st->invalid)) f |= 2u;
+            else if (sbig) f |= 4u;      // outside f16 range: answered by the per-query path
+            else U = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        }
+        Ubits[b] = __float_as_uint(U);
+        cand_count[b] = 0;
+        flags[b] = f;
+        active[b] = (real && f == 0) ? 1u : 0u;
+    }
+}
+
+// Between passes: a query whose candidate list overflowed is screened again
+// with its bound tightened by the rechecked candidates; the others stop.
+__global__ void k_tc_next_pass(const QuerySlot *__restrict__ slots, unsigned B, QueryParams qp, unsigned cap,
+                               unsigned *__restrict__ Ubits, unsigned *__restrict__ cand_count,
+                               unsigned *__restrict__ active, unsigned *__restrict__ n_active)
+{
+    const unsigned b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    if (active[b] && cand_count[b] > cap) {
+        const float U = prune_threshold(ld_volatile_u64(&slots[b].st->thr), qp.F);
+        if (U < __uint_as_float(Ubits[b])) Ubits[b] = __float_as_uint(U);
+        cand_count[b] = 0;
+        atomicAdd(n_active, 1u);
+    } else {
+        active[b] = 0;
+    }
+}
+
+// ------------------------------------------------------------ screen
+struct ScreenArgs {
+    const __half *rtiles;     // [RT][128 x len] f16 rows
+    const float *xn, *xnorm;  // [RT * 128]
+    const unsigned *ids_unused;
+    const __half *qtiles;     // [QT][128 x len] f16 queries
+    const float *qconst;      // [QT*128][4]
+    unsigned *Ubits;          // [QT*128] float bits, atomically lowered (k = 1)
+    unsigned *cand_count;     // [QT*128]
+    unsigned *cand_pos;       // [QT*128][cap]
+    const unsigned *active;   // [QT*128]: nonzero when the query collects candidates this pass
+    unsigned cap;
+    unsigned long long N;
+    unsigned len;
+    unsigned QT;
+    int k;
+    unsigned *status;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_tc_screen(ScreenArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long bar_a[2], bar_m[2], bar_q;
+    __shared__ unsigned tmem_base;
+    __shared__ float sU[kTcQ], sAlpha[kTcQ], sGamma[kTcQ], sQn[kTcQ];
+    __shared__ unsigned sAct[kTcQ];
+    __shared__ int s_fail;
+    const unsigned len = a.len;
+    const unsigned tile_bytes = kTcRows * len * 2;
+    unsigned char *bufA0 = smem;
+    unsigned char *bufA1 = smem + tile_bytes;
+    unsigned char *bufQ = smem + 2 * tile_bytes;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned QT = a.QT;
+    const unsigned groups = gridDim.x / QT;                 // CTAs per query tile
+    const unsigned qt = blockIdx.x % QT, g = blockIdx.x / QT;
+    const unsigned long long RT = (a.N + kTcRows - 1) / kTcRows;
+    // row tiles of this CTA: g, g + groups, ...
+    const unsigned long long nt = g < RT ? (RT - g + groups - 1) / groups : 0;
+
+    if (warp == 0) tmem_alloc(&tmem_base, 256);
+    if (tid == 0) {
+        s_fail = 0;
+        mbar_init(&bar_a[0], 1);
+        mbar_init(&bar_a[1], 1);
+        mbar_init(&bar_m[0], 1);
+        mbar_init(&bar_m[1], 1);
+        mbar_init(&bar_q, 1);
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    if (tid < kTcQ) {
+        const unsigned j = qt * kTcQ + tid;
+        sU[tid] = __uint_as_float(a.Ubits[j]);
+        sQn[tid] = a.qconst[4 * j + 0];
+        sAlpha[tid] = a.qconst[4 * j + 1];
+        sGamma[tid] = a.qconst[4 * j + 2];
+        sAct[tid] = a.active[j];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tmem_base;
+    auto load_tile = [&](unsigned long long j, int b) {
+        const unsigned long long rt = g + j * groups;
+        mbar_arrive_expect_tx(&bar_a[b], tile_bytes);
+        bulk_g2s(b ? bufA1 : bufA0, reinterpret_cast<const unsigned char *>(a.rtiles) + rt * tile_bytes, tile_bytes,
+                 &bar_a[b]);
+    };
+    if (tid == 0 && nt > 0) {
+        mbar_arrive_expect_tx(&bar_q, tile_bytes);
+        bulk_g2s(bufQ, reinterpret_cast<const unsigned char *>(a.qtiles) + (unsigned long long)qt * tile_bytes,
+                 tile_bytes, &bar_q);
+        load_tile(0, 0);
+        if (nt > 1) load_tile(1, 1);
+    }
+    const unsigned idesc = tc_idesc_f16(kTcRows, kTcQ);
+    const unsigned lbo = 128, sbo = (len / 8) * 128;
+    const unsigned sA0 = smem_u32(bufA0), sA1 = smem_u32(bufA1), sQ = smem_u32(bufQ);
+    auto issue_mma = [&](unsigned long long j) -> bool {
+        const int b = (int)(j & 1);
+        if (!mbar_wait_bounded(&bar_a[b], (unsigned)((j >> 1) & 1))) return false;
+        tc_fence_after();
+        const unsigned sa = b ? sA1 : sA0;
+        for (unsigned kk = 0; kk < len / 16; ++kk)
+            tc_mma_f16(tmem + b * kTcQ, tc_desc(sa + kk * 256, lbo, sbo), tc_desc(sQ + kk * 256, lbo, sbo), idesc,
+                       kk > 0);
+        tc_commit(&bar_m[b]);
+        return true;
+    };
+    bool ok = true;
+    if (tid == 0 && nt > 0) {
+        ok = mbar_wait_bounded(&bar_q, 0);
+        if (ok) ok = issue_mma(0);
+        if (!ok) s_fail = 1;
+    }
+    __syncthreads();
+
+    const float coefk = kKappa;
+    const unsigned row_in = (unsigned)((warp & 3) * 32 + lane);   // TMEM lane = tile row
+    const unsigned col0 = (unsigned)(warp >> 2) * 64;             // this warp's 64 query columns
+    for (unsigned long long j = 0; j < nt && !s_fail; ++j) {
+        const int b = (int)(j & 1);
+        if (tid == 0 && j + 1 < nt) {
+            if (!issue_mma(j + 1)) s_fail = 1;
+        }
+        // MMA j done: its A buffer may be refilled, its accumulator read
+        const bool done = mbar_wait_bounded(&bar_m[b], (unsigned)((j >> 1) & 1));
+        if (__syncthreads_or(!done) || s_fail) {
+            if (tid == 0) s_fail = 1;
+            break;
+        }
+        tc_fence_after();
+        if (tid == 0 && j + 2 < nt) load_tile(j + 2, b);
+        const unsigned long long rt = g + j * groups;
+        const unsigned long long row = rt * kTcRows + row_in;
+        const bool rvalid = row < a.N;
+        const float xn = rvalid ? a.xn[row] : 0.f;
+        const float xnorm = rvalid ? a.xnorm[row] : 0.f;
+        const float kxn = coefk * xn;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            float acc[32];
+            tmem_ld32(tmem + ((unsigned)((warp & 3) * 32) << 16) + b * kTcQ + col0 + half * 32, acc);
+            if (!rvalid) continue;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const unsigned c = col0 + half * 32 + i;
+                const float shat = fmaf(-2.f, acc[i], xn + sQn[c]);
+                const float eps = fmaf(xnorm, sAlpha[c], sGamma[c] + kxn);
+                const float U = sU[c];
+                if (shat - eps <= U && sAct[c]) {
+                    const unsigned qj = qt * kTcQ + c;
+                    const unsigned o = atomicAdd(&a.cand_count[qj], 1u);
+                    if (o < a.cap) a.cand_pos[(unsigned long long)qj * a.cap + o] = (unsigned)row;
+                }
+                if (a.k == 1) {
+                    const float up = fmaxf(shat + eps, 0.f);
+                    if (up < U) {
+                        atomicMin(reinterpret_cast<unsigned *>(&sU[c]), __float_as_uint(up));
+                        atomicMin(&a.Ubits[qt * kTcQ + c], __float_as_uint(up));
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        // pick up bounds lowered by the other CTAs of this query tile
+        if ((j & 63) == 63 && tid < kTcQ) {
+            const float G = __uint_as_float(a.Ubits[qt * kTcQ + tid]);
+            if (G < sU[tid]) sU[tid] = G;
+        }
+    }
+    if (s_fail && tid == 0) atomicOr(a.status, kStTimeout);
+    // drain: the other accumulator / buffer may still have an MMA or copy in flight
+    if (tid == 0 && s_fail) {
+        mbar_wait_bounded(&bar_m[0], 0);
+        mbar_wait_bounded(&bar_m[1], 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// ----------------------------------------------------------- recheck
+// blockIdx.y: query; warps take its candidates, recompute the exact FP32
+// distance and offer it (offer is idempotent for a row offered before).
+__global__ void __launch_bounds__(256)
+k_tc_recheck(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, unsigned B,
+             const unsigned *__restrict__ cand_count, const unsigned *__restrict__ cand_pos, unsigned cap,
+             const unsigned *__restrict__ active)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const unsigned b = blockIdx.y;
+    if (b >= B || !active[b]) return;
+    const QuerySlot slot = slots[b];
+    QueryState *st = slot.st;
+    float *qs = reinterpret_cast<float *>(dsm);
+    for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
+    __syncthreads();
+    const unsigned n = min(cand_count[b], cap);
+    const int lane = threadIdx.x & 31;
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    unsigned long long done = 0, aband = 0;
+    for (unsigned e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < n; e += nw) {
+        const unsigned pos = cand_pos[(unsigned long long)b * cap + e];
+        if (pos >= st->seed_lo && pos < st->seed_hi) continue;      // offered by the seed already
+        const float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        const float d2 = warp_ed2(qs, iv.raw + (unsigned long long)pos * iv.len, iv.len, thr);
+        if (d2 <= thr) {
+            ++done;
+            if (lane == 0) offer(qp, slot, iv.status, d2, iv.ids[pos]);
+        } else {
+            ++aband;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (done) atomicAdd(&st->c.refined, done);
+        if (aband) atomicAdd(&st->c.abandoned, aband);
+    }
+}
+
+// --------------------------------------------------- diagnostic GEMM
+__global__ void __launch_bounds__(128)
+k_tc_gemm_test(const __half *A, const __half *Bm, float *D, unsigned K, unsigned N, unsigned lbo, unsigned sbo,
+               unsigned *status)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long bar_ld, bar_mma;
+    __shared__ unsigned tmem_base;
+    const unsigned abytes = 128 * K * 2, bbytes = N * K * 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tmem_alloc(&tmem_base, 256);
+    if (tid == 0) {
+        mbar_init(&bar_ld, 1);
+        mbar_init(&bar_mma, 1);
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tmem_base;
+    bool ok = true;
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar_ld, abytes + bbytes);
+        bulk_g2s(smem, A, abytes, &bar_ld);
+        bulk_g2s(smem + abytes, Bm, bbytes, &bar_ld);
+        ok = mbar_wait_bounded(&bar_ld, 0);
+        if (ok) {
+            tc_fence_after();
+            const unsigned sa = smem_u32(smem), sb = smem_u32(smem + abytes);
+            for (unsigned kk = 0; kk < K / 16; ++kk)
+                tc_mma_f16(tmem, tc_desc(sa + kk * 256, lbo, sbo), tc_desc(sb + kk * 256, lbo, sbo),
+                           tc_idesc_f16(128, N), kk > 0);
+            tc_commit(&bar_mma);
+            ok = mbar_wait_bounded(&bar_mma, 0);
+        }
+        if (!ok) atomicOr(status, kStTimeout);
+    }
+    __syncthreads();
+    tc_fence_after();
+    for (unsigned c0 = 0; c0 < N; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + c0, v);
+        for (int i = 0; i < 32; ++i) D[(warp * 32 + lane) * N + c0 + i] = v[i];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+}  // namespace
+
+// At least 120 KB so that a single screen CTA fits on an SM: each CTA holds
+// 256 TMEM columns for its whole (persistent) life, and a second or third
+// resident CTA would wait in tcgen05.alloc for columns that never free up.
+size_t screen_smem_bytes(int len) { return std::max<size_t>(3ull * kTcRows * len * 2, 120ull * 1024); }
+
+void init_screen_attributes()
+{
+    cudaFuncSetAttribute(k_tc_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)screen_smem_bytes(kTcMaxLen));
+}
+
+void launch_make_screen_copy(const float *raw, unsigned long long N, int len, __half *tiles, float *xn, float *xnorm,
+                             unsigned *bad, cudaStream_t s)
+{
+    const unsigned long long rows = ((N + kTcRows - 1) / kTcRows) * kTcRows;
+    const unsigned long long want = (rows + 7) / 8;
+    const unsigned long long cap = (unsigned long long)num_sms() * 16;
+    k_make_screen_copy<<<(unsigned)std::min(want, cap), 256, 0, s>>>(raw, N, len, tiles, xn, xnorm, bad);
+}
+
+void launch_tc_qprep(const QuerySlot *slots, unsigned B, int len, const QueryParams &qp, __half *qtiles,
+                     float *qconst, unsigned *Ubits, unsigned *cand_count, unsigned *flags, unsigned *active,
+                     cudaStream_t s)
+{
+    const unsigned padded = (B + kTcQ - 1) / kTcQ * kTcQ;
+    k_tc_qprep<<<padded, 256, 0, s>>>(slots, B, len, qp, qtiles, qconst, Ubits, cand_count, flags, active);
+}
+
+void launch_tc_next_pass(const QuerySlot *slots, unsigned B, const QueryParams &qp, unsigned cap, unsigned *Ubits,
+                         unsigned *cand_count, unsigned *active, unsigned *n_active, cudaStream_t s)
+{
+    k_tc_next_pass<<<(B + 255) / 256, 256, 0, s>>>(slots, B, qp, cap, Ubits, cand_count, active, n_active);
+}
+
+void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm, const __half *qtiles,
+                      const float *qconst, unsigned *Ubits, unsigned *cand_count, unsigned *cand_pos,
+                      const unsigned *active, unsigned cap, unsigned long long N, int len, unsigned B, int k,
+                      unsigned *status, cudaStream_t s)
+{
+    ScreenArgs a;
+    a.rtiles = rtiles;
+    a.xn = xn;
+    a.xnorm = xnorm;
+    a.ids_unused = nullptr;
+    a.qtiles = qtiles;
+    a.qconst = qconst;
+    a.Ubits = Ubits;
+    a.cand_count = cand_count;
+    a.cand_pos = cand_pos;
+    a.active = active;
+    a.cap = cap;
+    a.N = N;
+    a.len = (unsigned)len;
+    a.QT = (B + kTcQ - 1) / kTcQ;
+    a.k = k;
+    a.status = status;
+    const unsigned groups = std::max(1u, (unsigned)num_sms() / a.QT);
+    k_tc_screen<<<groups * a.QT, kTcThreads, screen_smem_bytes(len), s>>>(a);
+}
+
+void launch_tc_recheck(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots, unsigned B,
+                       const unsigned *cand_count, const unsigned *cand_pos, unsigned cap, const unsigned *active,
+                       cudaStream_t s)
+{
+    k_tc_recheck<<<dim3(4, B), 256, iv.len * 4, s>>>(iv, qp, slots, B, cand_count, cand_pos, cap, active);
+}
+
+messi_status debug_tc_gemm(const uint16_t *A_host, const uint16_t *B_host, unsigned K, unsigned N, unsigned lbo,
+                           unsigned sbo, float *D_host)
+{
+    const size_t ab = 128ull * K * 2, bb = (size_t)N * K * 2, db = 128ull * N * 4;
+    char *d = nullptr;
+    if (cudaMalloc(&d, ab + bb + db + 256) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MESSI_ENOMEM, "messi_debug_tc_gemm: out of device memory");
+    }
+    unsigned *status = reinterpret_cast<unsigned *>(d + ab + bb + db);
+    cudaError_t e = cudaMemcpy(d, A_host, ab, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + ab, B_host, bb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(status, 0, 4);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tc_gemm_test, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(ab + bb));
+    if (e == cudaSuccess) {
+        k_tc_gemm_test<<<1, 128, ab + bb>>>(reinterpret_cast<const __half *>(d), reinterpret_cast<const __half *>(d + ab),
+                                            reinterpret_cast<float *>(d + ab + bb), K, N, lbo, sbo, status);
+        e = cudaDeviceSynchronize();
+    }
+    unsigned st = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, status, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(D_host, d + ab + bb, db, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(MESSI_ECUDA, std::string("messi_debug_tc_gemm: ") + cudaGetErrorString(e));
+    if (st) return fail(MESSI_ETIMEOUT, "messi_debug_tc_gemm: a bounded wait ran out");
+    return MESSI_OK;
+}
+
+}  // namespace messi
+
+extern "C" messi_status messi_debug_tc_gemm(const uint16_t *a_tile, const uint16_t *b_tile, uint32_t k, uint32_t n,
+                                            uint32_t lbo, uint32_t sbo, float *d)
+{
+    if (!a_tile || !b_tile || !d) return messi::fail(MESSI_EINVAL, "messi_debug_tc_gemm: null argument");
+    if (k == 0 || k % 16 || k > 256 || n == 0 || n % 32 || n > 256)
+        return messi::fail(MESSI_EINVAL, "messi_debug_tc_gemm: k must be a multiple of 16 <= 256, n a multiple of 32 <= 256");
+    return messi::debug_tc_gemm(a_tile, b_tile, k, n, lbo, sbo, d);
+}

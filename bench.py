@@ -40,12 +40,14 @@ def parse():
     ap.add_argument("--impl", default="messi", choices=["messi", "reference"])
     ap.add_argument("--n", type=int, default=100_000_000)
     ap.add_argument("--len", type=int, default=256)
-    ap.add_argument("--batch", type=int, default=256, help="queries per step")
+    ap.add_argument("--batch", type=int, default=1024, help="queries per step")
     ap.add_argument("--k", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=4, help="queries in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--form", default="both", choices=["both", "plain", "batched"])
+    ap.add_argument("--batch-mode", default="tc", choices=["tc", "lb"],
+                    help="batched kernels: tensor-core screen (tc) or fused lower bound + refine (lb)")
     ap.add_argument("--mix", default="mixed", choices=["mixed", "fresh", "s0.1", "s0.5", "s1.0"],
                     help="query class (default: the paper-shaped mix)")
     return ap.parse_args()
@@ -95,6 +97,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_peak_tensor():
+    """Dense f16/bf16 tensor peak in TFLOP/s: the sustained cuBLAS bf16 figure
+    (the screen runs for hundreds of ms at a time); f16 and bf16 share a rate."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured (bf16 sustained; f16 same rate)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback"
+
+
 def measured_peak_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -103,25 +115,26 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def scan_source_sha():
+def scan_source_sha(kernel: str = "k_lb_scan"):
     h = hashlib.sha256()
-    for name in ("query.cu", "device_common.cuh"):
+    files = ("screen.cu", "tc.cuh", "device_common.cuh") if kernel == "k_tc_screen" else ("query.cu", "device_common.cuh")
+    for name in files:
         with open(os.path.join(ROOT, "paper_2110_07519_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(n_series: int):
-    """DRAM bytes per scan launch from the committed ncu summary, scaled to
-    n_series, or None when the scan source changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "lb_scan_traffic.txt")
+def profiled_traffic(n_series: int, kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    to n_series, or None when its source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     try:
         text = open(path).read()
     except OSError:
         return None
     sha = re.search(r"source_sha:\s*(\w+)", text)
     per = re.search(r"dram_bytes_per_series:\s*([0-9.eE+-]+)", text)
-    if not sha or not per or sha.group(1) != scan_source_sha():
+    if not sha or not per or sha.group(1) != scan_source_sha(kernel):
         return None
     return float(per.group(1)) * n_series
 
@@ -277,6 +290,22 @@ def run_messi(args, ws, rank, local):
     stream = torch.cuda.current_stream(dev)
     peak, peak_kind = measured_peak_hbm()
 
+    # CPU baseline: the FP64 oracle on a bounded sample of the timed queries,
+    # over the generated collection (which is then released: the index holds
+    # its own copy)
+    cpu, oracle_q, r_ids, r_d2 = None, None, None, None
+    if rank == 0 and not args.no_cpu_baseline and args.cpu_sample > 0:
+        oracle_q = qpool[W * B:W * B + args.cpu_sample].cpu().numpy()
+        r_ids, r_d2, cpu_s, threads = oracle_sample(data, oracle_q, args.k)
+        cpu = {"value": args.cpu_sample / cpu_s, "unit": "queries/s", "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_sample} queries of the timed mix, FP64 brute force over all {args.n} "
+                         f"series (1M-row chunks copied to the host; copy time excluded)"}
+    qpool = qpool.clone()
+    del data
+    torch.cuda.empty_cache()
+
+    batch_mode = "tc_screen" if args.batch_mode == "tc" else "lb_refine"
+    m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN if args.batch_mode == "tc" else m.MESSI_BATCH_LB_REFINE)
     forms = {}
     for form in (["plain", "batched"] if args.form == "both" else [args.form]):
         r = time_form(m, ix, qpool, form, B, K, W, args.k, stream, pg, dev, ids, dists)
@@ -284,22 +313,31 @@ def run_messi(args, ws, rank, local):
         kern_avg_s = r["kern_ms"] * 1e-3 / max(r["kern_launches"], 1)
         if form == "plain":
             kernel, algo = "k_lb_scan", 16.0 * args.n
+            roof = {"bound": "hbm", "achieved": algo / kern_avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": algo / kern_avg_s / 1e9 / peak, "peak_kind": peak_kind}
+        elif batch_mode == "tc_screen":
+            # the screen's dense work: 2 * len flops per (series, query) pair, B queries per launch
+            kernel, algo = "k_tc_screen", 2.0 * args.len * args.n * B
+            tpk, tkind = measured_peak_tensor()
+            roof = {"bound": "tensor", "achieved": algo / kern_avg_s / 1e12, "peak": tpk, "unit": "TFLOP/s",
+                    "frac": algo / kern_avg_s / 1e12 / tpk, "peak_kind": tkind}
         else:
             kernel = "k_fused_ed"
             algo = 16.0 * args.n + 4.0 * args.len * r["rows"] / max(r["kern_launches"], 1)
+            roof = {"bound": "hbm", "achieved": algo / kern_avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": algo / kern_avg_s / 1e9 / peak, "peak_kind": peak_kind}
         q_bytes = 16.0 * args.n + 8.0 * r["survivors"] / nqt + 4.0 * args.len * r["rows"] / nqt
         forms[form] = {
             "value": ws * nqt / (r["elapsed_ms"] * 1e-3), "ms_per_step": r["elapsed_ms"] / K,
             "p50_ms": r["p50"], "p99_ms": r["p99"], "gpu_launches": r["launches"], "clocks": r["clocks"],
-            "roofline": {"bound": "hbm", "achieved": algo / kern_avg_s / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": algo / kern_avg_s / 1e9 / peak, "kernel": kernel, "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": algo, "avg_launch_ms": kern_avg_s * 1e3},
+            "roofline": dict(roof, kernel=kernel, algorithmic_per_launch=algo, avg_launch_ms=kern_avg_s * 1e3,
+                             launches=r["kern_launches"]),
             "counters": {"lb_survivors_per_query": r["survivors"] / nqt, "rows_read_per_query": r["rows"] / nqt},
             "query_roofline_frac": q_bytes / (r["elapsed_ms"] * 1e-3 / nqt) / 1e9 / peak,
         }
     head_form = max(forms, key=lambda f: forms[f]["value"])
     head = forms[head_form]
-    traffic = profiled_traffic(args.n) if head["roofline"]["kernel"] == "k_lb_scan" else None
+    traffic = profiled_traffic(args.n, head["roofline"]["kernel"])
     head["roofline"]["traffic"] = traffic
 
     # end to end through the C ABI with host buffers (pinned), copies inside
@@ -318,21 +356,14 @@ def run_messi(args, ws, rank, local):
         e2e = {"value": ws * B * K / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": B * args.len * 4,
                "d2h_bytes_per_step": B * args.k * 12, "form": head_form}
 
-    # FP64 oracle on a bounded sample: the CPU baseline and a parity spot check
-    cpu = None
-    parity = None
-    if rank == 0 and not args.no_cpu_baseline and args.cpu_sample > 0:
-        qs = qpool[W * B:W * B + args.cpu_sample].cpu().numpy()
-        r_ids, r_d2, cpu_s, threads = oracle_sample(data, qs, args.k)
-        parity = {"queries": int(args.cpu_sample)}
+    # FP64 oracle on the bounded sample, answered by each form after timing
+    parity = {"queries": int(oracle_q.shape[0])} if oracle_q is not None else None
+    if oracle_q is not None:
         for form in forms:
             fn = m.messi_query if form == "plain" else m.messi_query_batched
-            g_ids, g_d = fn(ix, qs, k=args.k)
+            g_ids, g_d = fn(ix, oracle_q, k=args.k)
             rel = np.abs(g_d.astype(np.float64) - np.sqrt(r_d2)) / np.maximum(np.sqrt(r_d2), 1e-30)
             parity[form] = {"ids_equal": bool(np.array_equal(g_ids, r_ids)), "max_rel_err": float(rel.max())}
-        cpu = {"value": args.cpu_sample / cpu_s, "unit": "queries/s", "cores": threads, "kind": "oracle",
-               "sample": f"{args.cpu_sample} queries of the timed mix, FP64 brute force over all {args.n} "
-                         f"series (1M-row chunks copied to the host; copy time excluded)"}
 
     if rank == 0:
         line = {

@@ -32,7 +32,8 @@ namespace {
 constexpr int kTcRows = 128;        // M: series per tile
 constexpr int kTcQ = 128;           // N: queries per tile
 constexpr int kTcThreads = 256;
-constexpr float kKappa = 2.4e-7f;   // 4u
+constexpr float kKappa = 2.4e-7f;   // 4u: FP32 evaluation of s and rounding of the norms
+constexpr float kKappaP = 7.2e-7f;  // 12u: kappa plus the rounding of the rearranged test
 constexpr int kTcMaxLen = 256;      // operand tiles of 128 x len halves: 3 tiles must fit in shared memory
 
 __device__ __forceinline__ float tc_coef(int len)
@@ -127,8 +128,8 @@ k_tc_qprep(const QuerySlot *__restrict__ slots, unsigned B, int len, QueryParams
         const float qn = (float)t;
         const float qnorm = __double2float_ru(sqrt(t * (1.0 + 1e-12)));
         const float beta = 5.9604645e-8f * sqrtf((float)len) * 1.002f;
-        const float alpha = (qnorm * (2.f * tc_coef(len) + 2.f * kKappa) + beta) * (1.f + 1e-6f);
-        const float gamma = (beta * qnorm + kKappa * qn) * (1.f + 1e-6f);
+        const float alpha = (qnorm * (2.f * tc_coef(len) + 2.f * kKappaP) + beta) * (1.f + 1e-6f);
+        const float gamma = (beta * qnorm + kKappaP * qn) * (1.f + 1e-6f);
         qconst[4 * b + 0] = qn;
         qconst[4 * b + 1] = alpha;
         qconst[4 * b + 2] = gamma;
@@ -185,14 +186,21 @@ struct ScreenArgs {
     unsigned *status;
 };
 
+// Operand roles: A = the CTA's query tile (M = 128 queries, TMEM lane =
+// query), B = a tile of 128 series (N = 128, TMEM column = series).  A thread
+// owns one query (its constants live in registers) and walks 64 series of
+// each tile.  Per pair the candidate test, rearranged so that only one
+// per-series pair of constants is needed,
+//     lower <= U  <=>  xnorm * alpha + (2 c - xn (1 - kappa'))  >=  qn - gamma' - U
+// costs two FMAs and a compare; a warp vote skips the rare candidate path.
+// The extra 8u in kappa' and gamma' covers the rounding of this form.
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_screen(ScreenArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bar_a[2], bar_m[2], bar_q;
     __shared__ unsigned tmem_base;
-    __shared__ float sU[kTcQ], sAlpha[kTcQ], sGamma[kTcQ], sQn[kTcQ];
-    __shared__ unsigned sAct[kTcQ];
+    __shared__ float2 rowc[kTcRows];        // (-xn (1 - kappa'), xnorm) of the current tile's series
     __shared__ int s_fail;
     const unsigned len = a.len;
     const unsigned tile_bytes = kTcRows * len * 2;
@@ -204,7 +212,6 @@ k_tc_screen(ScreenArgs a)
     const unsigned groups = gridDim.x / QT;                 // CTAs per query tile
     const unsigned qt = blockIdx.x % QT, g = blockIdx.x / QT;
     const unsigned long long RT = (a.N + kTcRows - 1) / kTcRows;
-    // row tiles of this CTA: g, g + groups, ...
     const unsigned long long nt = g < RT ? (RT - g + groups - 1) / groups : 0;
 
     if (warp == 0) tmem_alloc(&tmem_base, 256);
@@ -218,14 +225,16 @@ k_tc_screen(ScreenArgs a)
         fence_barrier_init();
         fence_proxy_async();
     }
-    if (tid < kTcQ) {
-        const unsigned j = qt * kTcQ + tid;
-        sU[tid] = __uint_as_float(a.Ubits[j]);
-        sQn[tid] = a.qconst[4 * j + 0];
-        sAlpha[tid] = a.qconst[4 * j + 1];
-        sGamma[tid] = a.qconst[4 * j + 2];
-        sAct[tid] = a.active[j];
-    }
+    // this thread's query and its constants
+    const unsigned qloc = (unsigned)((warp & 3) * 32 + lane);
+    const unsigned qj = qt * kTcQ + qloc;
+    const float qn = a.qconst[4 * qj + 0];
+    const float alpha = a.qconst[4 * qj + 1];
+    const float gamma = a.qconst[4 * qj + 2];
+    const bool act = a.active[qj] != 0;
+    float U = __uint_as_float(a.Ubits[qj]);
+    float E = act ? qn - gamma - U : __int_as_float(0x7f800000);   // inactive: never a candidate
+    const float one_m_kappa = 1.f - kKappaP;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -243,37 +252,39 @@ k_tc_screen(ScreenArgs a)
         load_tile(0, 0);
         if (nt > 1) load_tile(1, 1);
     }
-    const unsigned idesc = tc_idesc_f16(kTcRows, kTcQ);
+    const unsigned idesc = tc_idesc_f16(kTcQ, kTcRows);
     const unsigned lbo = 128, sbo = (len / 8) * 128;
     const unsigned sA0 = smem_u32(bufA0), sA1 = smem_u32(bufA1), sQ = smem_u32(bufQ);
     auto issue_mma = [&](unsigned long long j) -> bool {
         const int b = (int)(j & 1);
         if (!mbar_wait_bounded(&bar_a[b], (unsigned)((j >> 1) & 1))) return false;
         tc_fence_after();
-        const unsigned sa = b ? sA1 : sA0;
+        const unsigned sx = b ? sA1 : sA0;
         for (unsigned kk = 0; kk < len / 16; ++kk)
-            tc_mma_f16(tmem + b * kTcQ, tc_desc(sa + kk * 256, lbo, sbo), tc_desc(sQ + kk * 256, lbo, sbo), idesc,
+            tc_mma_f16(tmem + b * kTcRows, tc_desc(sQ + kk * 256, lbo, sbo), tc_desc(sx + kk * 256, lbo, sbo), idesc,
                        kk > 0);
         tc_commit(&bar_m[b]);
         return true;
     };
-    bool ok = true;
     if (tid == 0 && nt > 0) {
-        ok = mbar_wait_bounded(&bar_q, 0);
+        bool ok = mbar_wait_bounded(&bar_q, 0);
         if (ok) ok = issue_mma(0);
         if (!ok) s_fail = 1;
     }
     __syncthreads();
 
-    const float coefk = kKappa;
-    const unsigned row_in = (unsigned)((warp & 3) * 32 + lane);   // TMEM lane = tile row
-    const unsigned col0 = (unsigned)(warp >> 2) * 64;             // this warp's 64 query columns
+    const unsigned col0 = (unsigned)(warp >> 2) * 64;       // this warp's 64 series of each tile
     for (unsigned long long j = 0; j < nt && !s_fail; ++j) {
         const int b = (int)(j & 1);
         if (tid == 0 && j + 1 < nt) {
             if (!issue_mma(j + 1)) s_fail = 1;
         }
-        // MMA j done: its A buffer may be refilled, its accumulator read
+        const unsigned long long rt = g + j * groups;
+        if (tid < kTcRows) {
+            const unsigned long long row = rt * kTcRows + tid;
+            const bool rv = row < a.N;
+            rowc[tid] = make_float2(rv ? -a.xn[row] * one_m_kappa : 0.f, rv ? a.xnorm[row] : 0.f);
+        }
         const bool done = mbar_wait_bounded(&bar_m[b], (unsigned)((j >> 1) & 1));
         if (__syncthreads_or(!done) || s_fail) {
             if (tid == 0) s_fail = 1;
@@ -281,33 +292,38 @@ k_tc_screen(ScreenArgs a)
         }
         tc_fence_after();
         if (tid == 0 && j + 2 < nt) load_tile(j + 2, b);
-        const unsigned long long rt = g + j * groups;
-        const unsigned long long row = rt * kTcRows + row_in;
-        const bool rvalid = row < a.N;
-        const float xn = rvalid ? a.xn[row] : 0.f;
-        const float xnorm = rvalid ? a.xnorm[row] : 0.f;
-        const float kxn = coefk * xn;
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             float acc[32];
-            tmem_ld32(tmem + ((unsigned)((warp & 3) * 32) << 16) + b * kTcQ + col0 + half * 32, acc);
-            if (!rvalid) continue;
+            const unsigned cbase = col0 + half * 32;
+            tmem_ld32(tmem + ((unsigned)((warp & 3) * 32) << 16) + b * kTcRows + cbase, acc);
+            bool hit = false;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-                const unsigned c = col0 + half * 32 + i;
-                const float shat = fmaf(-2.f, acc[i], xn + sQn[c]);
-                const float eps = fmaf(xnorm, sAlpha[c], sGamma[c] + kxn);
-                const float U = sU[c];
-                if (shat - eps <= U && sAct[c]) {
-                    const unsigned qj = qt * kTcQ + c;
+                const float2 rc = rowc[cbase + i];
+                const float lhs = fmaf(rc.y, alpha, fmaf(2.f, acc[i], rc.x));
+                hit |= lhs >= E;
+            }
+            if (__any_sync(0xffffffffu, hit)) {
+                for (int i = 0; i < 32; ++i) {
+                    const float2 rc = rowc[cbase + i];
+                    const float lhs = fmaf(rc.y, alpha, fmaf(2.f, acc[i], rc.x));
+                    if (!(lhs >= E)) continue;
+                    const unsigned long long row = rt * kTcRows + cbase + i;
+                    if (row >= a.N) continue;
                     const unsigned o = atomicAdd(&a.cand_count[qj], 1u);
                     if (o < a.cap) a.cand_pos[(unsigned long long)qj * a.cap + o] = (unsigned)row;
-                }
-                if (a.k == 1) {
-                    const float up = fmaxf(shat + eps, 0.f);
-                    if (up < U) {
-                        atomicMin(reinterpret_cast<unsigned *>(&sU[c]), __float_as_uint(up));
-                        atomicMin(&a.Ubits[qt * kTcQ + c], __float_as_uint(up));
+                    if (a.k == 1) {
+                        // upper end of the estimate: s + eps, rounded up
+                        const float xn = a.xn[row];
+                        const float shat = fmaf(-2.f, acc[i], xn + qn);
+                        const float eps = fmaf(rc.y, alpha, gamma + kKappaP * xn);
+                        const float up = fmaxf(__fmul_ru(__fadd_ru(shat, eps), 1.0000003f), 0.f);
+                        if (up < U) {
+                            U = up;
+                            E = qn - gamma - U;
+                            atomicMin(&a.Ubits[qj], __float_as_uint(up));
+                        }
                     }
                 }
             }
@@ -315,13 +331,15 @@ k_tc_screen(ScreenArgs a)
         tc_fence_before();
         __syncthreads();
         // pick up bounds lowered by the other CTAs of this query tile
-        if ((j & 63) == 63 && tid < kTcQ) {
-            const float G = __uint_as_float(a.Ubits[qt * kTcQ + tid]);
-            if (G < sU[tid]) sU[tid] = G;
+        if (act && (j & 63) == 63) {
+            const float G = __uint_as_float(ld_volatile_u32(&a.Ubits[qj]));
+            if (G < U) {
+                U = G;
+                E = qn - gamma - U;
+            }
         }
     }
     if (s_fail && tid == 0) atomicOr(a.status, kStTimeout);
-    // drain: the other accumulator / buffer may still have an MMA or copy in flight
     if (tid == 0 && s_fail) {
         mbar_wait_bounded(&bar_m[0], 0);
         mbar_wait_bounded(&bar_m[1], 0);

@@ -31,10 +31,19 @@ namespace {
 
 constexpr int kTcRows = 128;        // M: series per tile
 constexpr int kTcQ = 128;           // N: queries per tile
-constexpr int kTcThreads = 256;
 constexpr float kKappa = 2.4e-7f;   // 4u: FP32 evaluation of s and rounding of the norms
 constexpr float kKappaP = 7.2e-7f;  // 12u: kappa plus the rounding of the rearranged test
-constexpr int kTcMaxLen = 256;      // operand tiles of 128 x len halves: 3 tiles must fit in shared memory
+constexpr int kTcMaxLen = 256;      // query tiles of 128 x len halves stay resident in shared memory
+constexpr int kTcMaxStages = 16;
+constexpr size_t kTcSmemBudget = 216 * 1024;   // dynamic shared memory of one screen CTA
+
+// K width of one streamed chunk of a series tile: the largest of 64, 32, 16
+// dividing len.  A tile is stored chunk-major: chunk c (k in [c*ck, c*ck+ck))
+// is a 128 x ck operand in the tensor-core layout.
+__host__ __device__ __forceinline__ unsigned chunk_k(unsigned len)
+{
+    return (len % 64 == 0) ? 64u : (len % 32 == 0) ? 32u : 16u;
+}
 
 __device__ __forceinline__ float tc_coef(int len)
 {
@@ -74,7 +83,9 @@ k_make_screen_copy(const float *__restrict__ raw, unsigned long long N, int len,
                 h[i] = __float2half_rn(v[i]);
                 ss = __dadd_rn(ss, __dmul_rn((double)v[i], (double)v[i]));
             }
-            *reinterpret_cast<uint4 *>(tbase + tc_offset(r, (unsigned)k0, (unsigned)len)) = *reinterpret_cast<uint4 *>(h);
+            const unsigned ck = chunk_k(len);
+            *reinterpret_cast<uint4 *>(tbase + (unsigned)(k0 / ck) * (kTcRows * ck * 2) +
+                                       tc_offset(r, (unsigned)(k0 % ck), ck)) = *reinterpret_cast<uint4 *>(h);
         }
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
@@ -179,6 +190,8 @@ struct ScreenArgs {
     unsigned *cand_pos;       // [QT*128][cap]
     const unsigned *active;   // [QT*128]: nonzero when the query collects candidates this pass
     unsigned cap;
+    unsigned qpc;             // query tiles per CTA (1 or 2)
+    unsigned stages;          // chunk stages of the ring
     unsigned long long N;
     unsigned len;
     unsigned QT;
@@ -186,168 +199,226 @@ struct ScreenArgs {
     unsigned *status;
 };
 
-// Operand roles: A = the CTA's query tile (M = 128 queries, TMEM lane =
-// query), B = a tile of 128 series (N = 128, TMEM column = series).  A thread
-// owns one query (its constants live in registers) and walks 64 series of
-// each tile.  Per pair the candidate test, rearranged so that only one
-// per-series pair of constants is needed,
+// Operand roles: A = a query tile (M = 128 queries, TMEM lane = query), B = a
+// tile of 128 series (N = 128, TMEM column = series).  Warp-specialised:
+//   warp 8 (producer)  streams the series tiles as K-chunks through an NS-deep
+//                      ring of shared-memory stages with TMA bulk copies;
+//   warp 9 (MMA)       issues tcgen05 MMAs chunk by chunk (one MMA per query
+//                      tile and 16-wide k step), commits each chunk to free its
+//                      stage and each finished tile to its accumulator buffer;
+//   warps 0-7          read accumulators from TMEM (double-buffered) and test
+//                      every (query, series) pair.
+// A CTA owns QPC (1 or 2) query tiles, so each series tile read from L2 serves
+// QPC * 128 queries.  An epilogue thread owns one query, whose constants stay
+// in registers; the candidate test, rearranged so that only one per-series
+// pair of constants is needed,
 //     lower <= U  <=>  xnorm * alpha + (2 c - xn (1 - kappa'))  >=  qn - gamma' - U
 // costs two FMAs and a compare; a warp vote skips the rare candidate path.
 // The extra 8u in kappa' and gamma' covers the rounding of this form.
-__global__ void __launch_bounds__(kTcThreads, 1)
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcCtrlThreads = kTcEpiWarps * 32 + 64;     // + producer warp + MMA warp
+
+// Named barrier of the 256 epilogue threads that also ORs a predicate over
+// them, so a bounded wait that ran out in one warp stops all of them at once.
+__device__ __forceinline__ bool epi_bar_any(bool v)
+{
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, 256, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)v)
+        : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(kTcCtrlThreads, 1)
 k_tc_screen(ScreenArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long bar_a[2], bar_m[2], bar_q;
+    __shared__ __align__(8) unsigned long long bar_full[kTcMaxStages], bar_empty[kTcMaxStages];
+    __shared__ __align__(8) unsigned long long bar_accf[2], bar_acce[2], bar_q;
     __shared__ unsigned tmem_base;
-    __shared__ float2 rowc[kTcRows];        // (-xn (1 - kappa'), xnorm) of the current tile's series
+    __shared__ float2 rowc[2][kTcRows];     // (-xn (1 - kappa'), xnorm) per accumulator buffer
     __shared__ int s_fail;
     const unsigned len = a.len;
-    const unsigned tile_bytes = kTcRows * len * 2;
-    unsigned char *bufA0 = smem;
-    unsigned char *bufA1 = smem + tile_bytes;
-    unsigned char *bufQ = smem + 2 * tile_bytes;
+    const unsigned ck = chunk_k(len), nch = len / ck;
+    const unsigned chunk_bytes = kTcRows * ck * 2;
+    const unsigned qtile_bytes = kTcQ * len * 2;
+    const unsigned QPC = a.qpc, NS = a.stages;
+    unsigned char *qbuf = smem;                               // QPC query tiles
+    unsigned char *ring = smem + QPC * qtile_bytes;           // NS chunk stages
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned QT = a.QT;
-    const unsigned groups = gridDim.x / QT;                 // CTAs per query tile
-    const unsigned qt = blockIdx.x % QT, g = blockIdx.x / QT;
+    const unsigned QG = (a.QT + QPC - 1) / QPC;               // query-tile groups
+    const unsigned groups = gridDim.x / QG;                   // CTAs per query-tile group
+    const unsigned qg = blockIdx.x % QG, g = blockIdx.x / QG;
+    const unsigned qt0 = qg * QPC;
+    const unsigned nq = min(QPC, a.QT - qt0);                 // query tiles of this CTA
     const unsigned long long RT = (a.N + kTcRows - 1) / kTcRows;
     const unsigned long long nt = g < RT ? (RT - g + groups - 1) / groups : 0;
 
-    if (warp == 0) tmem_alloc(&tmem_base, 256);
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
     if (tid == 0) {
         s_fail = 0;
-        mbar_init(&bar_a[0], 1);
-        mbar_init(&bar_a[1], 1);
-        mbar_init(&bar_m[0], 1);
-        mbar_init(&bar_m[1], 1);
+        for (unsigned i = 0; i < NS; ++i) {
+            mbar_init(&bar_full[i], 1);
+            mbar_init(&bar_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar_accf[i], 1);
+            mbar_init(&bar_acce[i], kTcEpiWarps);
+        }
         mbar_init(&bar_q, 1);
         fence_barrier_init();
         fence_proxy_async();
     }
-    // this thread's query and its constants
-    const unsigned qloc = (unsigned)((warp & 3) * 32 + lane);
-    const unsigned qj = qt * kTcQ + qloc;
-    const float qn = a.qconst[4 * qj + 0];
-    const float alpha = a.qconst[4 * qj + 1];
-    const float gamma = a.qconst[4 * qj + 2];
-    const bool act = a.active[qj] != 0;
-    float U = __uint_as_float(a.Ubits[qj]);
-    float E = act ? qn - gamma - U : __int_as_float(0x7f800000);   // inactive: never a candidate
-    const float one_m_kappa = 1.f - kKappaP;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = tmem_base;
-    auto load_tile = [&](unsigned long long j, int b) {
-        const unsigned long long rt = g + j * groups;
-        mbar_arrive_expect_tx(&bar_a[b], tile_bytes);
-        bulk_g2s(b ? bufA1 : bufA0, reinterpret_cast<const unsigned char *>(a.rtiles) + rt * tile_bytes, tile_bytes,
-                 &bar_a[b]);
-    };
-    if (tid == 0 && nt > 0) {
-        mbar_arrive_expect_tx(&bar_q, tile_bytes);
-        bulk_g2s(bufQ, reinterpret_cast<const unsigned char *>(a.qtiles) + (unsigned long long)qt * tile_bytes,
-                 tile_bytes, &bar_q);
-        load_tile(0, 0);
-        if (nt > 1) load_tile(1, 1);
-    }
-    const unsigned idesc = tc_idesc_f16(kTcQ, kTcRows);
-    const unsigned lbo = 128, sbo = (len / 8) * 128;
-    const unsigned sA0 = smem_u32(bufA0), sA1 = smem_u32(bufA1), sQ = smem_u32(bufQ);
-    auto issue_mma = [&](unsigned long long j) -> bool {
-        const int b = (int)(j & 1);
-        if (!mbar_wait_bounded(&bar_a[b], (unsigned)((j >> 1) & 1))) return false;
-        tc_fence_after();
-        const unsigned sx = b ? sA1 : sA0;
-        for (unsigned kk = 0; kk < len / 16; ++kk)
-            tc_mma_f16(tmem + b * kTcRows, tc_desc(sQ + kk * 256, lbo, sbo), tc_desc(sx + kk * 256, lbo, sbo), idesc,
-                       kk > 0);
-        tc_commit(&bar_m[b]);
-        return true;
-    };
-    if (tid == 0 && nt > 0) {
-        bool ok = mbar_wait_bounded(&bar_q, 0);
-        if (ok) ok = issue_mma(0);
-        if (!ok) s_fail = 1;
-    }
-    __syncthreads();
+    const unsigned acc_cols = QPC * 128;                      // columns of one accumulator buffer
 
-    const unsigned col0 = (unsigned)(warp >> 2) * 64;       // this warp's 64 series of each tile
-    for (unsigned long long j = 0; j < nt && !s_fail; ++j) {
-        const int b = (int)(j & 1);
-        if (tid == 0 && j + 1 < nt) {
-            if (!issue_mma(j + 1)) s_fail = 1;
-        }
-        const unsigned long long rt = g + j * groups;
-        if (tid < kTcRows) {
-            const unsigned long long row = rt * kTcRows + tid;
-            const bool rv = row < a.N;
-            rowc[tid] = make_float2(rv ? -a.xn[row] * one_m_kappa : 0.f, rv ? a.xnorm[row] : 0.f);
-        }
-        const bool done = mbar_wait_bounded(&bar_m[b], (unsigned)((j >> 1) & 1));
-        if (__syncthreads_or(!done) || s_fail) {
-            if (tid == 0) s_fail = 1;
-            break;
-        }
-        tc_fence_after();
-        if (tid == 0 && j + 2 < nt) load_tile(j + 2, b);
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            float acc[32];
-            const unsigned cbase = col0 + half * 32;
-            tmem_ld32(tmem + ((unsigned)((warp & 3) * 32) << 16) + b * kTcRows + cbase, acc);
-            bool hit = false;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const float2 rc = rowc[cbase + i];
-                const float lhs = fmaf(rc.y, alpha, fmaf(2.f, acc[i], rc.x));
-                hit |= lhs >= E;
+    if (warp == kTcEpiWarps) {
+        // ------------------------------------------------ producer
+        if (lane == 0 && nt > 0) {
+            mbar_arrive_expect_tx(&bar_q, nq * qtile_bytes);
+            for (unsigned qi = 0; qi < nq; ++qi)
+                bulk_g2s(qbuf + qi * qtile_bytes,
+                         reinterpret_cast<const unsigned char *>(a.qtiles) + (unsigned long long)(qt0 + qi) * qtile_bytes,
+                         qtile_bytes, &bar_q);
+            const unsigned long long total = nt * nch;
+            for (unsigned long long n = 0; n < total && !s_fail; ++n) {
+                const unsigned st = (unsigned)(n % NS);
+                const unsigned long long use = n / NS;
+                if (use > 0 && !mbar_wait_bounded(&bar_empty[st], (unsigned)((use - 1) & 1))) {
+                    s_fail = 1;
+                    break;
+                }
+                const unsigned long long j = n / nch, c = n % nch;
+                const unsigned long long rt = g + j * groups;
+                mbar_arrive_expect_tx(&bar_full[st], chunk_bytes);
+                bulk_g2s(ring + st * chunk_bytes,
+                         reinterpret_cast<const unsigned char *>(a.rtiles) + (rt * nch + c) * chunk_bytes, chunk_bytes,
+                         &bar_full[st]);
             }
-            if (__any_sync(0xffffffffu, hit)) {
+        }
+    } else if (warp == kTcEpiWarps + 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0 && nt > 0) {
+            const unsigned idesc = tc_idesc_f16(kTcQ, kTcRows);
+            const unsigned sq = smem_u32(qbuf), sr = smem_u32(ring);
+            const unsigned sbo_q = (len / 8) * 128, sbo_r = (ck / 8) * 128;
+            bool ok = mbar_wait_bounded(&bar_q, 0);
+            for (unsigned long long j = 0; j < nt && ok && !s_fail; ++j) {
+                const unsigned ab = (unsigned)(j & 1);
+                if (j >= 2 && !mbar_wait_bounded(&bar_acce[ab], (unsigned)(((j >> 1) - 1) & 1))) { ok = false; break; }
+                tc_fence_after();
+                for (unsigned c = 0; c < nch; ++c) {
+                    const unsigned long long n = j * nch + c;
+                    const unsigned st = (unsigned)(n % NS);
+                    if (!mbar_wait_bounded(&bar_full[st], (unsigned)((n / NS) & 1))) { ok = false; break; }
+                    tc_fence_after();
+                    for (unsigned kk = 0; kk < ck / 16; ++kk) {
+                        const unsigned long long bdesc = tc_desc(sr + st * chunk_bytes + kk * 256, 128, sbo_r);
+                        for (unsigned qi = 0; qi < nq; ++qi)
+                            tc_mma_f16(tmem + ab * acc_cols + qi * 128,
+                                       tc_desc(sq + qi * qtile_bytes + (c * (ck / 16) + kk) * 256, 128, sbo_q), bdesc,
+                                       idesc, (c | kk) != 0);
+                    }
+                    tc_commit(&bar_empty[st]);
+                }
+                if (!ok) break;
+                tc_commit(&bar_accf[ab]);
+            }
+            if (!ok) s_fail = 1;
+        }
+    } else {
+        // ------------------------------------------------ epilogue
+        const unsigned qi = (QPC == 2) ? (unsigned)(warp >> 2) : 0u;
+        const unsigned qloc = (unsigned)((warp & 3) * 32 + lane);
+        const unsigned qj = (qt0 + qi) * kTcQ + qloc;
+        const bool have = qt0 + qi < a.QT;
+        const float qn = have ? a.qconst[4 * qj + 0] : 0.f;
+        const float alpha = have ? a.qconst[4 * qj + 1] : 0.f;
+        const float gamma = have ? a.qconst[4 * qj + 2] : 0.f;
+        const bool act = have && a.active[qj] != 0;
+        float U = have ? __uint_as_float(a.Ubits[qj]) : -1.f;
+        float E = act ? qn - gamma - U : __int_as_float(0x7f800000);
+        const float one_m_kappa = 1.f - kKappaP;
+        // columns of this warp in an accumulator buffer: QPC = 2: all 128 series of
+        // its query tile; QPC = 1: half of them
+        const unsigned cbeg = (QPC == 2) ? qi * 128 : (unsigned)(warp >> 2) * 64;
+        const unsigned ncol = (QPC == 2) ? 128u : 64u;
+        const unsigned rbeg = (QPC == 2) ? 0u : (unsigned)(warp >> 2) * 64;   // first series of the tile
+        for (unsigned long long j = 0; j < nt; ++j) {
+            const unsigned ab = (unsigned)(j & 1);
+            const unsigned long long rt = g + j * groups;
+            if (tid < kTcRows) {
+                const unsigned long long row = rt * kTcRows + tid;
+                const bool rv = row < a.N;
+                rowc[ab][tid] = make_float2(rv ? -a.xn[row] * one_m_kappa : 0.f, rv ? a.xnorm[row] : 0.f);
+            }
+            const bool okw = mbar_wait_bounded(&bar_accf[ab], (unsigned)((j >> 1) & 1));
+            // also the barrier that publishes rowc to all epilogue warps
+            if (epi_bar_any(!okw)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            for (unsigned h = 0; h < ncol; h += 32) {
+                float acc[32];
+                tmem_ld32(tmem + ((unsigned)((warp & 3) * 32) << 16) + ab * acc_cols + cbeg + h, acc);
+                bool hit = false;
+#pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    const float2 rc = rowc[cbase + i];
+                    const float2 rc = rowc[ab][rbeg + h + i];
                     const float lhs = fmaf(rc.y, alpha, fmaf(2.f, acc[i], rc.x));
-                    if (!(lhs >= E)) continue;
-                    const unsigned long long row = rt * kTcRows + cbase + i;
-                    if (row >= a.N) continue;
-                    const unsigned o = atomicAdd(&a.cand_count[qj], 1u);
-                    if (o < a.cap) a.cand_pos[(unsigned long long)qj * a.cap + o] = (unsigned)row;
-                    if (a.k == 1) {
-                        // upper end of the estimate: s + eps, rounded up
-                        const float xn = a.xn[row];
-                        const float shat = fmaf(-2.f, acc[i], xn + qn);
-                        const float eps = fmaf(rc.y, alpha, gamma + kKappaP * xn);
-                        const float up = fmaxf(__fmul_ru(__fadd_ru(shat, eps), 1.0000003f), 0.f);
-                        if (up < U) {
-                            U = up;
-                            E = qn - gamma - U;
-                            atomicMin(&a.Ubits[qj], __float_as_uint(up));
+                    hit |= lhs >= E;
+                }
+                if (__any_sync(0xffffffffu, hit)) {
+                    for (int i = 0; i < 32; ++i) {
+                        const float2 rc = rowc[ab][rbeg + h + i];
+                        const float lhs = fmaf(rc.y, alpha, fmaf(2.f, acc[i], rc.x));
+                        if (!(lhs >= E)) continue;
+                        const unsigned long long row = rt * kTcRows + rbeg + h + i;
+                        if (row >= a.N) continue;
+                        const unsigned o = atomicAdd(&a.cand_count[qj], 1u);
+                        if (o < a.cap) a.cand_pos[(unsigned long long)qj * a.cap + o] = (unsigned)row;
+                        if (a.k == 1) {
+                            // upper end of the estimate: s + eps, rounded up
+                            const float xn = a.xn[row];
+                            const float shat = fmaf(-2.f, acc[i], xn + qn);
+                            const float eps = fmaf(rc.y, alpha, gamma + kKappaP * xn);
+                            const float up = fmaxf(__fmul_ru(__fadd_ru(shat, eps), 1.0000003f), 0.f);
+                            if (up < U) {
+                                U = up;
+                                E = qn - gamma - U;
+                                atomicMin(&a.Ubits[qj], __float_as_uint(up));
+                            }
                         }
                     }
                 }
             }
-        }
-        tc_fence_before();
-        __syncthreads();
-        // pick up bounds lowered by the other CTAs of this query tile
-        if (act && (j & 63) == 63) {
-            const float G = __uint_as_float(ld_volatile_u32(&a.Ubits[qj]));
-            if (G < U) {
-                U = G;
-                E = qn - gamma - U;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_acce[ab]);
+            // pick up bounds lowered by the other CTAs of these query tiles
+            if (act && (j & 63) == 63) {
+                const float G = __uint_as_float(ld_volatile_u32(&a.Ubits[qj]));
+                if (G < U) {
+                    U = G;
+                    E = qn - gamma - U;
+                }
             }
         }
-    }
-    if (s_fail && tid == 0) atomicOr(a.status, kStTimeout);
-    if (tid == 0 && s_fail) {
-        mbar_wait_bounded(&bar_m[0], 0);
-        mbar_wait_bounded(&bar_m[1], 0);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (s_fail && tid == 0) atomicOr(a.status, kStTimeout);
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // ----------------------------------------------------------- recheck
@@ -445,11 +516,27 @@ k_tc_gemm_test(const __half *A, const __half *Bm, float *D, unsigned K, unsigned
 // At least 120 KB so that a single screen CTA fits on an SM: each CTA holds
 // 256 TMEM columns for its whole (persistent) life, and a second or third
 // resident CTA would wait in tcgen05.alloc for columns that never free up.
-size_t screen_smem_bytes(int len) { return std::max<size_t>(3ull * kTcRows * len * 2, 120ull * 1024); }
+// Shared memory is always the full budget (kTcSmemBudget): one screen CTA per
+// SM, because each CTA holds all 512 TMEM columns for its whole (persistent)
+// life and a second resident CTA would wait in tcgen05.alloc forever.
+size_t screen_smem_bytes(int len)
+{
+    (void)len;
+    return kTcSmemBudget;
+}
+
+// ring stages that fit next to `qpc` resident query tiles
+unsigned screen_stages(int len, unsigned qpc)
+{
+    const size_t chunk = (size_t)kTcRows * chunk_k((unsigned)len) * 2;
+    const size_t q = (size_t)qpc * kTcQ * len * 2;
+    const size_t left = kTcSmemBudget > q ? kTcSmemBudget - q : 0;
+    return (unsigned)std::min<size_t>(kTcMaxStages, left / chunk);
+}
 
 void init_screen_attributes()
 {
-    cudaFuncSetAttribute(k_tc_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)screen_smem_bytes(kTcMaxLen));
+    cudaFuncSetAttribute(k_tc_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBudget);
 }
 
 void launch_make_screen_copy(const float *raw, unsigned long long N, int len, __half *tiles, float *xn, float *xnorm,
@@ -497,8 +584,11 @@ void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm,
     a.QT = (B + kTcQ - 1) / kTcQ;
     a.k = k;
     a.status = status;
-    const unsigned groups = std::max(1u, (unsigned)num_sms() / a.QT);
-    k_tc_screen<<<groups * a.QT, kTcThreads, screen_smem_bytes(len), s>>>(a);
+    a.qpc = (a.QT >= 2 && screen_stages(len, 2) >= 4) ? 2u : 1u;
+    a.stages = screen_stages(len, a.qpc);
+    const unsigned QG = (a.QT + a.qpc - 1) / a.qpc;
+    const unsigned groups = std::max(1u, (unsigned)num_sms() / QG);
+    k_tc_screen<<<groups * QG, kTcCtrlThreads, screen_smem_bytes(len), s>>>(a);
 }
 
 void launch_tc_recheck(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots, unsigned B,

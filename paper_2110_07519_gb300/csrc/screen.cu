@@ -352,14 +352,20 @@ k_tc_screen(ScreenArgs a)
         const unsigned cbeg = (QPC == 2) ? qi * 128 : (unsigned)(warp >> 2) * 64;
         const unsigned ncol = (QPC == 2) ? 128u : 64u;
         const unsigned rbeg = (QPC == 2) ? 0u : (unsigned)(warp >> 2) * 64;   // first series of the tile
+        // series norms of the next tile are fetched one tile ahead
+        float nxt_xn = 0.f, nxt_nrm = 0.f;
+        auto fetch_norms = [&](unsigned long long j) {
+            const unsigned long long row = (g + j * groups) * kTcRows + tid;
+            const bool rv = tid < kTcRows && j < nt && row < a.N;
+            nxt_xn = rv ? a.xn[row] : 0.f;
+            nxt_nrm = rv ? a.xnorm[row] : 0.f;
+        };
+        fetch_norms(0);
         for (unsigned long long j = 0; j < nt; ++j) {
             const unsigned ab = (unsigned)(j & 1);
             const unsigned long long rt = g + j * groups;
-            if (tid < kTcRows) {
-                const unsigned long long row = rt * kTcRows + tid;
-                const bool rv = row < a.N;
-                rowc[ab][tid] = make_float2(rv ? -a.xn[row] * one_m_kappa : 0.f, rv ? a.xnorm[row] : 0.f);
-            }
+            if (tid < kTcRows) rowc[ab][tid] = make_float2(-nxt_xn * one_m_kappa, nxt_nrm);
+            fetch_norms(j + 1);
             const bool okw = mbar_wait_bounded(&bar_accf[ab], (unsigned)((j >> 1) & 1));
             // also the barrier that publishes rowc to all epilogue warps
             if (epi_bar_any(!okw)) {

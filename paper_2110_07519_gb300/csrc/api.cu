@@ -43,24 +43,24 @@ void ensure_attributes()
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Growable device buffer owned by the index (host staging of inputs/outputs).
-bool ensure_stage(messi_index *ix, size_t bytes)
+bool ensure_stage(Workspace *ws, size_t bytes)
 {
-    if (ix->stage_bytes >= bytes) return true;
-    if (ix->stage_block) cudaFree(ix->stage_block);
-    ix->stage_block = nullptr;
-    ix->stage_bytes = 0;
-    if (cudaMalloc(&ix->stage_block, bytes) != cudaSuccess) {
+    if (ws->stage_bytes >= bytes) return true;
+    if (ws->stage_block) cudaFree(ws->stage_block);
+    ws->stage_block = nullptr;
+    ws->stage_bytes = 0;
+    if (cudaMalloc(&ws->stage_block, bytes) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    ix->stage_bytes = bytes;
+    ws->stage_bytes = bytes;
     return true;
 }
 
 // Plain-path workspace: one query slot with survivor arrays of N entries.
-messi_status ensure_workspace(messi_index *ix)
+messi_status ensure_workspace(messi_index *ix, Workspace *ws)
 {
-    if (ix->ws_block) return MESSI_OK;
+    if (ws->ws_block) return MESSI_OK;
     const size_t N = ix->N, len = ix->len;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -81,10 +81,10 @@ messi_status ensure_workspace(messi_index *ix)
         cudaGetLastError();
         return fail(MESSI_ENOMEM, "messi_query: cannot allocate the query workspace");
     }
-    ix->ws_block = base;
-    ix->ws_bytes = off;
+    ws->ws_block = base;
+    ws->ws_bytes = off;
     ix->device_bytes += off;
-    QuerySlot &s = ix->slot;
+    QuerySlot &s = ws->slot;
     s.st = reinterpret_cast<QueryState *>(base + o_st);
     s.lut = reinterpret_cast<float *>(base + o_lut);
     s.q = reinterpret_cast<float *>(base + o_q);
@@ -105,14 +105,14 @@ messi_status ensure_workspace(messi_index *ix)
 // Batched workspace: B query slots (no survivor arrays: the fused kernel keeps
 // survivors in shared memory), their device-side descriptor array, the work
 // counter and the call's counter accumulator.
-messi_status ensure_batch_workspace(messi_index *ix, unsigned B)
+messi_status ensure_batch_workspace(messi_index *ix, Workspace *ws, unsigned B)
 {
-    if (ix->bws_block && (unsigned)ix->bws_slots >= B) return MESSI_OK;
-    if (ix->bws_block) {
-        cudaFree(ix->bws_block);
-        ix->device_bytes -= ix->bws_bytes;
-        ix->bws_block = nullptr;
-        ix->bws_slots = 0;
+    if (ws->bws_block && (unsigned)ws->bws_slots >= B) return MESSI_OK;
+    if (ws->bws_block) {
+        cudaFree(ws->bws_block);
+        ix->device_bytes -= ws->bws_bytes;
+        ws->bws_block = nullptr;
+        ws->bws_slots = 0;
     }
     const size_t len = ix->len;
     const size_t per = align256(sizeof(QueryState)) + align256(kMaxSegments * kMaxCard * 4) + 3 * align256(len * 4) +
@@ -123,13 +123,13 @@ messi_status ensure_batch_workspace(messi_index *ix, unsigned B)
         cudaGetLastError();
         return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate the batch workspace");
     }
-    ix->bws_block = base;
-    ix->bws_bytes = head + per * B;
-    ix->bws_slots = (int)B;
-    ix->device_bytes += ix->bws_bytes;
-    ix->bslots_dev = reinterpret_cast<QuerySlot *>(base);
-    ix->bcounter = reinterpret_cast<unsigned *>(base + align256(B * sizeof(QuerySlot)));
-    ix->bacc = reinterpret_cast<QueryCounters *>(base + align256(B * sizeof(QuerySlot)) + align256(64));
+    ws->bws_block = base;
+    ws->bws_bytes = head + per * B;
+    ws->bws_slots = (int)B;
+    ix->device_bytes += ws->bws_bytes;
+    ws->bslots_dev = reinterpret_cast<QuerySlot *>(base);
+    ws->bcounter = reinterpret_cast<unsigned *>(base + align256(B * sizeof(QuerySlot)));
+    ws->bacc = reinterpret_cast<QueryCounters *>(base + align256(B * sizeof(QuerySlot)) + align256(64));
     std::vector<QuerySlot> host(B);
     char *p = base + head;
     for (unsigned b = 0; b < B; ++b) {
@@ -143,9 +143,9 @@ messi_status ensure_batch_workspace(messi_index *ix, unsigned B)
         q.karr = reinterpret_cast<unsigned long long *>(p); p += align256(kMaxK * 8);
         q.log = reinterpret_cast<unsigned long long *>(p); p += align256(kLogCap * 8);
         q.seedbuf = reinterpret_cast<unsigned long long *>(p); p += align256(kSeedMax * 8);
-        q.acc = ix->bacc;
+        q.acc = ws->bacc;
     }
-    if (!cuda_ok(cudaMemcpy(ix->bslots_dev, host.data(), B * sizeof(QuerySlot), cudaMemcpyHostToDevice),
+    if (!cuda_ok(cudaMemcpy(ws->bslots_dev, host.data(), B * sizeof(QuerySlot), cudaMemcpyHostToDevice),
                  "messi_query_batched: slot table upload"))
         return MESSI_ECUDA;
     return MESSI_OK;
@@ -194,10 +194,10 @@ struct TcWs {
     unsigned *Ubits, *cand_count, *flags, *active, *cand_pos, *n_active;
 };
 
-TcWs tc_ws_view(messi_index *ix)
+TcWs tc_ws_view(messi_index *ix, Workspace *ws)
 {
-    const unsigned P = (ix->tcws_B + 127) / 128 * 128;
-    char *p = static_cast<char *>(ix->tcws_block);
+    const unsigned P = (ws->tcws_B + 127) / 128 * 128;
+    char *p = static_cast<char *>(ws->tcws_block);
     TcWs w;
     w.qtiles = reinterpret_cast<__half *>(p); p += align256((size_t)P * ix->len * 2);
     w.qconst = reinterpret_cast<float *>(p); p += align256((size_t)P * 16);
@@ -210,23 +210,23 @@ TcWs tc_ws_view(messi_index *ix)
     return w;
 }
 
-messi_status ensure_tc_workspace(messi_index *ix, unsigned B)
+messi_status ensure_tc_workspace(messi_index *ix, Workspace *ws, unsigned B)
 {
-    if (ix->tcws_block && ix->tcws_B >= B) return MESSI_OK;
-    if (ix->tcws_block) {
-        cudaFree(ix->tcws_block);
-        ix->device_bytes -= ix->tcws_bytes;
-        ix->tcws_block = nullptr;
+    if (ws->tcws_block && ws->tcws_B >= B) return MESSI_OK;
+    if (ws->tcws_block) {
+        cudaFree(ws->tcws_block);
+        ix->device_bytes -= ws->tcws_bytes;
+        ws->tcws_block = nullptr;
     }
     const size_t P = (B + 127) / 128 * 128;
     const size_t bytes = align256(P * ix->len * 2) + align256(P * 16) + 4 * align256(P * 4) + 256 + P * kTcCap * 4;
-    if (cudaMalloc(&ix->tcws_block, bytes) != cudaSuccess) {
+    if (cudaMalloc(&ws->tcws_block, bytes) != cudaSuccess) {
         cudaGetLastError();
-        ix->tcws_block = nullptr;
+        ws->tcws_block = nullptr;
         return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate the screening workspace");
     }
-    ix->tcws_bytes = bytes;
-    ix->tcws_B = B;
+    ws->tcws_bytes = bytes;
+    ws->tcws_B = B;
     ix->device_bytes += bytes;
     return MESSI_OK;
 }
@@ -252,14 +252,14 @@ IndexView view_of(const messi_index *ix)
     return v;
 }
 
-cudaEvent_t pool_event(messi_index *ix, size_t i)
+cudaEvent_t pool_event(Workspace *ws, size_t i)
 {
-    while (ix->ev_pool.size() <= i) {
+    while (ws->ev_pool.size() <= i) {
         cudaEvent_t e;
         cudaEventCreate(&e);
-        ix->ev_pool.push_back(e);
+        ws->ev_pool.push_back(e);
     }
-    return ix->ev_pool[i];
+    return ws->ev_pool[i];
 }
 
 messi_status check_sizes(uint64_t n, uint32_t len, uint32_t segments, uint32_t card)
@@ -292,6 +292,15 @@ bool cuda_ok(cudaError_t e, const char *what)
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     cudaGetLastError();
     return false;
+}
+
+void free_workspace(Workspace &w)
+{
+    void *ptrs[] = {w.ws_block, w.stage_block, w.bws_block, w.tcws_block};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : w.ev_pool) cudaEventDestroy(e);
+    w = Workspace{};
 }
 
 int num_sms()
@@ -374,13 +383,11 @@ messi_status messi_breakpoints(uint32_t cardinality, double *out)
 void messi_free(messi_index *ix)
 {
     if (!ix) return;
-    void *ptrs[] = {ix->raw,    ix->sax,      ix->ids,         ix->pos_of_id, ix->leaf_off,
-                    ix->leaf_key, ix->leaf_depth, ix->beta64,   ix->status,    ix->ws_block,
-                    ix->stage_block, ix->bws_block, ix->screen16, ix->tcws_block};
+    void *ptrs[] = {ix->raw,      ix->sax,        ix->ids,    ix->pos_of_id, ix->leaf_off,
+                    ix->leaf_key, ix->leaf_depth, ix->beta64, ix->status,    ix->screen16};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    for (cudaEvent_t e : ix->ev_pool) cudaEventDestroy(e);
-    if (ix->counters_host) cudaFreeHost(ix->counters_host);
+    free_workspace(ix->ws);
     delete ix;
 }
 
@@ -510,7 +517,7 @@ messi_status messi_build(const float *series, uint64_t n, uint32_t len, uint32_t
         messi_free(ix);
         return fail(MESSI_EINVAL, "messi_build: the series hold a non-finite value");
     }
-    ix->last_stream = s;
+    ix->ws.last_stream = s;
     *out = ix;
     return MESSI_OK;
 }
@@ -526,21 +533,20 @@ static messi_status query_args(const messi_index *ix, const float *queries, uint
     return MESSI_OK;
 }
 
-messi_status messi_query(const messi_index *cix, const float *queries, uint32_t nq, uint32_t k,
-                         messi_dist dist, uint32_t window, int64_t *ids, float *dists, messi_stream stream)
+messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uint32_t nq, uint32_t k,
+                       messi_dist dist, uint32_t window, int64_t *ids, float *dists, messi_stream stream)
 {
-    messi_status chk = query_args(cix, queries, nq, k, dist, window, ids, dists);
+    messi_status chk = query_args(ix, queries, nq, k, dist, window, ids, dists);
     if (chk != MESSI_OK) return chk;
-    messi_index *ix = const_cast<messi_index *>(cix);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ensure_attributes();
-    if ((chk = ensure_workspace(ix)) != MESSI_OK) return chk;
+    if ((chk = ensure_workspace(ix, ws)) != MESSI_OK) return chk;
 
     const bool hq = !is_device_ptr(queries), hi = !is_device_ptr(ids), hd = !is_device_ptr(dists);
     const size_t qbytes = (size_t)nq * ix->len * 4, ibytes = (size_t)nq * k * 8, dbytes = (size_t)nq * k * 4;
     const size_t need = (hq ? align256(qbytes) : 0) + (hi ? align256(ibytes) : 0) + (hd ? align256(dbytes) : 0);
-    if (need && !ensure_stage(ix, need)) return fail(MESSI_ENOMEM, "messi_query: cannot allocate staging buffers");
-    char *stage = static_cast<char *>(ix->stage_block);
+    if (need && !ensure_stage(ws, need)) return fail(MESSI_ENOMEM, "messi_query: cannot allocate staging buffers");
+    char *stage = static_cast<char *>(ws->stage_block);
     const float *dq = queries;
     long long *did = reinterpret_cast<long long *>(ids);
     float *ddist = dists;
@@ -559,68 +565,67 @@ messi_status messi_query(const messi_index *cix, const float *queries, uint32_t 
     qp.dist = (int)dist;
     qp.r = dist == MESSI_DTW ? (int)window : 0;
     qp.F = band_factor(qp.dist, ix->len);
-    const QuerySlot slot = ix->slot;
+    const QuerySlot slot = ws->slot;
     MESSI_CUDA(cudaMemsetAsync(slot.acc, 0, sizeof(QueryCounters), s));
-    const unsigned long long launches0 = ix->launches;
-    ix->scan_ev.clear();
-    ix->query_ev.clear();
+    const unsigned long long launches0 = ws->launches;
+    ws->scan_ev.clear();
+    ws->query_ev.clear();
     size_t evn = 0;
     for (uint32_t qi = 0; qi < nq; ++qi) {
         int eq0 = -1, es0 = -1;
         if (ix->profiling) {
             eq0 = (int)evn;
-            cudaEventRecord(pool_event(ix, evn++), s);
+            cudaEventRecord(pool_event(ws, evn++), s);
         }
         launch_prep(iv, qp, slot, dq + (size_t)qi * ix->len, s);
-        launch_seed(iv, qp, slot, s, &ix->launches);
+        launch_seed(iv, qp, slot, s, &ws->launches);
         if (ix->profiling) {
             es0 = (int)evn;
-            cudaEventRecord(pool_event(ix, evn++), s);
+            cudaEventRecord(pool_event(ws, evn++), s);
         }
         launch_scan(iv, qp, slot, s);
         if (ix->profiling) {
-            cudaEventRecord(pool_event(ix, evn++), s);
-            ix->scan_ev.push_back({es0, es0 + 1});
+            cudaEventRecord(pool_event(ws, evn++), s);
+            ws->scan_ev.push_back({es0, es0 + 1});
         }
-        launch_refine(iv, qp, slot, s, &ix->launches);
+        launch_refine(iv, qp, slot, s, &ws->launches);
         launch_finalize(iv, qp, slot, did + (size_t)qi * k, ddist + (size_t)qi * k, s);
-        ix->launches += 3;
+        ws->launches += 3;
         if (ix->profiling) {
-            cudaEventRecord(pool_event(ix, evn++), s);
-            ix->query_ev.push_back({eq0, (int)evn - 1});
+            cudaEventRecord(pool_event(ws, evn++), s);
+            ws->query_ev.push_back({eq0, (int)evn - 1});
         }
     }
     MESSI_CUDA(cudaGetLastError());
-    ix->last = messi_stats{};
-    ix->last.queries = nq;
-    ix->last.kernel_launches = ix->launches - launches0;
-    ix->last_stream = s;
-    ix->last_batched = false;
+    ws->last = messi_stats{};
+    ws->last.queries = nq;
+    ws->last.kernel_launches = ws->launches - launches0;
+    ws->last_stream = s;
+    ws->last_batched = false;
     if (hi) MESSI_CUDA(cudaMemcpyAsync(ids, did, ibytes, cudaMemcpyDeviceToHost, s));
     if (hd) MESSI_CUDA(cudaMemcpyAsync(dists, ddist, dbytes, cudaMemcpyDeviceToHost, s));
     if (hq || hi || hd) MESSI_CUDA(cudaStreamSynchronize(s));
     return MESSI_OK;
 }
 
-messi_status messi_query_batched(const messi_index *cix, const float *queries, uint32_t nq, uint32_t k,
-                                 messi_dist dist, uint32_t window, uint32_t batch, int64_t *ids, float *dists,
-                                 messi_stream stream)
+messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, uint32_t nq, uint32_t k,
+                         messi_dist dist, uint32_t window, uint32_t batch, int64_t *ids, float *dists,
+                         messi_stream stream)
 {
-    messi_status chk = query_args(cix, queries, nq, k, dist, window, ids, dists);
+    messi_status chk = query_args(ix, queries, nq, k, dist, window, ids, dists);
     if (chk != MESSI_OK) return chk;
     // DTW queries take the per-query kernels (the fused batch kernel is ED)
-    if (dist == MESSI_DTW) return messi_query(cix, queries, nq, k, dist, window, ids, dists, stream);
-    messi_index *ix = const_cast<messi_index *>(cix);
+    if (dist == MESSI_DTW) return run_plain(ix, ws, queries, nq, k, dist, window, ids, dists, stream);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ensure_attributes();
     const unsigned B = std::min<unsigned>(batch ? batch : ix->tune_batch, nq);
-    if ((chk = ensure_batch_workspace(ix, B)) != MESSI_OK) return chk;
+    if ((chk = ensure_batch_workspace(ix, ws, B)) != MESSI_OK) return chk;
 
     const bool hq = !is_device_ptr(queries), hi = !is_device_ptr(ids), hd = !is_device_ptr(dists);
     const size_t qbytes = (size_t)nq * ix->len * 4, ibytes = (size_t)nq * k * 8, dbytes = (size_t)nq * k * 4;
     const size_t need = (hq ? align256(qbytes) : 0) + (hi ? align256(ibytes) : 0) + (hd ? align256(dbytes) : 0);
-    if (need && !ensure_stage(ix, need)) return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate staging buffers");
-    char *stage = static_cast<char *>(ix->stage_block);
+    if (need && !ensure_stage(ws, need)) return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate staging buffers");
+    char *stage = static_cast<char *>(ws->stage_block);
     const float *dq = queries;
     long long *did = reinterpret_cast<long long *>(ids);
     float *ddist = dists;
@@ -639,47 +644,47 @@ messi_status messi_query_batched(const messi_index *cix, const float *queries, u
     qp.dist = 0;
     qp.r = 0;
     qp.F = band_factor(0, ix->len);
-    MESSI_CUDA(cudaMemsetAsync(ix->bacc, 0, sizeof(QueryCounters), s));
-    const unsigned long long launches0 = ix->launches;
-    ix->scan_ev.clear();
-    ix->query_ev.clear();
+    MESSI_CUDA(cudaMemsetAsync(ws->bacc, 0, sizeof(QueryCounters), s));
+    const unsigned long long launches0 = ws->launches;
+    ws->scan_ev.clear();
+    ws->query_ev.clear();
     size_t evn = 0;
     bool use_tc = ix->batch_mode == 1;
     if (use_tc && (chk = ensure_screen_copy(ix, s)) != MESSI_OK) return chk;
     use_tc = use_tc && ix->screen_state == 1;
-    if (use_tc && (chk = ensure_tc_workspace(ix, B)) != MESSI_OK) return chk;
+    if (use_tc && (chk = ensure_tc_workspace(ix, ws, B)) != MESSI_OK) return chk;
     for (uint32_t g = 0; g < nq && use_tc; g += B) {
         const unsigned nb = std::min<unsigned>(B, nq - g);
         int eq0 = -1, es0 = -1;
         if (ix->profiling) {
             eq0 = (int)evn;
-            cudaEventRecord(pool_event(ix, evn++), s);
+            cudaEventRecord(pool_event(ws, evn++), s);
         }
-        const TcWs w = tc_ws_view(ix);
-        launch_batch_seed(iv, qp, ix->bslots_dev, nb, dq + (size_t)g * ix->len, s, &ix->launches);
-        launch_tc_qprep(ix->bslots_dev, nb, ix->len, qp, w.qtiles, w.qconst, w.Ubits, w.cand_count, w.flags,
+        const TcWs w = tc_ws_view(ix, ws);
+        launch_batch_seed(iv, qp, ws->bslots_dev, nb, dq + (size_t)g * ix->len, s, &ws->launches);
+        launch_tc_qprep(ws->bslots_dev, nb, ix->len, qp, w.qtiles, w.qconst, w.Ubits, w.cand_count, w.flags,
                         w.active, s);
-        ++ix->launches;
+        ++ws->launches;
         unsigned more = 1;
         for (int pass = 0; pass < 3 && more; ++pass) {
             if (ix->profiling) {
                 es0 = (int)evn;
-                cudaEventRecord(pool_event(ix, evn++), s);
+                cudaEventRecord(pool_event(ws, evn++), s);
             }
             launch_tc_screen(ix->screen16, ix->xn, ix->xnorm, w.qtiles, w.qconst, w.Ubits, w.cand_count, w.cand_pos,
                              w.active, kTcCap, ix->N, ix->len, nb, (int)k, ix->status, s);
             if (ix->profiling) {
-                cudaEventRecord(pool_event(ix, evn++), s);
-                ix->scan_ev.push_back({es0, es0 + 1});
+                cudaEventRecord(pool_event(ws, evn++), s);
+                ws->scan_ev.push_back({es0, es0 + 1});
             }
-            launch_tc_recheck(iv, qp, ix->bslots_dev, nb, w.cand_count, w.cand_pos, kTcCap, w.active, s);
+            launch_tc_recheck(iv, qp, ws->bslots_dev, nb, w.cand_count, w.cand_pos, kTcCap, w.active, s);
             MESSI_CUDA(cudaMemsetAsync(w.n_active, 0, 4, s));
-            launch_tc_next_pass(ix->bslots_dev, nb, qp, kTcCap, w.Ubits, w.cand_count, w.active, w.n_active, s);
-            ix->launches += 3;
+            launch_tc_next_pass(ws->bslots_dev, nb, qp, kTcCap, w.Ubits, w.cand_count, w.active, w.n_active, s);
+            ws->launches += 3;
             MESSI_CUDA(cudaMemcpyAsync(&more, w.n_active, 4, cudaMemcpyDeviceToHost, s));
             MESSI_CUDA(cudaStreamSynchronize(s));
         }
-        launch_batch_finalize(iv, qp, ix->bslots_dev, nb, did + (size_t)g * k, ddist + (size_t)g * k, s, &ix->launches);
+        launch_batch_finalize(iv, qp, ws->bslots_dev, nb, did + (size_t)g * k, ddist + (size_t)g * k, s, &ws->launches);
         // queries the screen could not settle (values outside f16 range, or
         // still overflowing after three passes): the per-query kernels
         std::vector<unsigned> hflags(nb), hact(nb);
@@ -688,21 +693,21 @@ messi_status messi_query_batched(const messi_index *cix, const float *queries, u
         MESSI_CUDA(cudaStreamSynchronize(s));
         for (unsigned b = 0; b < nb; ++b) {
             if ((hflags[b] & 4u) || hact[b]) {
-                if ((chk = ensure_workspace(ix)) != MESSI_OK) return chk;
+                if ((chk = ensure_workspace(ix, ws)) != MESSI_OK) return chk;
                 QueryParams q1 = qp;
-                const QuerySlot one = ix->slot;
+                const QuerySlot one = ws->slot;
                 MESSI_CUDA(cudaMemsetAsync(one.acc, 0, sizeof(QueryCounters), s));
                 launch_prep(iv, q1, one, dq + (size_t)(g + b) * ix->len, s);
-                launch_seed(iv, q1, one, s, &ix->launches);
+                launch_seed(iv, q1, one, s, &ws->launches);
                 launch_scan(iv, q1, one, s);
-                launch_refine(iv, q1, one, s, &ix->launches);
+                launch_refine(iv, q1, one, s, &ws->launches);
                 launch_finalize(iv, q1, one, did + (size_t)(g + b) * k, ddist + (size_t)(g + b) * k, s);
-                ix->launches += 3;
+                ws->launches += 3;
             }
         }
         if (ix->profiling) {
-            cudaEventRecord(pool_event(ix, evn++), s);
-            for (unsigned r = 0; r < nb; ++r) ix->query_ev.push_back({eq0, (int)evn - 1});
+            cudaEventRecord(pool_event(ws, evn++), s);
+            for (unsigned r = 0; r < nb; ++r) ws->query_ev.push_back({eq0, (int)evn - 1});
         }
     }
     for (uint32_t g = 0; g < nq && !use_tc; g += B) {
@@ -711,39 +716,57 @@ messi_status messi_query_batched(const messi_index *cix, const float *queries, u
         cudaEvent_t f0 = nullptr, f1 = nullptr;
         if (ix->profiling) {
             eq0 = (int)evn;
-            cudaEventRecord(pool_event(ix, evn++), s);
+            cudaEventRecord(pool_event(ws, evn++), s);
             es0 = (int)evn;
-            f0 = pool_event(ix, evn++);
-            f1 = pool_event(ix, evn++);
+            f0 = pool_event(ws, evn++);
+            f1 = pool_event(ws, evn++);
         }
-        launch_batch(iv, qp, ix->bslots_dev, nb, dq + (size_t)g * ix->len, did + (size_t)g * k, ddist + (size_t)g * k,
-                     ix->tune_chunk_tiles, ix->tune_ctas_per_sm, ix->bcounter, s, &ix->launches, f0, f1);
+        launch_batch(iv, qp, ws->bslots_dev, nb, dq + (size_t)g * ix->len, did + (size_t)g * k, ddist + (size_t)g * k,
+                     ix->tune_chunk_tiles, ix->tune_ctas_per_sm, ws->bcounter, s, &ws->launches, f0, f1);
         if (ix->profiling) {
-            ix->scan_ev.push_back({es0, es0 + 1});
-            cudaEventRecord(pool_event(ix, evn++), s);
-            for (unsigned r = 0; r < nb; ++r) ix->query_ev.push_back({eq0, (int)evn - 1});
+            ws->scan_ev.push_back({es0, es0 + 1});
+            cudaEventRecord(pool_event(ws, evn++), s);
+            for (unsigned r = 0; r < nb; ++r) ws->query_ev.push_back({eq0, (int)evn - 1});
         }
     }
     MESSI_CUDA(cudaGetLastError());
-    ix->last = messi_stats{};
-    ix->last.queries = nq;
-    ix->last.kernel_launches = ix->launches - launches0;
-    ix->last_stream = s;
-    ix->last_batched = true;
+    ws->last = messi_stats{};
+    ws->last.queries = nq;
+    ws->last.kernel_launches = ws->launches - launches0;
+    ws->last_stream = s;
+    ws->last_batched = true;
     if (hi) MESSI_CUDA(cudaMemcpyAsync(ids, did, ibytes, cudaMemcpyDeviceToHost, s));
     if (hd) MESSI_CUDA(cudaMemcpyAsync(dists, ddist, dbytes, cudaMemcpyDeviceToHost, s));
     if (hq || hi || hd) MESSI_CUDA(cudaStreamSynchronize(s));
     return MESSI_OK;
 }
 
+messi_status messi_query(const messi_index *cix, const float *queries, uint32_t nq, uint32_t k,
+                         messi_dist dist, uint32_t window, int64_t *ids, float *dists, messi_stream stream)
+{
+    if (!cix) return fail(MESSI_EINVAL, "messi_query: null index");
+    messi_index *ix = const_cast<messi_index *>(cix);
+    return run_plain(ix, &ix->ws, queries, nq, k, dist, window, ids, dists, stream);
+}
+
+messi_status messi_query_batched(const messi_index *cix, const float *queries, uint32_t nq, uint32_t k,
+                                 messi_dist dist, uint32_t window, uint32_t batch, int64_t *ids, float *dists,
+                                 messi_stream stream)
+{
+    if (!cix) return fail(MESSI_EINVAL, "messi_query_batched: null index");
+    messi_index *ix = const_cast<messi_index *>(cix);
+    return run_batched(ix, &ix->ws, queries, nq, k, dist, window, batch, ids, dists, stream);
+}
+
 messi_status messi_query_stats(const messi_index *cix, messi_stats *out)
 {
     if (!cix || !out) return fail(MESSI_EINVAL, "messi_query_stats: null argument");
     messi_index *ix = const_cast<messi_index *>(cix);
-    *out = ix->last;
-    const QueryCounters *acc = ix->last_batched ? ix->bacc : ix->slot.acc;
+    Workspace *ws = &ix->ws;
+    *out = ws->last;
+    const QueryCounters *acc = ws->last_batched ? ws->bacc : ws->slot.acc;
     if (!acc) return MESSI_OK;
-    MESSI_CUDA(cudaStreamSynchronize(ix->last_stream));
+    MESSI_CUDA(cudaStreamSynchronize(ws->last_stream));
     QueryCounters c{};
     MESSI_CUDA(cudaMemcpy(&c, acc, sizeof(c), cudaMemcpyDeviceToHost));
     out->lb_evaluated = c.lb_evaluated;
@@ -756,17 +779,17 @@ messi_status messi_query_stats(const messi_index *cix, messi_stats *out)
     out->tie_rechecks = c.tie_rechecks;
     if (ix->profiling) {
         double sum = 0.0;
-        for (auto &pr : ix->scan_ev) {
+        for (auto &pr : ws->scan_ev) {
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, ix->ev_pool[pr.first], ix->ev_pool[pr.second]);
+            cudaEventElapsedTime(&ms, ws->ev_pool[pr.first], ws->ev_pool[pr.second]);
             sum += ms;
         }
         out->scan_ms = sum;
-        out->scan_launches = ix->scan_ev.size();
+        out->scan_launches = ws->scan_ev.size();
         std::vector<double> lat;
-        for (auto &pr : ix->query_ev) {
+        for (auto &pr : ws->query_ev) {
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, ix->ev_pool[pr.first], ix->ev_pool[pr.second]);
+            cudaEventElapsedTime(&ms, ws->ev_pool[pr.first], ws->ev_pool[pr.second]);
             lat.push_back(ms);
         }
         if (!lat.empty()) {
@@ -817,15 +840,16 @@ messi_status messi_lower_bounds(const messi_index *cix, const float *query, mess
     if (dist != MESSI_ED && dist != MESSI_DTW) return fail(MESSI_EINVAL, "messi_lower_bounds: unknown distance");
     if (dist == MESSI_DTW && window >= (uint32_t)cix->len) return fail(MESSI_EINVAL, "messi_lower_bounds: window must be < len");
     messi_index *ix = const_cast<messi_index *>(cix);
+    Workspace *ws = &ix->ws;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ensure_attributes();
-    messi_status chk = ensure_workspace(ix);
+    messi_status chk = ensure_workspace(ix, ws);
     if (chk != MESSI_OK) return chk;
     const bool hq = !is_device_ptr(query), ho = !is_device_ptr(lb2);
     const size_t qbytes = (size_t)ix->len * 4, obytes = (size_t)ix->N * 4;
-    if ((hq || ho) && !ensure_stage(ix, align256(qbytes) + align256(obytes)))
+    if ((hq || ho) && !ensure_stage(ws, align256(qbytes) + align256(obytes)))
         return fail(MESSI_ENOMEM, "messi_lower_bounds: cannot allocate staging buffers");
-    char *stage = static_cast<char *>(ix->stage_block);
+    char *stage = static_cast<char *>(ws->stage_block);
     const float *dq = query;
     float *dout = lb2;
     if (hq) {
@@ -835,8 +859,8 @@ messi_status messi_lower_bounds(const messi_index *cix, const float *query, mess
     if (ho) dout = reinterpret_cast<float *>(stage + align256(qbytes));
     const IndexView iv = view_of(ix);
     QueryParams qp{1, (int)dist, dist == MESSI_DTW ? (int)window : 0, band_factor((int)dist, ix->len)};
-    launch_prep(iv, qp, ix->slot, dq, s);
-    launch_lower_bounds(iv, ix->slot, dout, s);
+    launch_prep(iv, qp, ws->slot, dq, s);
+    launch_lower_bounds(iv, ws->slot, dout, s);
     ix->launches += 2;
     MESSI_CUDA(cudaGetLastError());
     if (ho) MESSI_CUDA(cudaMemcpyAsync(lb2, dout, obytes, cudaMemcpyDeviceToHost, s));

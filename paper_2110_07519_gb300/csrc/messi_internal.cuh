@@ -105,6 +105,40 @@ struct QueryParams {
 
 }  // namespace messi
 
+namespace messi {
+// Mutable per-call state of the query paths.  The index owns one; a server
+// owns one per stream so that batches in flight on different streams never
+// share scratch memory.
+struct Workspace {
+    // plain path: one query slot with survivor arrays of N entries
+    void *ws_block = nullptr;
+    size_t ws_bytes = 0;
+    QuerySlot slot{};
+    // staging of host queries / outputs
+    void *stage_block = nullptr;
+    size_t stage_bytes = 0;
+    // batched path
+    void *bws_block = nullptr;
+    size_t bws_bytes = 0;
+    int bws_slots = 0;
+    QuerySlot *bslots_dev = nullptr;
+    unsigned *bcounter = nullptr;
+    QueryCounters *bacc = nullptr;
+    bool last_batched = false;
+    // tensor-core screen, per batch
+    void *tcws_block = nullptr;
+    size_t tcws_bytes = 0;
+    unsigned tcws_B = 0;
+    // statistics of the last call
+    messi_stats last{};
+    cudaStream_t last_stream = nullptr;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> scan_ev, query_ev;   // pairs of event indices
+    unsigned long long launches = 0;
+};
+void free_workspace(Workspace &w);
+}  // namespace messi
+
 struct messi_index {
     int device = 0;
     unsigned long long N = 0;
@@ -122,41 +156,20 @@ struct messi_index {
     double *beta64 = nullptr;
     unsigned int *status = nullptr;
     double beta_host[256] = {0};
-    // plain-path workspace (lazily allocated)
-    void *ws_block = nullptr;
-    size_t ws_bytes = 0;
-    messi::QuerySlot slot{};
-    // staging for host queries / outputs
-    void *stage_block = nullptr;
-    size_t stage_bytes = 0;
-    // batched workspace
-    void *bws_block = nullptr;
-    size_t bws_bytes = 0;
-    int bws_slots = 0;
-    messi::QuerySlot *bslots_dev = nullptr;
-    unsigned *bcounter = nullptr;
-    messi::QueryCounters *bacc = nullptr;
-    bool last_batched = false;
-    // tuned shapes of the batched path
-    unsigned tune_batch = 64, tune_chunk_tiles = 32, tune_ctas_per_sm = 2;
-    int batch_mode = 1;                 // 0: lower bound + FP32 refine, 1: tensor-core screen
-    // tensor-core screen: f16 tile copy of the rows, norms, per-batch buffers
-    __half *screen16 = nullptr;
-    float *xn = nullptr, *xnorm = nullptr;
-    int screen_state = 0;               // 0 not built, 1 ready, -1 unavailable (values outside f16 range)
-    void *tcws_block = nullptr;
-    size_t tcws_bytes = 0;
-    unsigned tcws_B = 0;
+    // default workspace of messi_query / messi_query_batched
+    messi::Workspace ws;
     // bookkeeping
     size_t device_bytes = 0;
     double build_ms = 0.0;
     bool profiling = false;
-    messi_stats last{};
-    cudaStream_t last_stream = nullptr;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, int>> scan_ev, query_ev;   // pairs of event indices
     unsigned long long launches = 0;
-    messi::QueryCounters *counters_host = nullptr;        // pinned readback
+    // tuned shapes of the batched path
+    unsigned tune_batch = 64, tune_chunk_tiles = 32, tune_ctas_per_sm = 2;
+    int batch_mode = 1;                 // 0: lower bound + FP32 refine, 1: tensor-core screen
+    // tensor-core screen: f16 tile copy of the rows and their norms
+    __half *screen16 = nullptr;
+    float *xn = nullptr, *xnorm = nullptr;
+    int screen_state = 0;               // 0 not built, 1 ready, -1 unavailable (values outside f16 range)
 };
 
 namespace messi {

@@ -219,6 +219,56 @@ messi_status messi_index_layout(const messi_index *ix, uint32_t *order, uint64_t
  * j = 1..c-1).  Host only, no GPU needed.  out: cardinality-1 doubles. */
 messi_status messi_breakpoints(uint32_t cardinality, double *out);
 
+/* ------------------------------------------------------------ serving ----
+ * A request loop over a resident index (the paper answers queries one after
+ * another and has no counterpart).  Requests enter an arrival queue; worker
+ * threads, one per CUDA stream, admit them into device batches in arrival
+ * order while the device memory charged to unfinished requests stays within
+ * mem_budget, run each batch (ED: messi_query_batched kernels; DTW: the
+ * per-query kernels) with k = the largest k of the batch, and give every
+ * request the first k of its row.  Batches on different streams overlap on
+ * the device.  A request's result does not depend on what else is in flight:
+ * the answer is exact and a k-NN answer is a prefix of any larger k.
+ */
+typedef struct {
+    uint32_t max_batch;     /* queries per device batch; default 1024            */
+    uint32_t max_k;         /* largest k a request may ask for; default 64       */
+    uint32_t streams;       /* worker streams (batches in flight); default 2     */
+    uint32_t max_queued;    /* arrival-queue cap (0 = unbounded); submit returns
+                               EBUSY beyond it                                   */
+    uint64_t mem_budget;    /* device bytes charged to admitted unfinished
+                               requests (0 = streams * max_batch requests)       */
+    uint64_t reserved[4];
+} messi_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, batches, inflight_peak;
+    double p50_ms, p99_ms, mean_ms;   /* submit-to-result latency of completed requests */
+    uint64_t reserved[4];
+} messi_server_stats;
+
+/* Start a server on `ix` (which must outlive it); cfg may be NULL.  Builds
+ * the screening copy of the index if needed and allocates per-stream
+ * buffers.  Synchronises the device. */
+messi_status messi_server_create(messi_index *ix, const messi_server_config *cfg, messi_server **out);
+
+/* Queue one query (host pointer, len floats; copied before return).  Returns
+ * a ticket.  EINVAL for bad k / window, EBUSY when the queue is full. */
+messi_status messi_server_submit(messi_server *srv, const float *query, uint32_t k, messi_dist dist,
+                                 uint32_t window, uint64_t *ticket);
+
+/* Collect a finished request: ids / dists are host arrays of its k entries,
+ * latency_ms (may be NULL) the time from submit to result.  Waits up to
+ * wait_us microseconds; EBUSY when not finished yet, EINVAL for an unknown or
+ * already collected ticket. */
+messi_status messi_server_poll(messi_server *srv, uint64_t ticket, int64_t *ids, float *dists,
+                               double *latency_ms, uint64_t wait_us);
+
+messi_status messi_server_get_stats(messi_server *srv, messi_server_stats *out);
+
+/* Stop the workers after the queued requests and release everything. */
+void messi_server_destroy(messi_server *srv);
+
 /* Thread-local description of the last failure ("" when none). */
 const char *messi_last_error(void);
 

@@ -59,6 +59,21 @@ class MessiIndexInfo(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class MessiServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("max_k", ctypes.c_uint32), ("streams", ctypes.c_uint32),
+                ("max_queued", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 4)]
+
+
+class MessiServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "rejected", "batches", "inflight_peak")] + [
+        ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+        ("reserved", ctypes.c_uint64 * 4)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
+
+
 _SIGS = {
     "messi_build": [_P, _U64, _U32, _U32, _U32, _P, _P, ctypes.POINTER(_P)],
     "messi_free": [_P],
@@ -75,12 +90,18 @@ _SIGS = {
     "messi_summarize": [_P, _U64, _U32, _U32, _U32, _P, _P],
     "messi_index_layout": [_P, _P, _P, _P],
     "messi_breakpoints": [_U32, _P],
+    "messi_server_create": [_P, ctypes.POINTER(MessiServerConfig), ctypes.POINTER(_P)],
+    "messi_server_submit": [_P, _P, _U32, _I, _U32, ctypes.POINTER(_U64)],
+    "messi_server_poll": [_P, _U64, _P, _P, ctypes.POINTER(ctypes.c_double), _U64],
+    "messi_server_get_stats": [_P, ctypes.POINTER(MessiServerStats)],
+    "messi_server_destroy": [_P],
     "messi_last_error": [],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
     _fn.argtypes = _args
-    _fn.restype = ctypes.c_char_p if _name == "messi_last_error" else (None if _name == "messi_free" else _I)
+    _fn.restype = ctypes.c_char_p if _name == "messi_last_error" else (
+        None if _name in ("messi_free", "messi_server_destroy") else _I)
 
 
 class MessiError(RuntimeError):
@@ -306,6 +327,59 @@ def messi_breakpoints(cardinality: int) -> np.ndarray:
 def messi_free(index: Index):
     """Release the index's device memory now (also done when it is collected)."""
     index.free()
+
+
+# ----------------------------------------------------------------- serving
+class Server:
+    def __init__(self, handle, index):
+        self.handle = handle
+        self.index = index          # the index must outlive the server
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.messi_server_destroy(h)
+            self.handle = None
+
+
+def messi_server_create(index: Index, max_batch: int = 0, max_k: int = 0, streams: int = 0,
+                        max_queued: int = 0, mem_budget: int = 0) -> Server:
+    cfg = MessiServerConfig()
+    cfg.max_batch, cfg.max_k, cfg.streams, cfg.max_queued, cfg.mem_budget = (max_batch, max_k, streams,
+                                                                             max_queued, mem_budget)
+    out = ctypes.c_void_p()
+    _check(_lib.messi_server_create(index.handle, ctypes.byref(cfg), ctypes.byref(out)), "messi_server_create")
+    return Server(out, index)
+
+
+def messi_server_submit(server: Server, query, k: int = 1, dist: int = MESSI_ED, window: int = 0) -> int:
+    q = np.ascontiguousarray(query, dtype=np.float32).reshape(-1)
+    t = ctypes.c_uint64()
+    _check(_lib.messi_server_submit(server.handle, q.ctypes.data, k, dist, window, ctypes.byref(t)),
+           "messi_server_submit")
+    return t.value
+
+
+def messi_server_poll(server: Server, ticket: int, k: int, wait_us: int = 0):
+    """(ids, dists, latency_ms) of a finished request, or None while it runs."""
+    ids = np.empty(k, dtype=np.int64)
+    d = np.empty(k, dtype=np.float32)
+    lat = ctypes.c_double()
+    st = _lib.messi_server_poll(server.handle, ticket, ids.ctypes.data, d.ctypes.data, ctypes.byref(lat), wait_us)
+    if st == 5:
+        return None
+    _check(st, "messi_server_poll")
+    return ids, d, lat.value
+
+
+def messi_server_get_stats(server: Server) -> dict:
+    out = MessiServerStats()
+    _check(_lib.messi_server_get_stats(server.handle, ctypes.byref(out)), "messi_server_get_stats")
+    return out.as_dict()
+
+
+def messi_server_destroy(server: Server):
+    server.__del__()
 
 
 def messi_last_error() -> str:

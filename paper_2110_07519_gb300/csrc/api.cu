@@ -522,6 +522,9 @@ messi_status messi_build(const float *series, uint64_t n, uint32_t len, uint32_t
     return MESSI_OK;
 }
 
+}  // extern "C"
+
+namespace messi {
 static messi_status query_args(const messi_index *ix, const float *queries, uint32_t nq, uint32_t k,
                                messi_dist dist, uint32_t window, const int64_t *ids, const float *dists)
 {
@@ -740,6 +743,10 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
     if (hq || hi || hd) MESSI_CUDA(cudaStreamSynchronize(s));
     return MESSI_OK;
 }
+
+}  // namespace messi
+
+extern "C" {
 
 messi_status messi_query(const messi_index *cix, const float *queries, uint32_t nq, uint32_t k,
                          messi_dist dist, uint32_t window, int64_t *ids, float *dists, messi_stream stream)

@@ -139,6 +139,16 @@ struct Workspace {
 void free_workspace(Workspace &w);
 }  // namespace messi
 
+struct messi_index;
+namespace messi {
+// query paths on an explicit workspace (api.cu)
+messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uint32_t nq, uint32_t k,
+                       messi_dist dist, uint32_t window, int64_t *ids, float *dists, messi_stream stream);
+messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, uint32_t nq, uint32_t k,
+                         messi_dist dist, uint32_t window, uint32_t batch, int64_t *ids, float *dists,
+                         messi_stream stream);
+}  // namespace messi
+
 struct messi_index {
     int device = 0;
     unsigned long long N = 0;

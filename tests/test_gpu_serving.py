@@ -1,0 +1,101 @@
+"""Serving loop: requests submitted one at a time and the same requests
+arriving as a Poisson stream (continuous batching, mixed ED / DTW and k)
+give identical results, which also match the FP64 oracle."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def m():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import paper_2110_07519_gb300 as mod
+
+    return mod
+
+
+def make_requests(x, count, seed):
+    rng = np.random.default_rng(seed)
+    qs = synth.query_mix(x, count, seed=seed)
+    reqs = []
+    for i in range(count):
+        dtw = rng.random() < 0.2
+        reqs.append((qs[i], int(rng.choice([1, 10])), 1 if dtw else 0, 12 if dtw else 0))
+    return reqs
+
+
+def test_alone_equals_in_the_mix_and_oracle(m):
+    x = synth.random_walks(60_000, 128, seed=901)
+    ix = m.messi_build(torch.from_numpy(x).cuda(), 16, 256)
+    srv = m.messi_server_create(ix, max_batch=64, max_k=16, streams=2)
+    reqs = make_requests(x, 120, seed=902)
+
+    alone = []
+    for q, k, dist, r in reqs:
+        t = m.messi_server_submit(srv, q, k, dist, r)
+        res = None
+        while res is None:
+            res = m.messi_server_poll(srv, t, k, wait_us=200_000)
+        alone.append(res)
+
+    # the same requests as a Poisson stream while results are collected
+    rng = np.random.default_rng(903)
+    order = rng.permutation(len(reqs))
+    tickets = {}
+
+    def producer():
+        for i in order:
+            q, k, dist, r = reqs[i]
+            tickets[i] = m.messi_server_submit(srv, q, k, dist, r)
+            time.sleep(rng.exponential(200e-6))
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    mixed = [None] * len(reqs)
+    for i in order:
+        k = reqs[i][1]
+        while mixed[i] is None:
+            mixed[i] = m.messi_server_poll(srv, tickets[i], k, wait_us=200_000)
+    for i in range(len(reqs)):
+        assert np.array_equal(alone[i][0], mixed[i][0]), i
+        assert np.array_equal(alone[i][1], mixed[i][1]), i
+    st = m.messi_server_get_stats(srv)
+    assert st["completed"] == st["submitted"] == 2 * len(reqs)
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+
+    # exactness against the oracle on a sample of both distances
+    for i in [j for j in range(len(reqs)) if reqs[j][2] == 0][:10] + [j for j in range(len(reqs)) if reqs[j][2] == 1][:4]:
+        q, k, dist, r = reqs[i]
+        ref_ids, ref_d2 = oracle.knn(x, q, k, dist, r)
+        assert np.array_equal(mixed[i][0], ref_ids[0]), i
+        rel = np.abs(mixed[i][1] - np.sqrt(ref_d2[0])) / np.maximum(np.sqrt(ref_d2[0]), 1e-30)
+        assert rel.max() <= 1e-5
+    m.messi_server_destroy(srv)
+
+
+def test_server_rejects_bad_requests(m):
+    x = synth.random_walks(2000, 64, seed=904)
+    ix = m.messi_build(torch.from_numpy(x).cuda(), 16, 256)
+    srv = m.messi_server_create(ix, max_batch=8, max_k=4, streams=1, max_queued=1000)
+    with pytest.raises(m.MessiError):
+        m.messi_server_submit(srv, x[0], k=5)                 # above max_k
+    with pytest.raises(m.MessiError):
+        m.messi_server_submit(srv, x[0], k=1, dist=1, window=64)
+    with pytest.raises(m.MessiError):
+        m.messi_server_poll(srv, 12345, 1)                    # unknown ticket
+    t = m.messi_server_submit(srv, x[7], k=2)
+    res = None
+    while res is None:
+        res = m.messi_server_poll(srv, t, 2, wait_us=100_000)
+    assert res[0][0] == 7 and res[1][0] == 0.0
+    m.messi_server_destroy(srv)

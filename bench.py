@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--form", default="both", choices=["both", "plain", "batched"])
+    ap.add_argument("--serve", action="store_true", help="serving-loop measurement instead of the step bench")
+    ap.add_argument("--serve-n", type=int, default=50_000_000)
+    ap.add_argument("--serve-len", type=int, default=128)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000, 10000, 100000])
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-max", type=int, default=60000)
     ap.add_argument("--batch-mode", default="tc", choices=["tc", "lb"],
                     help="batched kernels: tensor-core screen (tc) or fused lower bound + refine (lb)")
     ap.add_argument("--mix", default="mixed", choices=["mixed", "fresh", "s0.1", "s0.5", "s1.0"],
@@ -385,9 +391,79 @@ def run_messi(args, ws, rank, local):
         pg.destroy_process_group()
 
 
+def run_serve(args, ws, rank, local):
+    """Serving loop: Poisson arrivals at several rates, 80% ED / 20% DTW
+    (window 10%), k in {1, 10}; submit-to-result latency and completed
+    queries/s, for the tensor-core screened and the lower-bound batch kernels."""
+    import threading
+
+    import torch
+
+    import paper_2110_07519_gb300 as m
+    import synth
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    n, length = args.serve_n, args.serve_len
+    data = synth.random_walks_torch(n, length, seed=synth.DATASET_SEED + rank, device=dev)
+    ix = m.messi_build(data, 16, 256)
+    pool = synth.query_mix_torch(data, 4096, seed=synth.QUERY_SEED).cpu().numpy()
+    del data
+    torch.cuda.empty_cache()
+    r_dtw = int(0.10 * length)
+    out = {}
+    for mode_name, mode in (("tc_screen", m.MESSI_BATCH_TC_SCREEN), ("lb_refine", m.MESSI_BATCH_LB_REFINE)):
+        m.messi_set_batch_mode(ix, mode)
+        res_mode = {}
+        for rate in args.serve_rates:
+            srv = m.messi_server_create(ix, max_batch=1024, max_k=16, streams=2)
+            rng = np.random.default_rng(int(rate))
+            total = int(min(args.serve_seconds * rate, args.serve_max))
+            kinds = rng.random(total) < 0.2
+            ks = rng.choice([1, 10], size=total)
+            tickets = [None] * total
+            t0 = time.perf_counter()
+
+            def producer():
+                nxt = time.perf_counter()
+                for i in range(total):
+                    nxt += rng.exponential(1.0 / rate)
+                    while time.perf_counter() < nxt:
+                        pass
+                    dtw = bool(kinds[i])
+                    tickets[i] = m.messi_server_submit(srv, pool[i % len(pool)], int(ks[i]), 1 if dtw else 0,
+                                                       r_dtw if dtw else 0)
+
+            th = threading.Thread(target=producer)
+            th.start()
+            th.join()
+            lat = []
+            for i in range(total):
+                r = None
+                while r is None:
+                    r = m.messi_server_poll(srv, tickets[i], int(ks[i]), wait_us=500_000)
+                lat.append(r[2])
+            wall = time.perf_counter() - t0
+            st = m.messi_server_get_stats(srv)
+            m.messi_server_destroy(srv)
+            lat = np.array(lat)
+            res_mode[str(rate)] = {"offered_qps": rate, "completed": total, "served_qps": total / wall,
+                                   "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                   "batches": st["batches"], "inflight_peak": st["inflight_peak"]}
+        out[mode_name] = res_mode
+    print(json.dumps({"mode": "serve", "config": {"workload": f"{n} x {length} fp32 random walks, 80% ED / 20% DTW "
+                                                              f"(window {r_dtw}), k in {{1,10}}, Poisson arrivals",
+                                                  "data": DATA_DESC},
+                      "results": out}), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
+    if args.serve:
+        if rank == 0:
+            run_serve(args, ws, rank, local)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank, local)
     else:

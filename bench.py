@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--len", type=int, default=256)
     ap.add_argument("--batch", type=int, default=1024, help="queries per step")
     ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--dist", default="ed", choices=["ed", "dtw"])
+    ap.add_argument("--window", type=int, default=-1, help="DTW reach in points (default 10%% of len)")
     ap.add_argument("--cpu-sample", type=int, default=4, help="queries in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -152,7 +154,7 @@ def dist_env():
     return ws, rank, local
 
 
-def oracle_sample(data_t, queries_np, k, chunk=1 << 20):
+def oracle_sample(data_t, queries_np, k, chunk=1 << 20, dist=0, r=0):
     """FP64 brute force of `queries_np` over the device collection `data_t`,
     copied to the host chunk by chunk; returns (ids, d2, cpu_seconds, threads)."""
     import torch
@@ -168,7 +170,7 @@ def oracle_sample(data_t, queries_np, k, chunk=1 << 20):
         host[: hi - lo].copy_(data_t[lo:hi])
         rows = host[: hi - lo].numpy()
         t0 = time.perf_counter()
-        part = oracle.knn(rows, queries_np, k, oracle.ED, id_base=lo)
+        part = oracle.knn(rows, queries_np, k, dist, r, id_base=lo)
         best = part if best is None else oracle.merge_topk([best, part], k)
         cpu_s += time.perf_counter() - t0
     return best[0], best[1], cpu_s, oracle.max_threads()
@@ -213,15 +215,15 @@ def run_reference(args, ws, rank, local):
 
 
 # -------------------------------------------------------------- GPU arm
-def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists):
+def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists, dist=0, window=0):
     """W warm-up and K timed steps of one query form; per-step stats."""
     import torch
 
     def step(qs):
         if form == "plain":
-            m.messi_query(ix, qs, k=k, ids=ids, dists=dists)
+            m.messi_query(ix, qs, k=k, dist=dist, window=window, ids=ids, dists=dists)
         else:
-            m.messi_query_batched(ix, qs, k=k, batch=B, ids=ids, dists=dists)
+            m.messi_query_batched(ix, qs, k=k, dist=dist, window=window, batch=B, ids=ids, dists=dists)
 
     m.messi_set_profiling(ix, True)
     for s in range(W):
@@ -255,9 +257,9 @@ def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists):
         elapsed_ms = float(t.item())
     # per-query latency percentiles over every timed query in one call
     if form == "plain":
-        m.messi_query(ix, qpool[W * B:(W + K) * B], k=k)
+        m.messi_query(ix, qpool[W * B:(W + K) * B], k=k, dist=dist, window=window)
     else:
-        m.messi_query_batched(ix, qpool[W * B:(W + K) * B], k=k, batch=B)
+        m.messi_query_batched(ix, qpool[W * B:(W + K) * B], k=k, dist=dist, window=window, batch=B)
     st_all = m.messi_query_stats(ix)
     m.messi_set_profiling(ix, False)
     agg.update(elapsed_ms=elapsed_ms, clocks=clk, p50=st_all["query_ms_p50"], p99=st_all["query_ms_p99"])
@@ -302,7 +304,10 @@ def run_messi(args, ws, rank, local):
     cpu, oracle_q, r_ids, r_d2 = None, None, None, None
     if rank == 0 and not args.no_cpu_baseline and args.cpu_sample > 0:
         oracle_q = qpool[W * B:W * B + args.cpu_sample].cpu().numpy()
-        r_ids, r_d2, cpu_s, threads = oracle_sample(data, oracle_q, args.k)
+        r_ids, r_d2, cpu_s, threads = oracle_sample(data, oracle_q, args.k,
+                                                    dist=1 if args.dist == "dtw" else 0,
+                                                    r=(args.window if args.window >= 0 else int(0.10 * args.len))
+                                                    if args.dist == "dtw" else 0)
         cpu = {"value": args.cpu_sample / cpu_s, "unit": "queries/s", "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_sample} queries of the timed mix, FP64 brute force over all {args.n} "
                          f"series (1M-row chunks copied to the host; copy time excluded)"}
@@ -310,11 +315,13 @@ def run_messi(args, ws, rank, local):
     del data
     torch.cuda.empty_cache()
 
+    dist_code = 1 if args.dist == "dtw" else 0
+    window = (args.window if args.window >= 0 else int(0.10 * args.len)) if dist_code else 0
     batch_mode = "tc_screen" if args.batch_mode == "tc" else "lb_refine"
     m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN if args.batch_mode == "tc" else m.MESSI_BATCH_LB_REFINE)
     forms = {}
     for form in (["plain", "batched"] if args.form == "both" else [args.form]):
-        r = time_form(m, ix, qpool, form, B, K, W, args.k, stream, pg, dev, ids, dists)
+        r = time_form(m, ix, qpool, form, B, K, W, args.k, stream, pg, dev, ids, dists, dist_code, window)
         nqt = B * K
         kern_avg_s = r["kern_ms"] * 1e-3 / max(r["kern_launches"], 1)
         if form == "plain":
@@ -367,7 +374,7 @@ def run_messi(args, ws, rank, local):
     if oracle_q is not None:
         for form in forms:
             fn = m.messi_query if form == "plain" else m.messi_query_batched
-            g_ids, g_d = fn(ix, oracle_q, k=args.k)
+            g_ids, g_d = fn(ix, oracle_q, k=args.k, dist=dist_code, window=window)
             rel = np.abs(g_d.astype(np.float64) - np.sqrt(r_d2)) / np.maximum(np.sqrt(r_d2), 1e-30)
             parity[form] = {"ids_equal": bool(np.array_equal(g_ids, r_ids)), "max_rel_err": float(rel.max())}
 
@@ -376,7 +383,8 @@ def run_messi(args, ws, rank, local):
             "metric": METRIC, "value": head["value"], "unit": "queries/s", "n_gpus": ws, "steps": K, "warmup": W,
             "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": head["value"] / PAPER_QPS, "dtype": "f32", "data": DATA_DESC,
-            "config": {"workload": f"{args.n} x {args.len} fp32 random walks, ED, k={args.k}, 16 segments, "
+            "config": {"workload": f"{args.n} x {args.len} fp32 random walks, "
+                                   f"{'ED' if not dist_code else f'DTW window {window}'}, k={args.k}, 16 segments, "
                                    f"8-bit SAX", "form": head_form, "queries": args.mix,
                        "queries_per_step": B, "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (16 B iSAX word per series streamed per query)"},

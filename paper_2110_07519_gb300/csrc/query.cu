@@ -773,6 +773,120 @@ k_fused_ed(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, un
     }
 }
 
+// ------------------------------------------------- DTW, one thread per candidate
+// Band of width W = 2R+1 (R >= r, the window; band cells farther than r from
+// the diagonal are +inf) held in registers: D[b] is the cell (i, i - R + b) of
+// the current row, xw[b] the candidate value x[i - R + b].  Row by row each
+// thread updates its band in place (diagonal = old D[b], up = old D[b+1],
+// left = new D[b-1]) -- the same recurrence, operands and FP32 operations as
+// the warp wavefront -- and abandons when a row minimum exceeds the live
+// threshold (every warping path crosses every row).  Threads advance
+// independently through their own candidates (a strided share of the list).
+template <int R>
+__device__ __forceinline__ float thread_dtw(const float *__restrict__ qs, const float *__restrict__ x, int n, int r,
+                                            float thr)
+{
+    constexpr int W = 2 * R + 1;
+    const float INF = f_inf();
+    float D[W], xw[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+        D[b] = (b == R) ? 0.f : INF;                      // row -1: only the diagonal of (0, 0) is open
+        const int j = b - R;                              // x index of band cell b in row 0
+        xw[b] = (j >= 0 && j < n) ? __ldg(x + j) : 0.f;
+    }
+    for (int i = 0; i < n; ++i) {
+        const float qi = qs[i];
+        float left = INF, rmin = INF;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const int j = i - R + b;
+            const float up = (b + 1 < W) ? D[b + 1] : INF;
+            const float best = fminf(fminf(D[b], up), left);
+            const float d = qi - xw[b];
+            const bool inside = j >= 0 && j < n && (b - R <= r) && (R - b <= r);
+            const float v = inside ? d * d + best : INF;
+            D[b] = v;
+            left = v;
+            rmin = fminf(rmin, v);
+        }
+        if (rmin > thr) return rmin;
+        // slide the candidate window by one
+#pragma unroll
+        for (int b = 0; b + 1 < W; ++b) xw[b] = xw[b + 1];
+        const int jn = i + 1 + R;
+        xw[W - 1] = (jn < n) ? __ldg(x + jn) : 0.f;
+    }
+    return D[R];
+}
+
+template <int R, int MODE>   // MODE 0: refine the LB_Keogh survivors, 1: seed range
+__global__ void __launch_bounds__(128)
+k_dtw_thread(IndexView iv, QueryParams qp, QuerySlot slot)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    QueryState *st = slot.st;
+    if (ld_volatile_u32(&st->invalid)) return;
+    float *qs = reinterpret_cast<float *>(dsm);
+    for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
+    __syncthreads();
+    const unsigned lo = MODE ? st->seed_lo : 0u;
+    const unsigned count = MODE ? st->seed_hi - st->seed_lo : ld_volatile_u32(&st->surv2_count);
+    const unsigned T = gridDim.x * blockDim.x;
+    unsigned long long done = 0, aband = 0;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += T) {
+        const unsigned pos = MODE ? lo + e : slot.surv2[e];
+        const float thr = MODE ? f_inf() : prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        const float d2 = thread_dtw<R>(qs, iv.raw + (unsigned long long)pos * iv.len, iv.len, qp.r, thr);
+        if (MODE) {
+            slot.seedbuf[e] = pack_cand(d2, iv.ids[pos]);
+        } else if (d2 <= thr) {
+            ++done;
+            offer(qp, slot, iv.status, d2, iv.ids[pos]);
+        } else {
+            ++aband;
+        }
+    }
+    if (!MODE) {
+        if (done) atomicAdd(&st->c.refined, done);
+        if (aband) atomicAdd(&st->c.abandoned, aband);
+    }
+}
+
+// smallest instantiated band reach >= r (or -1: use the warp wavefront)
+int dtw_thread_reach(int r)
+{
+    static const int reaches[] = {0, 1, 2, 4, 6, 8, 12, 16, 20, 25, 32};
+    for (int R : reaches)
+        if (R >= r) return R;
+    return -1;
+}
+
+template <int MODE>
+bool launch_dtw_thread(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot, cudaStream_t s)
+{
+    const int R = dtw_thread_reach(qp.r);
+    const unsigned grid = num_sms() * 8;
+    const size_t sm = (size_t)iv.len * 4;
+    switch (R) {
+#define MESSI_DTW_CASE(RR) \
+    case RR: k_dtw_thread<RR, MODE><<<grid, 128, sm, s>>>(iv, qp, slot); return true;
+        MESSI_DTW_CASE(0)
+        MESSI_DTW_CASE(1)
+        MESSI_DTW_CASE(2)
+        MESSI_DTW_CASE(4)
+        MESSI_DTW_CASE(6)
+        MESSI_DTW_CASE(8)
+        MESSI_DTW_CASE(12)
+        MESSI_DTW_CASE(16)
+        MESSI_DTW_CASE(20)
+        MESSI_DTW_CASE(25)
+        MESSI_DTW_CASE(32)
+#undef MESSI_DTW_CASE
+        default: return false;
+    }
+}
+
 // ------------------------------------------------------------- finalize
 // Bitonic sort of n (power of two) entries in shared memory with a caller
 // ordering `less(i, j)` and swap `swap(i, j)`.
@@ -1004,7 +1118,7 @@ void launch_seed(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cud
     if (qp.dist == 0) {
         const size_t sm = iv.len * 4;
         k_seed_dist<0><<<num_sms() * 2, 256, sm, s>>>(iv, qp, slot);
-    } else {
+    } else if (!launch_dtw_thread<1>(iv, qp, slot, s)) {
         const int wpb = dtw_warps_per_block(iv.len);
         const size_t sm = (size_t)iv.len * 4 + (size_t)wpb * 3 * iv.len * 4;
         k_seed_dist<1><<<num_sms() * 4, wpb * 32, sm, s>>>(iv, qp, slot);
@@ -1031,9 +1145,11 @@ void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, c
         if (launches) *launches += 1;
     } else {
         k_lbk<<<num_sms() * 8, 256, iv.len * 8, s>>>(iv, qp, slot);
-        const int wpb = dtw_warps_per_block(iv.len);
-        const size_t sm = (size_t)iv.len * 4 + (size_t)wpb * 3 * iv.len * 4;
-        k_dtw<<<num_sms() * 4, wpb * 32, sm, s>>>(iv, qp, slot);
+        if (!launch_dtw_thread<0>(iv, qp, slot, s)) {
+            const int wpb = dtw_warps_per_block(iv.len);
+            const size_t sm = (size_t)iv.len * 4 + (size_t)wpb * 3 * iv.len * 4;
+            k_dtw<<<num_sms() * 4, wpb * 32, sm, s>>>(iv, qp, slot);
+        }
         if (launches) *launches += 2;
     }
 }

@@ -458,6 +458,8 @@ def run_serve(args, ws, rank, local):
             res_mode[str(rate)] = {"offered_qps": rate, "completed": total, "served_qps": total / wall,
                                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                                    "batches": st["batches"], "inflight_peak": st["inflight_peak"]}
+            print(json.dumps({"mode": "serve-partial", "batch_kernels": mode_name, "rate": rate,
+                              **res_mode[str(rate)]}), file=sys.stderr, flush=True)
         out[mode_name] = res_mode
     print(json.dumps({"mode": "serve", "config": {"workload": f"{n} x {length} fp32 random walks, 80% ED / 20% DTW "
                                                               f"(window {r_dtw}), k in {{1,10}}, Poisson arrivals",

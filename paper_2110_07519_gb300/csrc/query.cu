@@ -514,32 +514,56 @@ k_refine_ed(IndexView iv, QueryParams qp, QuerySlot slot)
 }
 
 // ------------------------------------------------------ DTW: LB_Keogh
+// Warp per survivor.  First LB_Keogh of the candidate against the query's
+// envelope (Sec. 3.4); if that does not prune, the same bound with the roles
+// swapped -- the candidate's envelope against the query -- which is also a
+// lower bound of the banded DTW (the band is symmetric, so DTW(Q, C) =
+// DTW(C, Q)) and is tight exactly where the first is loose: a noisy query has
+// a wide envelope, a smooth candidate a narrow one.  The candidate's envelope
+// comes from van Herk / Gil-Werman block prefix and suffix maxima (minima)
+// in the warp's shared-memory buffer.  Every operation of both bounds rounds
+// toward -inf.
+__device__ __forceinline__ float lbk_tail(float acc)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) acc = __fadd_rd(acc, __shfl_xor_sync(0xffffffffu, acc, off));
+    return acc;
+}
+
 __global__ void __launch_bounds__(256)
-k_lbk(IndexView iv, QueryParams qp, QuerySlot slot)
+k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ unsigned prefix[kMaxScanGrid + 1];
     __shared__ unsigned counts[kMaxScanGrid];
     QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
+    const int len = iv.len;
     float *Us = reinterpret_cast<float *>(dsm);
-    float *Ls = Us + iv.len;
-    for (int i = threadIdx.x; i < iv.len; i += blockDim.x) {
+    float *Ls = Us + len;
+    float *qs = Ls + len;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *P = qs + len + (size_t)wib * 4 * len;      // per warp: prefix max, suffix max, prefix min, suffix min
+    float *S = P + len, *Pm = S + len, *Sm = Pm + len;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
         Us[i] = slot.U[i];
         Ls[i] = slot.L[i];
+        qs[i] = slot.q[i];
     }
     const unsigned G = st->scan_grid;
     const unsigned long long RW = st->region_words;
     const unsigned nchunks = chunk_prefix(slot, G, prefix, counts);
-    const int lane = threadIdx.x & 31;
-    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    const int r = qp.r < len - 1 ? qp.r : len - 1;
+    const int w = 2 * r + 1;
+    const int nblk = (len + w - 1) / w;
+    const unsigned nw = gridDim.x * wpb;
     unsigned long long pass = 0;
     unsigned pend = 0, npend = 0;          // passing positions, one per lane, flushed by 32
-    for (unsigned ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += nw) {
-        const unsigned r = region_of(ch, prefix, G);
-        const unsigned within = (ch - prefix[r]) * 32 + lane;
-        const bool valid = within < counts[r];
-        const unsigned long long i = r * RW + within;
+    for (unsigned ch = blockIdx.x * wpb + wib; ch < nchunks; ch += nw) {
+        const unsigned rg = region_of(ch, prefix, G);
+        const unsigned within = (ch - prefix[rg]) * 32 + lane;
+        const bool valid = within < counts[rg];
+        const unsigned long long i = rg * RW + within;
         const unsigned pos = valid ? slot.surv_pos[i] : 0u;
         const float lb = valid ? slot.surv_lb[i] : f_inf();
         const float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
@@ -548,24 +572,67 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot)
             const int a = __ffs(mask) - 1;
             mask &= mask - 1;
             const unsigned pa = __shfl_sync(0xffffffffu, pos, a);
-            const float *x = iv.raw + (unsigned long long)pa * iv.len;
-            // LB_Keogh^2, every operation rounded toward -inf (a certain lower bound)
+            const float *x = iv.raw + (unsigned long long)pa * len;
+            // candidate against the query's envelope
             float acc = 0.f;
             bool pruned = false;
-            for (int base = 0; base < iv.len; base += 256) {
-                for (int t = lane; t < 256 && base + t < iv.len; t += 32) {
+            for (int base = 0; base < len && !pruned; base += 256) {
+                for (int t = lane; t < 256 && base + t < len; t += 32) {
                     const int idx = base + t;
                     const float c = __ldg(x + idx);
+                    P[idx] = c;                               // keep the row for the second bound
                     float d = 0.f;
                     if (c > Us[idx]) d = __fsub_rd(c, Us[idx]);
                     else if (c < Ls[idx]) d = __fsub_rd(Ls[idx], c);
                     acc = __fadd_rd(acc, __fmul_rd(d, d));
                 }
-                float tot = acc;
-#pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) tot = __fadd_rd(tot, __shfl_xor_sync(0xffffffffu, tot, off));
-                if (tot > thr) { pruned = true; break; }
+                if (lbk_tail(acc) > thr) pruned = true;
             }
+            if (!pruned && r > 0) {
+                __syncwarp();
+                // block prefix / suffix extrema of the candidate (blocks of w points)
+                for (int blk = lane; blk < nblk; blk += 32) {
+                    const int b0 = blk * w, b1 = min(len, b0 + w);
+                    float mx = -f_inf(), mn = f_inf();
+                    for (int t = b0; t < b1; ++t) {
+                        const float v = P[t];
+                        mx = fmaxf(mx, v);
+                        mn = fminf(mn, v);
+                        S[t] = mx;        // running prefix max, moved to P below
+                        Sm[t] = mn;
+                    }
+                    mx = -f_inf();
+                    mn = f_inf();
+                    for (int t = b1 - 1; t >= b0; --t) {
+                        const float v = P[t];
+                        mx = fmaxf(mx, v);
+                        mn = fminf(mn, v);
+                        P[t] = S[t];      // prefix max
+                        Pm[t] = Sm[t];    // prefix min
+                        S[t] = mx;        // suffix max
+                        Sm[t] = mn;       // suffix min
+                    }
+                }
+                __syncwarp();
+                float acc2 = 0.f;
+                for (int base = 0; base < len && !pruned; base += 256) {
+                    for (int t = lane; t < 256 && base + t < len; t += 32) {
+                        const int idx = base + t;
+                        const int lo = idx - r < 0 ? 0 : idx - r, hi = idx + r > len - 1 ? len - 1 : idx + r;
+                        float U, L;
+                        if (lo == 0) { U = P[hi]; L = Pm[hi]; }
+                        else if (hi == len - 1) { U = S[lo]; L = Sm[lo]; }
+                        else { U = fmaxf(S[lo], P[hi]); L = fminf(Sm[lo], Pm[hi]); }
+                        const float c = qs[idx];
+                        float d = 0.f;
+                        if (c > U) d = __fsub_rd(c, U);
+                        else if (c < L) d = __fsub_rd(L, c);
+                        acc2 = __fadd_rd(acc2, __fmul_rd(d, d));
+                    }
+                    if (lbk_tail(acc2) > thr) pruned = true;
+                }
+            }
+            __syncwarp();
             if (!pruned) {
                 ++pass;
                 if (lane == (int)npend) pend = pa;
@@ -1103,6 +1170,7 @@ void init_kernel_attributes()
     cudaFuncSetAttribute(k_fused_ed, cudaFuncAttributeMaxDynamicSharedMemorySize, kFuSmemFixed + kMaxLen * 4);
     init_screen_attributes();
     cudaFuncSetAttribute(k_dtw, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(k_lbk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_seed_dist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
 }
 
@@ -1144,7 +1212,9 @@ void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, c
         k_refine_ed<<<num_sms() * 8, 256, iv.len * 4, s>>>(iv, qp, slot);
         if (launches) *launches += 1;
     } else {
-        k_lbk<<<num_sms() * 8, 256, iv.len * 8, s>>>(iv, qp, slot);
+        // per warp 4 rows of len floats (row / extrema), plus the query and its envelope
+        const int wpb = std::max(1, std::min(8, (int)((96 * 1024 - 12 * iv.len) / (16 * iv.len))));
+        k_lbk<<<num_sms() * 4, wpb * 32, (size_t)iv.len * 12 + (size_t)wpb * 16 * iv.len, s>>>(iv, qp, slot, wpb);
         if (!launch_dtw_thread<0>(iv, qp, slot, s)) {
             const int wpb = dtw_warps_per_block(iv.len);
             const size_t sm = (size_t)iv.len * 4 + (size_t)wpb * 3 * iv.len * 4;

@@ -100,9 +100,15 @@ void worker_loop(messi_server *srv, Worker *w)
             srv->cv_work.wait(lk, [&] { return srv->stop || !srv->arrivals.empty(); });
             if (srv->stop && srv->arrivals.empty()) return;
             // admit in arrival order: same (distance, window) as the oldest
-            // request, while the memory budget allows
-            const messi_dist d0 = srv->arrivals.front().dist;
-            const uint32_t w0 = srv->arrivals.front().window;
+            // request of this worker's preferred distance (worker 0 prefers ED,
+            // the others DTW, so ED batches never queue behind DTW batches),
+            // while the memory budget allows
+            const messi_dist pref = (w == srv->workers[0] || srv->workers.size() == 1) ? MESSI_ED : MESSI_DTW;
+            auto first = srv->arrivals.begin();
+            for (auto it = srv->arrivals.begin(); it != srv->arrivals.end(); ++it)
+                if (it->dist == pref) { first = it; break; }
+            const messi_dist d0 = first->dist;
+            const uint32_t w0 = first->window;
             for (auto it = srv->arrivals.begin(); it != srv->arrivals.end() && batch.size() < maxB;) {
                 if (it->dist == d0 && (d0 == MESSI_ED || it->window == w0)) {
                     if (!batch.empty() && srv->admitted_cost + it->cost > srv->cfg.mem_budget) break;

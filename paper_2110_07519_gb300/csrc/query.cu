@@ -619,10 +619,19 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
                     for (int t = lane; t < 256 && base + t < len; t += 32) {
                         const int idx = base + t;
                         const int lo = idx - r < 0 ? 0 : idx - r, hi = idx + r > len - 1 ? len - 1 : idx + r;
+                        // [lo, hi] spans at most two adjacent blocks.  Within one
+                        // block it starts at the block start (prefix extremum at
+                        // hi) or ends at the block end (suffix extremum at lo);
+                        // across two, the suffix of the first joins the prefix of
+                        // the second.
                         float U, L;
-                        if (lo == 0) { U = P[hi]; L = Pm[hi]; }
-                        else if (hi == len - 1) { U = S[lo]; L = Sm[lo]; }
-                        else { U = fmaxf(S[lo], P[hi]); L = fminf(Sm[lo], Pm[hi]); }
+                        if (lo / w == hi / w) {
+                            if (lo % w == 0) { U = P[hi]; L = Pm[hi]; }
+                            else { U = S[lo]; L = Sm[lo]; }
+                        } else {
+                            U = fmaxf(S[lo], P[hi]);
+                            L = fminf(Sm[lo], Pm[hi]);
+                        }
                         const float c = qs[idx];
                         float d = 0.f;
                         if (c > U) d = __fsub_rd(c, U);

@@ -188,6 +188,18 @@ def test_dtw_window_zero_equals_ed(m, dtw_set):
     assert np.array_equal(a[0].cpu().numpy(), b[0].cpu().numpy())
 
 
+@pytest.mark.parametrize("n,r", [(128, 12), (128, 5), (128, 30), (64, 7), (64, 20), (256, 40)])
+def test_dtw_window_shapes(m, n, r):
+    # windows whose 2r+1 blocks do not divide the length (series ends)
+    x = synth.random_walks(8000, n, seed=300 + n + r)
+    ix = m.messi_build(cuda(x), 16, 256, leaf_capacity=300)
+    q = np.concatenate([synth.random_walks(3, n, seed=301 + r), synth.noisy_members(x, 3, 1.0, seed=302 + r)[0]])
+    for k in (1, 4):
+        ids, d = m.messi_query(ix, cuda(q), k=k, dist=m.MESSI_DTW, window=r)
+        m.messi_check(ix)
+        check_knn(ids, d, *oracle.knn(x, q, k, oracle.DTW, r))
+
+
 def test_dtw_short_series_full_window(m):
     x = synth.random_walks(3000, 64, seed=71)
     ix = m.messi_build(cuda(x), 16, 256, leaf_capacity=50)

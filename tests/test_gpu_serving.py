@@ -66,9 +66,17 @@ def test_alone_equals_in_the_mix_and_oracle(m):
         k = reqs[i][1]
         while mixed[i] is None:
             mixed[i] = m.messi_server_poll(srv, tickets[i], k, wait_us=200_000)
-    for i in range(len(reqs)):
-        assert np.array_equal(alone[i][0], mixed[i][0]), i
-        assert np.array_equal(alone[i][1], mixed[i][1]), i
+    bad = [i for i in range(len(reqs))
+           if not (np.array_equal(alone[i][0], mixed[i][0]) and np.array_equal(alone[i][1], mixed[i][1]))]
+    if bad:
+        lines = []
+        for i in bad[:5]:
+            q, k, dist, r = reqs[i]
+            ref_ids, ref_d2 = oracle.knn(x, q, k, dist, r)
+            lines.append(f"req {i}: dist={dist} k={k} r={r}\n alone {alone[i][0].tolist()} {alone[i][1].tolist()}"
+                         f"\n mixed {mixed[i][0].tolist()} {mixed[i][1].tolist()}"
+                         f"\n oracle {ref_ids[0].tolist()} {np.sqrt(ref_d2[0]).tolist()}")
+        pytest.fail(f"{len(bad)} requests differ alone vs in the mix:\n" + "\n".join(lines))
     st = m.messi_server_get_stats(srv)
     assert st["completed"] == st["submitted"] == 2 * len(reqs)
     assert st["p99_ms"] >= st["p50_ms"] > 0

@@ -71,7 +71,10 @@ messi_status ensure_workspace(messi_index *ix, Workspace *ws)
     const size_t o_st = take(sizeof(QueryState));
     const size_t o_lut = take(kMaxSegments * kMaxCard * 4);
     const size_t o_q = take(len * 4), o_u = take(len * 4), o_l = take(len * 4);
-    const size_t o_karr = take(kMaxK * 8), o_log = take(kLogCap * 8), o_seed = take(kSeedMax * 8);
+    // every position is offered at most once on this path: a log of N + seed
+    // entries cannot overflow
+    const size_t log_cap = N + kSeedMax;
+    const size_t o_karr = take(kMaxK * 8), o_log = take(log_cap * 8), o_seed = take(kSeedMax * 8);
     const size_t o_sp = take(N * 4), o_sl = take(N * 4), o_s2 = take(N * 4);
     const size_t o_dtw = take(32 * 3 * len * 8);
     const size_t o_rc = take(kMaxScanGrid * 4);
@@ -99,6 +102,7 @@ messi_status ensure_workspace(messi_index *ix, Workspace *ws)
     s.dtw64 = reinterpret_cast<double *>(base + o_dtw);
     s.region_count = reinterpret_cast<unsigned *>(base + o_rc);
     s.acc = reinterpret_cast<QueryCounters *>(base + o_acc);
+    s.log_cap = (unsigned)std::min<size_t>(log_cap, 0xffffffffu);
     return MESSI_OK;
 }
 
@@ -116,7 +120,7 @@ messi_status ensure_batch_workspace(messi_index *ix, Workspace *ws, unsigned B)
     }
     const size_t len = ix->len;
     const size_t per = align256(sizeof(QueryState)) + align256(kMaxSegments * kMaxCard * 4) + 3 * align256(len * 4) +
-                       align256(kMaxK * 8) + align256(kLogCap * 8) + align256(kSeedMax * 8);
+                       align256(kMaxK * 8) + align256(kBatchLogCap * 8) + align256(kSeedMax * 8);
     const size_t head = align256(B * sizeof(QuerySlot)) + align256(64) + align256(sizeof(QueryCounters));
     char *base = nullptr;
     if (cudaMalloc(&base, head + per * B) != cudaSuccess) {
@@ -141,7 +145,8 @@ messi_status ensure_batch_workspace(messi_index *ix, Workspace *ws, unsigned B)
         q.U = reinterpret_cast<float *>(p); p += align256(len * 4);
         q.L = reinterpret_cast<float *>(p); p += align256(len * 4);
         q.karr = reinterpret_cast<unsigned long long *>(p); p += align256(kMaxK * 8);
-        q.log = reinterpret_cast<unsigned long long *>(p); p += align256(kLogCap * 8);
+        q.log = reinterpret_cast<unsigned long long *>(p); p += align256(kBatchLogCap * 8);
+        q.log_cap = kBatchLogCap;
         q.seedbuf = reinterpret_cast<unsigned long long *>(p); p += align256(kSeedMax * 8);
         q.acc = ws->bacc;
     }

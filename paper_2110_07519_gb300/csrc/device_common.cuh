@@ -307,7 +307,7 @@ static __device__ __noinline__ void offer(const QueryParams &qp, const QuerySlot
     const unsigned long long T = ld_volatile_u64(&st->thr);
     if (!(d2 <= prune_threshold(T, qp.F))) return;
     const unsigned li = atomicAdd(&st->log_count, 1u);
-    if (li < (unsigned)kLogCap) slot.log[li] = P;
+    if (li < slot.log_cap) slot.log[li] = P;
     if (P >= T) return;
     if (qp.k == 1) {
         const unsigned long long old = atomicMin(&st->thr, P);

@@ -29,7 +29,8 @@ constexpr int kMaxSegments = 16;
 constexpr int kMaxCard = 256;
 constexpr int kMaxLen = 4096;
 constexpr int kMaxK = 1024;
-constexpr int kLogCap = 8192;        // near-tie / accepted-candidate log per query
+constexpr int kLogCap = 8192;        // candidates the final step resolves at once (shared memory)
+constexpr int kBatchLogCap = 20480;  // log entries of a batched query slot
 constexpr int kSeedMax = 4096;       // series of the seed leaf refined up front
 constexpr unsigned long long kEmpty = ~0ull;   // packed "no candidate"
 constexpr int kMaxScanGrid = 2048;   // scan CTAs (each owns one survivor region)
@@ -71,7 +72,7 @@ struct QuerySlot {
     float *q;                   // [len] query
     float *U, *L;               // [len] LB_Keogh envelope (DTW)
     unsigned long long *karr;   // [kMaxK] sorted k best (k > 1)
-    unsigned long long *log;    // [kLogCap]
+    unsigned long long *log;    // [log_cap] accepted / near-tie candidates
     unsigned long long *seedbuf;// [kSeedMax]
     unsigned int *surv_pos;     // [N] (plain path only), region of scan CTA c
     float *surv_lb;             // [N]    starts at c * region_words
@@ -79,6 +80,7 @@ struct QuerySlot {
     unsigned int *surv2;        // [N]
     double *dtw64;              // [32 warps][3][len] FP64 DTW diagonals (finalize)
     QueryCounters *acc;         // per-call counter accumulator
+    unsigned log_cap;           // entries of `log`
 };
 
 // Parameters every query kernel needs, passed by value.

@@ -91,6 +91,7 @@ extern "C" messi_status messi_lower_bounds_noalloc(const messi_index *ix, const 
     slot.q = reinterpret_cast<float *>(b + kStateBytes + kLutBytes);
     slot.U = reinterpret_cast<float *>(b + kStateBytes + kLutBytes + kRowBytes);
     slot.L = reinterpret_cast<float *>(b + kStateBytes + kLutBytes + 2 * kRowBytes);
+    slot.log_cap = 0;   // no candidates are logged on this path
     // the array keeps the previous call's contents: the query state starts at zero
     if (!cuda_ok(cudaMemsetAsync(slot.st, 0, kStateBytes, s), "messi_lower_bounds_noalloc: clear state"))
         return MESSI_ECUDA;

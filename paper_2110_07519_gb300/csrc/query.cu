@@ -277,7 +277,7 @@ __device__ __forceinline__ void seed_select_body(const IndexView &iv, const Quer
     for (unsigned i = threadIdx.x; i < cnt; i += blockDim.x)
         if (cand_d2(buf[i]) <= band) {
             const unsigned li = atomicAdd(&nlog, 1u);
-            if (li < (unsigned)kLogCap) slot.log[li] = buf[i];
+            if (li < slot.log_cap) slot.log[li] = buf[i];
         }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1005,19 +1005,25 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
     const unsigned long long T = st->thr;
     const float band = prune_threshold(T, qp.F);
     const unsigned logged = st->log_count;
+    __shared__ int overflow;
     if (tid == 0) {
         ncand = 0;
         ambiguous = 0;
-        if (logged > (unsigned)kLogCap) atomicOr(iv.status, kStTieOverflow);
+        overflow = logged > slot.log_cap;
     }
     __syncthreads();
-    const unsigned nlog = min(logged, (unsigned)kLogCap);
+    const unsigned nlog = min(logged, slot.log_cap);
     for (unsigned i = tid; i < nlog; i += blockDim.x) {
         const unsigned long long P = slot.log[i];
-        if (cand_d2(P) <= band) cand[atomicAdd(&ncand, 1u)] = P;
+        if (cand_d2(P) <= band) {
+            const unsigned o = atomicAdd(&ncand, 1u);
+            if (o < (unsigned)kLogCap) cand[o] = P;
+            else overflow = 1;
+        }
     }
     __syncthreads();
-    const unsigned c = ncand;
+    if (tid == 0 && overflow) atomicOr(iv.status, kStTieOverflow);
+    const unsigned c = min(ncand, (unsigned)kLogCap);
     unsigned npow = 1;
     while (npow < c) npow <<= 1;
     for (unsigned i = c + tid; i < npow; i += blockDim.x) cand[i] = kEmpty;

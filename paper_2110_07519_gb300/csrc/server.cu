@@ -82,7 +82,7 @@ size_t request_cost(const messi_index *ix, uint32_t k)
 {
     // query row, result row and the per-query slot of the batch workspace
     // (table, state, k-array, near-tie log, seed buffer)
-    return (size_t)ix->len * 4 + (size_t)k * 12 + kMaxSegments * kMaxCard * 4 + kMaxK * 8 + kLogCap * 8 +
+    return (size_t)ix->len * 4 + (size_t)k * 12 + kMaxSegments * kMaxCard * 4 + kMaxK * 8 + kBatchLogCap * 8 +
            kSeedMax * 8 + 3 * (size_t)ix->len * 4 + 256;
 }
 

@@ -200,6 +200,19 @@ def test_dtw_window_shapes(m, n, r):
         check_knn(ids, d, *oracle.knn(x, q, k, oracle.DTW, r))
 
 
+def test_dtw_many_logged_candidates(m):
+    # fresh random-walk queries against 60K series: the first refinement wave
+    # accepts tens of thousands of candidates against a loose seed threshold,
+    # all of which the near-tie log must keep
+    x = synth.random_walks(60000, 128, seed=310)
+    ix = m.messi_build(cuda(x), 16, 256)
+    q = synth.random_walks(6, 128, seed=311)
+    for k in (1, 10):
+        ids, d = m.messi_query(ix, cuda(q), k=k, dist=m.MESSI_DTW, window=12)
+        m.messi_check(ix)
+        check_knn(ids, d, *oracle.knn(x, q, k, oracle.DTW, 12))
+
+
 def test_dtw_short_series_full_window(m):
     x = synth.random_walks(3000, 64, seed=71)
     ix = m.messi_build(cuda(x), 16, 256, leaf_capacity=50)

@@ -89,6 +89,7 @@ def test_alone_equals_in_the_mix_and_oracle(m):
         rel = np.abs(mixed[i][1] - np.sqrt(ref_d2[0])) / np.maximum(np.sqrt(ref_d2[0]), 1e-30)
         assert rel.max() <= 1e-5
     m.messi_server_destroy(srv)
+    m.messi_check(ix)
 
 
 def test_server_rejects_bad_requests(m):

@@ -177,6 +177,17 @@ def oracle_sample(data_t, queries_np, k, chunk=1 << 20, dist=0, r=0):
 
 
 # ------------------------------------------------------------ reference arm
+def mixed_order(qpool, rank):
+    """The query mix comes grouped by class (fresh, then each noise level); a
+    fixed permutation spreads the classes evenly over the steps."""
+    import torch
+
+    g = torch.Generator()
+    g.manual_seed(4242 + rank)
+    perm = torch.randperm(qpool.shape[0], generator=g).to(qpool.device)
+    return qpool.index_select(0, perm).contiguous()
+
+
 def run_reference(args, ws, rank, local):
     if rank != 0:
         return
@@ -189,7 +200,7 @@ def run_reference(args, ws, rank, local):
     torch.cuda.set_device(dev)
     oracle.build()
     data = synth.random_walks_torch(args.n, args.len, device=dev)
-    qpool = synth.query_mix_torch(data, args.warmup + args.steps, seed=synth.QUERY_SEED).cpu().numpy()
+    qpool = mixed_order(synth.query_mix_torch(data, args.warmup + args.steps, seed=synth.QUERY_SEED), 0).cpu().numpy()
     times = []
     threads = oracle.max_threads()
     for step in range(args.warmup + args.steps):
@@ -288,7 +299,7 @@ def run_messi(args, ws, rank, local):
     info = m.messi_index_get_info(ix)
     build_gbps = args.n * args.len * 4 / (info["build_ms"] * 1e-3) / 1e9
     if args.mix == "mixed":
-        qpool = synth.query_mix_torch(data, (W + K) * B, seed=synth.QUERY_SEED + rank)
+        qpool = mixed_order(synth.query_mix_torch(data, (W + K) * B, seed=synth.QUERY_SEED + rank), rank)
     elif args.mix == "fresh":
         qpool = synth.random_walks_torch((W + K) * B, args.len, seed=synth.QUERY_SEED + rank, device=dev)
     else:
@@ -415,7 +426,7 @@ def run_serve(args, ws, rank, local):
     n, length = args.serve_n, args.serve_len
     data = synth.random_walks_torch(n, length, seed=synth.DATASET_SEED + rank, device=dev)
     ix = m.messi_build(data, 16, 256)
-    pool = synth.query_mix_torch(data, 4096, seed=synth.QUERY_SEED).cpu().numpy()
+    pool = mixed_order(synth.query_mix_torch(data, 4096, seed=synth.QUERY_SEED), rank).cpu().numpy()
     del data
     torch.cuda.empty_cache()
     r_dtw = int(0.10 * length)

@@ -75,7 +75,8 @@ messi_status ensure_workspace(messi_index *ix, Workspace *ws)
     // entries cannot overflow
     const size_t log_cap = N + kSeedMax;
     const size_t o_karr = take(kMaxK * 8), o_log = take(log_cap * 8), o_seed = take(kSeedMax * 8);
-    const size_t o_sp = take(N * 4), o_sl = take(N * 4), o_s2 = take(N * 4);
+    const size_t o_sp = take(N * 4), o_sl = take(N * 4), o_s2 = take(N * 4), o_s2l = take(N * 4);
+    const size_t o_bk = take(2 * kOrderBuckets * 4);
     const size_t o_dtw = take(32 * 3 * len * 8);
     const size_t o_rc = take(kMaxScanGrid * 4);
     const size_t o_acc = take(sizeof(QueryCounters));
@@ -99,10 +100,15 @@ messi_status ensure_workspace(messi_index *ix, Workspace *ws)
     s.surv_pos = reinterpret_cast<unsigned *>(base + o_sp);
     s.surv_lb = reinterpret_cast<float *>(base + o_sl);
     s.surv2 = reinterpret_cast<unsigned *>(base + o_s2);
+    s.surv2_lb = reinterpret_cast<float *>(base + o_s2l);
+    s.bucket = reinterpret_cast<unsigned *>(base + o_bk);
     s.dtw64 = reinterpret_cast<double *>(base + o_dtw);
     s.region_count = reinterpret_cast<unsigned *>(base + o_rc);
     s.acc = reinterpret_cast<QueryCounters *>(base + o_acc);
     s.log_cap = (unsigned)std::min<size_t>(log_cap, 0xffffffffu);
+    // bucket counts start at zero; every ordering step leaves them cleared
+    if (!cuda_ok(cudaMemset(s.bucket, 0, kOrderBuckets * 4), "messi_query: clear the bound buckets"))
+        return MESSI_ECUDA;
     return MESSI_OK;
 }
 
@@ -156,6 +162,8 @@ messi_status ensure_batch_workspace(messi_index *ix, Workspace *ws, unsigned B)
     return MESSI_OK;
 }
 
+}  // namespace
+
 // f16 tile copy of the rows for the tensor-core screen (built on first use).
 messi_status ensure_screen_copy(messi_index *ix, cudaStream_t s)
 {
@@ -192,6 +200,8 @@ messi_status ensure_screen_copy(messi_index *ix, cudaStream_t s)
     ix->screen_state = 1;
     return MESSI_OK;
 }
+
+namespace {
 
 struct TcWs {
     __half *qtiles;

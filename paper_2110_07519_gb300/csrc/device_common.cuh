@@ -291,6 +291,12 @@ __device__ T warp_dtw(const float *__restrict__ q, const float *__restrict__ x, 
     return diag[(last % 3) * n + (n - 1)];
 }
 
+// ------------------------------------------------------- bound ordering
+// Bucket of a non-negative FP32 lower bound: its exponent and top 4 mantissa
+// bits, monotone in the bound.  order_floor(b) is the smallest bound in b.
+__device__ __forceinline__ unsigned order_bucket(float lb) { return (__float_as_uint(lb) & 0x7fffffffu) >> 19; }
+__device__ __forceinline__ float order_floor(unsigned b) { return __uint_as_float(b << 19); }
+
 // ------------------------------------------------------------------ offer
 // Present a computed candidate (squared FP32 distance, original id) to a
 // query's best-so-far.  Candidates within the near-tie band of the current
@@ -314,13 +320,19 @@ static __device__ __noinline__ void offer(const QueryParams &qp, const QuerySlot
         if (P < old) atomicAdd(&st->c.bsf_updates, 1ull);
         return;
     }
-    unsigned spins = 0;
+    // many threads can finish candidates at once (one candidate per thread):
+    // a waiter leaves as soon as the k-th best it would displace has dropped
+    // below it, and backs off exponentially so the holder's release is not
+    // queued behind a storm of failed exchanges
+    unsigned spins = 0, nap = 32;
     while (atomicCAS(&st->lock, 0u, 1u) != 0u) {
+        if (P >= ld_volatile_u64(&st->thr)) return;
         if (++spins > kSpinLimit) {
             atomicOr(status, kStTimeout);
             return;
         }
-        __nanosleep(64);
+        __nanosleep(nap);
+        if (nap < 2048) nap <<= 1;
     }
     __threadfence();
     volatile unsigned long long *ka = slot.karr;

@@ -31,6 +31,7 @@ constexpr int kMaxLen = 4096;
 constexpr int kMaxK = 1024;
 constexpr int kLogCap = 8192;        // candidates the final step resolves at once (shared memory)
 constexpr int kBatchLogCap = 20480;  // log entries of a batched query slot
+constexpr int kOrderBuckets = 4096;  // survivors bucketed by the top 12 bits of their FP32 bound
 constexpr int kSeedMax = 4096;       // series of the seed leaf refined up front
 constexpr unsigned long long kEmpty = ~0ull;   // packed "no candidate"
 constexpr int kMaxScanGrid = 2048;   // scan CTAs (each owns one survivor region)
@@ -61,6 +62,7 @@ struct QueryState {
     unsigned int invalid;       // non-finite query value seen
     unsigned int scan_grid;     // CTAs of the last scan: survivor regions
     unsigned int region_words;  // words (and survivor slots) per scan CTA
+    unsigned int ord_count;     // survivors in the bound-ordered list
     uint4 qkey;                 // interleaved key of the query word
     QueryCounters c;
 };
@@ -77,7 +79,9 @@ struct QuerySlot {
     unsigned int *surv_pos;     // [N] (plain path only), region of scan CTA c
     float *surv_lb;             // [N]    starts at c * region_words
     unsigned int *region_count; // [kMaxScanGrid] survivors found by each scan CTA
-    unsigned int *surv2;        // [N]
+    unsigned int *surv2;        // [N] compact LB_Keogh survivors, or the bound-ordered ED survivors
+    float *surv2_lb;            // [N] their lower bounds
+    unsigned int *bucket;       // [2][kOrderBuckets] bucket counts, then write cursors
     double *dtw64;              // [32 warps][3][len] FP64 DTW diagonals (finalize)
     QueryCounters *acc;         // per-call counter accumulator
     unsigned log_cap;           // entries of `log`
@@ -144,6 +148,14 @@ void free_workspace(Workspace &w);
 struct messi_index;
 namespace messi {
 // query paths on an explicit workspace (api.cu)
+// Builds the f16 screening copy of the rows if the index has none yet
+// (screen_state 0); leaves screen_state -1 where the rows cannot use it.
+messi_status ensure_screen_copy(messi_index *ix, cudaStream_t s);
+// Survivors of the scan (src 0: per-CTA regions of surv_pos / surv_lb) or of
+// LB_Keogh (src 1: surv2 / surv2_lb) written to dst_pos / dst_lb in
+// increasing order of lower-bound bucket; st->ord_count receives their number.
+void launch_order(const QueryParams &qp, const QuerySlot &slot, int src, unsigned *dst_pos, float *dst_lb,
+                  cudaStream_t s);
 messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uint32_t nq, uint32_t k,
                        messi_dist dist, uint32_t window, int64_t *ids, float *dists, messi_stream stream);
 messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, uint32_t nq, uint32_t k,

@@ -465,26 +465,25 @@ __global__ void __launch_bounds__(256)
 k_refine_ed(IndexView iv, QueryParams qp, QuerySlot slot)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ unsigned prefix[kMaxScanGrid + 1];
-    __shared__ unsigned counts[kMaxScanGrid];
     QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
     float *qs = reinterpret_cast<float *>(dsm);
     for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
-    const unsigned G = st->scan_grid;
-    const unsigned long long RW = st->region_words;
-    const unsigned nchunks = chunk_prefix(slot, G, prefix, counts);
+    __syncthreads();
+    // survivors in increasing lower-bound bucket: a warp takes chunks of 32
+    // and stops once a chunk's first (smallest) bucket lies above the threshold
+    const unsigned n = ld_volatile_u32(&st->ord_count);
+    const unsigned nchunks = (n + 31) >> 5;
     const int lane = threadIdx.x & 31;
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
     unsigned long long done = 0, aband = 0;
     for (unsigned ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += nw) {
-        const unsigned r = region_of(ch, prefix, G);
-        const unsigned within = (ch - prefix[r]) * 32 + lane;
-        const bool valid = within < counts[r];
-        const unsigned long long i = r * RW + within;
-        const unsigned pos = valid ? slot.surv_pos[i] : 0u;
-        const float lb = valid ? slot.surv_lb[i] : f_inf();
+        const unsigned i = ch * 32 + lane;
+        const bool valid = i < n;
+        const unsigned pos = valid ? slot.surv2[i] : 0u;
+        const float lb = valid ? slot.surv2_lb[i] : f_inf();
         float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        if (order_floor(order_bucket(__shfl_sync(0xffffffffu, lb, 0))) > thr) break;
         unsigned mask = __ballot_sync(0xffffffffu, valid && lb <= thr);
         while (mask) {
             const int a = __ffs(mask) - 1;
@@ -559,6 +558,7 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
     const unsigned nw = gridDim.x * wpb;
     unsigned long long pass = 0;
     unsigned pend = 0, npend = 0;          // passing positions, one per lane, flushed by 32
+    float pend_lb = 0.f;                   // and their LB_Keogh bounds
     for (unsigned ch = blockIdx.x * wpb + wib; ch < nchunks; ch += nw) {
         const unsigned rg = region_of(ch, prefix, G);
         const unsigned within = (ch - prefix[rg]) * 32 + lane;
@@ -574,7 +574,7 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
             const unsigned pa = __shfl_sync(0xffffffffu, pos, a);
             const float *x = iv.raw + (unsigned long long)pa * len;
             // candidate against the query's envelope
-            float acc = 0.f;
+            float acc = 0.f, lbv = 0.f;
             bool pruned = false;
             for (int base = 0; base < len && !pruned; base += 256) {
                 for (int t = lane; t < 256 && base + t < len; t += 32) {
@@ -586,7 +586,8 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
                     else if (c < Ls[idx]) d = __fsub_rd(Ls[idx], c);
                     acc = __fadd_rd(acc, __fmul_rd(d, d));
                 }
-                if (lbk_tail(acc) > thr) pruned = true;
+                lbv = lbk_tail(acc);
+                if (lbv > thr) pruned = true;
             }
             if (!pruned && r > 0) {
                 __syncwarp();
@@ -638,18 +639,24 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
                         else if (c < L) d = __fsub_rd(L, c);
                         acc2 = __fadd_rd(acc2, __fmul_rd(d, d));
                     }
-                    if (lbk_tail(acc2) > thr) pruned = true;
+                    const float lb2v = lbk_tail(acc2);
+                    if (lb2v > thr) pruned = true;
+                    lbv = fmaxf(lbv, lb2v);
                 }
             }
             __syncwarp();
             if (!pruned) {
                 ++pass;
-                if (lane == (int)npend) pend = pa;
+                if (lane == (int)npend) {
+                    pend = pa;
+                    pend_lb = lbv;
+                }
                 if (++npend == 32) {
                     unsigned o = 0;
                     if (lane == 0) o = atomicAdd(&st->surv2_count, 32u);
                     o = __shfl_sync(0xffffffffu, o, 0);
                     slot.surv2[o + lane] = pend;
+                    slot.surv2_lb[o + lane] = pend_lb;
                     npend = 0;
                 }
             }
@@ -659,7 +666,10 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
         unsigned o = 0;
         if (lane == 0) o = atomicAdd(&st->surv2_count, npend);
         o = __shfl_sync(0xffffffffu, o, 0);
-        if ((unsigned)lane < npend) slot.surv2[o + lane] = pend;
+        if ((unsigned)lane < npend) {
+            slot.surv2[o + lane] = pend;
+            slot.surv2_lb[o + lane] = pend_lb;
+        }
     }
     if (lane == 0 && pass) atomicAdd(&st->c.lbk_survivors, pass);
 }
@@ -676,12 +686,17 @@ k_dtw(IndexView iv, QueryParams qp, QuerySlot slot)
     float *diag = qs + iv.len + wib * 3 * iv.len;
     for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
     __syncthreads();
-    const unsigned count = ld_volatile_u32(&st->surv2_count);
+    const unsigned count = ld_volatile_u32(&st->ord_count);
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
     unsigned long long done = 0, aband = 0;
     for (unsigned i = blockIdx.x * (blockDim.x >> 5) + wib; i < count; i += nw) {
-        const unsigned pos = slot.surv2[i];
+        // bound-ordered list: once a bucket floor exceeds the threshold, so
+        // does everything later in this warp's sequence
+        const unsigned pos = slot.surv_pos[i];
+        const float lb = slot.surv_lb[i];
         const float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        if (order_floor(order_bucket(lb)) > thr) break;
+        if (lb > thr) continue;
         const float d2 = warp_dtw<float>(qs, iv.raw + (unsigned long long)pos * iv.len, iv.len, qp.r, diag, thr);
         if (d2 > thr) { ++aband; continue; }
         ++done;
@@ -907,12 +922,19 @@ k_dtw_thread(IndexView iv, QueryParams qp, QuerySlot slot)
     for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
     __syncthreads();
     const unsigned lo = MODE ? st->seed_lo : 0u;
-    const unsigned count = MODE ? st->seed_hi - st->seed_lo : ld_volatile_u32(&st->surv2_count);
+    const unsigned count = MODE ? st->seed_hi - st->seed_lo : ld_volatile_u32(&st->ord_count);
     const unsigned T = gridDim.x * blockDim.x;
     unsigned long long done = 0, aband = 0;
     for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += T) {
-        const unsigned pos = MODE ? lo + e : slot.surv2[e];
+        const unsigned pos = MODE ? lo + e : slot.surv_pos[e];
         const float thr = MODE ? f_inf() : prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        if (!MODE) {
+            // bound-ordered list: this thread's later candidates lie in the
+            // same or higher buckets
+            const float lb = slot.surv_lb[e];
+            if (order_floor(order_bucket(lb)) > thr) break;
+            if (lb > thr) continue;
+        }
         const float d2 = thread_dtw<R>(qs, iv.raw + (unsigned long long)pos * iv.len, iv.len, qp.r, thr);
         if (MODE) {
             slot.seedbuf[e] = pack_cand(d2, iv.ids[pos]);
@@ -1224,18 +1246,20 @@ void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, c
                    unsigned long long *launches)
 {
     if (qp.dist == 0) {
+        launch_order(qp, slot, 0, slot.surv2, slot.surv2_lb, s);
         k_refine_ed<<<num_sms() * 8, 256, iv.len * 4, s>>>(iv, qp, slot);
-        if (launches) *launches += 1;
+        if (launches) *launches += 4;
     } else {
         // per warp 4 rows of len floats (row / extrema), plus the query and its envelope
         const int wpb = std::max(1, std::min(8, (int)((96 * 1024 - 12 * iv.len) / (16 * iv.len))));
         k_lbk<<<num_sms() * 4, wpb * 32, (size_t)iv.len * 12 + (size_t)wpb * 16 * iv.len, s>>>(iv, qp, slot, wpb);
+        launch_order(qp, slot, 1, slot.surv_pos, slot.surv_lb, s);
         if (!launch_dtw_thread<0>(iv, qp, slot, s)) {
             const int wpb = dtw_warps_per_block(iv.len);
             const size_t sm = (size_t)iv.len * 4 + (size_t)wpb * 3 * iv.len * 4;
             k_dtw<<<num_sms() * 4, wpb * 32, sm, s>>>(iv, qp, slot);
         }
-        if (launches) *launches += 2;
+        if (launches) *launches += 5;
     }
 }
 

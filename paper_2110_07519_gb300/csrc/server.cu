@@ -201,11 +201,10 @@ messi_status messi_server_create(messi_index *ix, const messi_server_config *cfg
         srv->cfg.mem_budget = (uint64_t)srv->cfg.streams * srv->cfg.max_batch * request_cost(ix, srv->cfg.max_k);
     cudaSetDevice(ix->device);
     // build the screening copy now, before several workers could race to do it
-    {
-        int64_t ids[1];
-        float d[1];
-        std::vector<float> q(ix->len, 0.f);
-        messi_status st = messi_query_batched(ix, q.data(), 1, 1, MESSI_ED, 0, 1, ids, d, nullptr);
+    if (ix->batch_mode == 1) {
+        messi_status st = ensure_screen_copy(ix, nullptr);
+        if (st == MESSI_OK && !cuda_ok(cudaStreamSynchronize(nullptr), "messi_server_create: screening copy"))
+            st = MESSI_ECUDA;
         if (st != MESSI_OK) {
             delete srv;
             return st;

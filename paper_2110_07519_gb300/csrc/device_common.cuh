@@ -97,6 +97,29 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+// Non-blocking probe of a phase.
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for a thread that also issues tensor-core work: try_wait can
+// hold the issuing thread for hundreds of cycles even on a completed phase,
+// so the phase is probed with test_wait first and try_wait only takes over
+// for long waits.
+__device__ __forceinline__ bool mbar_wait_issuer(unsigned long long *bar, unsigned parity)
+{
+    for (unsigned it = 0; it < 4096; ++it)
+        if (mbar_test_wait(bar, parity)) return true;
+    return mbar_wait_bounded(bar, parity);
+}
 
 // ------------------------------------------------------ iSAX lower bound
 // Squared lower bound of one iSAX word: sum over segments of the table entry

@@ -201,8 +201,11 @@ struct ScreenArgs {
 
 // Operand roles: A = a query tile (M = 128 queries, TMEM lane = query), B = a
 // tile of 128 series (N = 128, TMEM column = series).  Warp-specialised:
-//   warp 8 (producer)  streams the series tiles as K-chunks through an NS-deep
-//                      ring of shared-memory stages with TMA bulk copies;
+//   warps 8, 10        (producers) stream the series tiles as K-chunks through
+//                      an NS-deep ring of shared-memory stages with TMA bulk
+//                      copies, taking alternate chunks: one thread's bulk
+//                      copies complete one after another, two threads keep
+//                      twice as many in flight;
 //   warp 9 (MMA)       issues tcgen05 MMAs chunk by chunk (one MMA per query
 //                      tile and 16-wide k step), commits each chunk to free its
 //                      stage and each finished tile to its accumulator buffer;
@@ -210,13 +213,54 @@ struct ScreenArgs {
 //                      every (query, series) pair.
 // A CTA owns QPC (1 or 2) query tiles, so each series tile read from L2 serves
 // QPC * 128 queries.  An epilogue thread owns one query, whose constants stay
-// in registers; the candidate test, rearranged so that only one per-series
-// pair of constants is needed,
-//     lower <= U  <=>  xnorm * alpha + (2 c - xn (1 - kappa'))  >=  qn - gamma' - U
-// costs two FMAs and a compare; a warp vote skips the rare candidate path.
-// The extra 8u in kappa' and gamma' covers the rounding of this form.
+// in registers.  The candidate test, rearranged so that only per-series
+// constants meet the accumulator,
+//     lower <= U  <=>  xnorm * alpha + (2 c - xn (1 - kappa'))  >=  qn - gamma' - U,
+// is first applied with alpha replaced by the largest alpha of the CTA's
+// queries (xnorm >= 0, so the left side only grows): one per-series constant
+//     r = xnorm * alpha_max - xn (1 - kappa')   (rounded up)
+// read four at a time as a shared-memory broadcast, then one FMA (rounded up)
+// and a compare per pair.  A warp vote skips the rare path, which re-tests
+// the pair with its own query's alpha before taking it as a candidate.  The
+// extra 8u in kappa' and gamma' covers the rounding of the exact form.  The
+// tensor core reads both operands from shared memory at close to the full
+// shared-memory bandwidth, so the epilogue keeps its own shared-memory
+// traffic to one broadcast per four pairs.
 constexpr int kTcEpiWarps = 8;
-constexpr int kTcCtrlThreads = kTcEpiWarps * 32 + 64;     // + producer warp + MMA warp
+constexpr int kTcCtrlThreads = kTcEpiWarps * 32 + 96;     // + 2 producer warps + MMA warp
+constexpr int kTcProdWarp0 = kTcEpiWarps, kTcMmaWarp = kTcEpiWarps + 1, kTcProdWarp1 = kTcEpiWarps + 2;
+
+// Two 32-column TMEM loads under one wait.
+__device__ __forceinline__ void tmem_ld64(unsigned taddr, float (&v)[64])
+{
+    unsigned r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr + 32u)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Named barrier over the 256 epilogue threads.
+__device__ __forceinline__ void epi_bar_sync() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
 
 // Named barrier of the 256 epilogue threads that also ORs a predicate over
 // them, so a bounded wait that ran out in one warp stops all of them at once.
@@ -234,6 +278,57 @@ __device__ __forceinline__ bool epi_bar_any(bool v)
     return r != 0;
 }
 
+// Rare path of the epilogue: the pair (query qj, series row) passed the test
+// with the CTA's largest alpha; re-test it with the query's own alpha, record
+// it as a candidate, and for k = 1 lower the query's bound U with the upper
+// end of its estimate.  Returns the (possibly lowered) U.
+struct CandidateSink {
+    const float *xn, *xnorm;
+    unsigned *cand_count, *cand_pos, *Ubits;
+    unsigned long long N;
+    unsigned cap;
+    int k;
+};
+
+__device__ __noinline__ float screen_candidate(CandidateSink a, unsigned qj, unsigned long long row, float acc,
+                                               float qn, float alpha, float gamma, float E, float U)
+{
+    if (row >= a.N) return U;
+    const float one_m_kappa = 1.f - kKappaP;
+    const float xn = a.xn[row], xnrm = a.xnorm[row];
+    const float lhs = fmaf(xnrm, alpha, fmaf(2.f, acc, -xn * one_m_kappa));
+    if (!(lhs >= E)) return U;
+    const unsigned o = atomicAdd(&a.cand_count[qj], 1u);
+    if (o < a.cap) a.cand_pos[(unsigned long long)qj * a.cap + o] = (unsigned)row;
+    if (a.k == 1) {
+        // upper end of the estimate: s + eps, rounded up
+        const float shat = fmaf(-2.f, acc, xn + qn);
+        const float eps = fmaf(xnrm, alpha, gamma + kKappaP * xn);
+        const float up = fmaxf(__fmul_ru(__fadd_ru(shat, eps), 1.0000003f), 0.f);
+        if (up < U) {
+            atomicMin(&a.Ubits[qj], __float_as_uint(up));
+            return up;
+        }
+    }
+    return U;
+}
+
+// One chunk of KS 16-wide k-steps for NQ query tiles sharing the series
+// operand; k-step kk starts kk * 256 bytes further in both operands.
+template <int KS, int NQ>
+__device__ __forceinline__ void mma_chunk(unsigned d, unsigned long long ad, unsigned long long bd, unsigned qstride16,
+                                          unsigned idesc, bool accumulate)
+{
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk)
+#pragma unroll
+        for (int qi = 0; qi < NQ; ++qi)
+            tc_mma_f16(d + qi * 128, ad + qi * qstride16 + kk * 16u, bd + kk * 16u, idesc,
+                       (kk > 0 || accumulate) ? 1u : 0u);
+}
+
+// KS = chunk width / 16 (1, 2 or 4)
+template <int KS>
 __global__ void __launch_bounds__(kTcCtrlThreads, 1)
 k_tc_screen(ScreenArgs a)
 {
@@ -241,10 +336,12 @@ k_tc_screen(ScreenArgs a)
     __shared__ __align__(8) unsigned long long bar_full[kTcMaxStages], bar_empty[kTcMaxStages];
     __shared__ __align__(8) unsigned long long bar_accf[2], bar_acce[2], bar_q;
     __shared__ unsigned tmem_base;
-    __shared__ float2 rowc[2][kTcRows];     // (-xn (1 - kappa'), xnorm) per accumulator buffer
+    __shared__ __align__(16) float rowr[2][kTcRows];   // xnorm alpha_max - xn (1 - kappa') per buffer
+    __shared__ unsigned s_amax;                       // bits of the CTA's largest alpha
     __shared__ int s_fail;
     const unsigned len = a.len;
-    const unsigned ck = chunk_k(len), nch = len / ck;
+    constexpr unsigned ck = KS * 16;
+    const unsigned nch = len / ck;
     const unsigned chunk_bytes = kTcRows * ck * 2;
     const unsigned qtile_bytes = kTcQ * len * 2;
     const unsigned QPC = a.qpc, NS = a.stages;
@@ -262,6 +359,7 @@ k_tc_screen(ScreenArgs a)
     if (warp == 0) tmem_alloc(&tmem_base, 512);
     if (tid == 0) {
         s_fail = 0;
+        s_amax = 0u;
         for (unsigned i = 0; i < NS; ++i) {
             mbar_init(&bar_full[i], 1);
             mbar_init(&bar_empty[i], 1);
@@ -280,54 +378,75 @@ k_tc_screen(ScreenArgs a)
     const unsigned tmem = tmem_base;
     const unsigned acc_cols = QPC * 128;                      // columns of one accumulator buffer
 
-    if (warp == kTcEpiWarps) {
-        // ------------------------------------------------ producer
+    if (warp == kTcProdWarp0 || warp == kTcProdWarp1) {
+        // ------------------------------------------------ producers
+        const unsigned p = (warp == kTcProdWarp0) ? 0u : 1u;
         if (lane == 0 && nt > 0) {
-            mbar_arrive_expect_tx(&bar_q, nq * qtile_bytes);
-            for (unsigned qi = 0; qi < nq; ++qi)
-                bulk_g2s(qbuf + qi * qtile_bytes,
-                         reinterpret_cast<const unsigned char *>(a.qtiles) + (unsigned long long)(qt0 + qi) * qtile_bytes,
-                         qtile_bytes, &bar_q);
+            if (p == 0) {
+                mbar_arrive_expect_tx(&bar_q, nq * qtile_bytes);
+                for (unsigned qi = 0; qi < nq; ++qi)
+                    bulk_g2s(qbuf + qi * qtile_bytes,
+                             reinterpret_cast<const unsigned char *>(a.qtiles) +
+                                 (unsigned long long)(qt0 + qi) * qtile_bytes,
+                             qtile_bytes, &bar_q);
+            }
+            // chunk n = p, p + 2, ...: ring stage st = n mod NS in use u = n / NS
+            // (a stage in use u > 0 waits for its release in use u - 1), and
+            // series tile j, chunk c of the chunk sequence, all advanced by 2
             const unsigned long long total = nt * nch;
-            for (unsigned long long n = 0; n < total && !s_fail; ++n) {
-                const unsigned st = (unsigned)(n % NS);
-                const unsigned long long use = n / NS;
-                if (use > 0 && !mbar_wait_bounded(&bar_empty[st], (unsigned)((use - 1) & 1))) {
+            unsigned st = p, u = 0, c = p % nch;
+            unsigned long long j = p / nch;
+            for (unsigned long long n = p; n < total && !s_fail; n += 2) {
+                if (u > 0 && !mbar_wait_issuer(&bar_empty[st], (u - 1u) & 1u)) {
                     s_fail = 1;
                     break;
                 }
-                const unsigned long long j = n / nch, c = n % nch;
                 const unsigned long long rt = g + j * groups;
                 mbar_arrive_expect_tx(&bar_full[st], chunk_bytes);
                 bulk_g2s(ring + st * chunk_bytes,
                          reinterpret_cast<const unsigned char *>(a.rtiles) + (rt * nch + c) * chunk_bytes, chunk_bytes,
                          &bar_full[st]);
+                st += 2;
+                while (st >= NS) {
+                    st -= NS;
+                    ++u;
+                }
+                c += 2;
+                while (c >= nch) {
+                    c -= nch;
+                    ++j;
+                }
             }
         }
-    } else if (warp == kTcEpiWarps + 1) {
+    } else if (warp == kTcMmaWarp) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0 && nt > 0) {
             const unsigned idesc = tc_idesc_f16(kTcQ, kTcRows);
             const unsigned sq = smem_u32(qbuf), sr = smem_u32(ring);
             const unsigned sbo_q = (len / 8) * 128, sbo_r = (ck / 8) * 128;
+            // descriptors of k-step 0 of query tile 0 and of ring stage 0; the
+            // others differ only in the start-address field (address >> 4,
+            // bits 0-13), reached by plain adds since every shared-memory
+            // address here is below 256 KB
+            const unsigned long long ad0 = tc_desc(sq, 128, sbo_q), bd0 = tc_desc(sr, 128, sbo_r);
+            const unsigned qstride16 = qtile_bytes >> 4, cstride16 = chunk_bytes >> 4;
             bool ok = mbar_wait_bounded(&bar_q, 0);
+            unsigned st = 0, fpar = 0;          // ring stage and the parity of its current fill
             for (unsigned long long j = 0; j < nt && ok && !s_fail; ++j) {
                 const unsigned ab = (unsigned)(j & 1);
-                if (j >= 2 && !mbar_wait_bounded(&bar_acce[ab], (unsigned)(((j >> 1) - 1) & 1))) { ok = false; break; }
+                if (j >= 2 && !mbar_wait_issuer(&bar_acce[ab], (unsigned)(((j >> 1) - 1) & 1))) { ok = false; break; }
                 tc_fence_after();
                 for (unsigned c = 0; c < nch; ++c) {
-                    const unsigned long long n = j * nch + c;
-                    const unsigned st = (unsigned)(n % NS);
-                    if (!mbar_wait_bounded(&bar_full[st], (unsigned)((n / NS) & 1))) { ok = false; break; }
+                    if (!mbar_wait_issuer(&bar_full[st], fpar)) { ok = false; break; }
                     tc_fence_after();
-                    for (unsigned kk = 0; kk < ck / 16; ++kk) {
-                        const unsigned long long bdesc = tc_desc(sr + st * chunk_bytes + kk * 256, 128, sbo_r);
-                        for (unsigned qi = 0; qi < nq; ++qi)
-                            tc_mma_f16(tmem + ab * acc_cols + qi * 128,
-                                       tc_desc(sq + qi * qtile_bytes + (c * (ck / 16) + kk) * 256, 128, sbo_q), bdesc,
-                                       idesc, (c | kk) != 0);
-                    }
+                    const unsigned long long ad = ad0 + c * (KS * 16u), bd = bd0 + st * cstride16;
+                    if (nq == 2) mma_chunk<KS, 2>(tmem + ab * acc_cols, ad, bd, qstride16, idesc, c != 0);
+                    else mma_chunk<KS, 1>(tmem + ab * acc_cols, ad, bd, qstride16, idesc, c != 0);
                     tc_commit(&bar_empty[st]);
+                    if (++st == NS) {
+                        st = 0;
+                        fpar ^= 1u;
+                    }
                 }
                 if (!ok) break;
                 tc_commit(&bar_accf[ab]);
@@ -345,8 +464,13 @@ k_tc_screen(ScreenArgs a)
         const float gamma = have ? a.qconst[4 * qj + 2] : 0.f;
         const bool act = have && a.active[qj] != 0;
         float U = have ? __uint_as_float(a.Ubits[qj]) : -1.f;
-        float E = act ? qn - gamma - U : __int_as_float(0x7f800000);
+        float E = act ? __fsub_rd(__fsub_rd(qn, gamma), U) : __int_as_float(0x7f800000);
         const float one_m_kappa = 1.f - kKappaP;
+        // alpha >= 0: its bits order like the values
+        if (act) atomicMax(&s_amax, __float_as_uint(alpha));
+        epi_bar_sync();
+        const float amax = __uint_as_float(s_amax);
+        const CandidateSink sink{a.xn, a.xnorm, a.cand_count, a.cand_pos, a.Ubits, a.N, a.cap, a.k};
         // columns of this warp in an accumulator buffer: QPC = 2: all 128 series of
         // its query tile; QPC = 1: half of them
         const unsigned cbeg = (QPC == 2) ? qi * 128 : (unsigned)(warp >> 2) * 64;
@@ -364,45 +488,35 @@ k_tc_screen(ScreenArgs a)
         for (unsigned long long j = 0; j < nt; ++j) {
             const unsigned ab = (unsigned)(j & 1);
             const unsigned long long rt = g + j * groups;
-            if (tid < kTcRows) rowc[ab][tid] = make_float2(-nxt_xn * one_m_kappa, nxt_nrm);
+            if (tid < kTcRows) rowr[ab][tid] = __fmaf_ru(nxt_nrm, amax, __fmul_ru(-nxt_xn, one_m_kappa));
             fetch_norms(j + 1);
             const bool okw = mbar_wait_bounded(&bar_accf[ab], (unsigned)((j >> 1) & 1));
-            // also the barrier that publishes rowc to all epilogue warps
+            // also the barrier that publishes rowr to all epilogue warps
             if (epi_bar_any(!okw)) {
                 s_fail = 1;
                 break;
             }
             tc_fence_after();
-            for (unsigned h = 0; h < ncol; h += 32) {
-                float acc[32];
-                tmem_ld32(tmem + ((unsigned)((warp & 3) * 32) << 16) + ab * acc_cols + cbeg + h, acc);
+            for (unsigned h = 0; h < ncol; h += 64) {
+                float acc[64];
+                tmem_ld64(tmem + ((unsigned)((warp & 3) * 32) << 16) + ab * acc_cols + cbeg + h, acc);
+                const float4 *r4 = reinterpret_cast<const float4 *>(&rowr[ab][rbeg + h]);
                 bool hit = false;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const float2 rc = rowc[ab][rbeg + h + i];
-                    const float lhs = fmaf(rc.y, alpha, fmaf(2.f, acc[i], rc.x));
-                    hit |= lhs >= E;
+                for (int i = 0; i < 16; ++i) {
+                    const float4 r = r4[i];
+                    hit |= __fmaf_ru(2.f, acc[4 * i + 0], r.x) >= E;
+                    hit |= __fmaf_ru(2.f, acc[4 * i + 1], r.y) >= E;
+                    hit |= __fmaf_ru(2.f, acc[4 * i + 2], r.z) >= E;
+                    hit |= __fmaf_ru(2.f, acc[4 * i + 3], r.w) >= E;
                 }
                 if (__any_sync(0xffffffffu, hit)) {
-                    for (int i = 0; i < 32; ++i) {
-                        const float2 rc = rowc[ab][rbeg + h + i];
-                        const float lhs = fmaf(rc.y, alpha, fmaf(2.f, acc[i], rc.x));
-                        if (!(lhs >= E)) continue;
-                        const unsigned long long row = rt * kTcRows + rbeg + h + i;
-                        if (row >= a.N) continue;
-                        const unsigned o = atomicAdd(&a.cand_count[qj], 1u);
-                        if (o < a.cap) a.cand_pos[(unsigned long long)qj * a.cap + o] = (unsigned)row;
-                        if (a.k == 1) {
-                            // upper end of the estimate: s + eps, rounded up
-                            const float xn = a.xn[row];
-                            const float shat = fmaf(-2.f, acc[i], xn + qn);
-                            const float eps = fmaf(rc.y, alpha, gamma + kKappaP * xn);
-                            const float up = fmaxf(__fmul_ru(__fadd_ru(shat, eps), 1.0000003f), 0.f);
-                            if (up < U) {
-                                U = up;
-                                E = qn - gamma - U;
-                                atomicMin(&a.Ubits[qj], __float_as_uint(up));
-                            }
+                    // unrolled so the accumulators stay in registers
+#pragma unroll
+                    for (int i = 0; i < 64; ++i) {
+                        if (__fmaf_ru(2.f, acc[i], rowr[ab][rbeg + h + i]) >= E) {
+                            U = screen_candidate(sink, qj, rt * kTcRows + rbeg + h + i, acc[i], qn, alpha, gamma, E, U);
+                            E = __fsub_rd(__fsub_rd(qn, gamma), U);
                         }
                     }
                 }
@@ -415,7 +529,7 @@ k_tc_screen(ScreenArgs a)
                 const float G = __uint_as_float(ld_volatile_u32(&a.Ubits[qj]));
                 if (G < U) {
                     U = G;
-                    E = qn - gamma - U;
+                    E = __fsub_rd(__fsub_rd(qn, gamma), U);
                 }
             }
         }
@@ -542,7 +656,9 @@ unsigned screen_stages(int len, unsigned qpc)
 
 void init_screen_attributes()
 {
-    cudaFuncSetAttribute(k_tc_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBudget);
+    cudaFuncSetAttribute(k_tc_screen<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBudget);
+    cudaFuncSetAttribute(k_tc_screen<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBudget);
+    cudaFuncSetAttribute(k_tc_screen<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBudget);
 }
 
 void launch_make_screen_copy(const float *raw, unsigned long long N, int len, __half *tiles, float *xn, float *xnorm,
@@ -594,7 +710,10 @@ void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm,
     a.stages = screen_stages(len, a.qpc);
     const unsigned QG = (a.QT + a.qpc - 1) / a.qpc;
     const unsigned groups = std::max(1u, (unsigned)num_sms() / QG);
-    k_tc_screen<<<groups * QG, kTcCtrlThreads, screen_smem_bytes(len), s>>>(a);
+    const unsigned ks = chunk_k((unsigned)len) / 16;
+    if (ks == 4) k_tc_screen<4><<<groups * QG, kTcCtrlThreads, screen_smem_bytes(len), s>>>(a);
+    else if (ks == 2) k_tc_screen<2><<<groups * QG, kTcCtrlThreads, screen_smem_bytes(len), s>>>(a);
+    else k_tc_screen<1><<<groups * QG, kTcCtrlThreads, screen_smem_bytes(len), s>>>(a);
 }
 
 void launch_tc_recheck(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots, unsigned B,

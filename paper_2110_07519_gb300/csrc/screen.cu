@@ -209,6 +209,12 @@ struct ScreenArgs {
 //   warp 9 (MMA)       issues tcgen05 MMAs chunk by chunk (one MMA per query
 //                      tile and 16-wide k step), commits each chunk to free its
 //                      stage and each finished tile to its accumulator buffer;
+//   warp 11 (relay)    waits on the mbarriers the MMA warp depends on (chunk
+//                      loaded, accumulator buffer drained) and meets the MMA
+//                      warp at a named barrier once per chunk: an mbarrier
+//                      wait in the thread that issues the MMAs costs it
+//                      hundreds of cycles even when the phase is complete,
+//                      a named barrier does not;
 //   warps 0-7          read accumulators from TMEM (double-buffered) and test
 //                      every (query, series) pair.
 // A CTA owns QPC (1 or 2) query tiles, so each series tile read from L2 serves
@@ -227,8 +233,12 @@ struct ScreenArgs {
 // shared-memory bandwidth, so the epilogue keeps its own shared-memory
 // traffic to one broadcast per four pairs.
 constexpr int kTcEpiWarps = 8;
-constexpr int kTcCtrlThreads = kTcEpiWarps * 32 + 96;     // + 2 producer warps + MMA warp
-constexpr int kTcProdWarp0 = kTcEpiWarps, kTcMmaWarp = kTcEpiWarps + 1, kTcProdWarp1 = kTcEpiWarps + 2;
+constexpr int kTcCtrlThreads = kTcEpiWarps * 32 + 128;    // + 2 producer warps + MMA warp + relay warp
+constexpr int kTcProdWarp0 = kTcEpiWarps, kTcMmaWarp = kTcEpiWarps + 1, kTcProdWarp1 = kTcEpiWarps + 2,
+              kTcRelayWarp = kTcEpiWarps + 3;
+
+// Named barrier 3: the MMA warp and the relay warp, once per chunk.
+__device__ __forceinline__ void relay_bar_sync() { asm volatile("bar.sync 3, 64;" ::: "memory"); }
 
 // Two 32-column TMEM loads under one wait.
 __device__ __forceinline__ void tmem_ld64(unsigned taddr, float (&v)[64])
@@ -338,7 +348,7 @@ k_tc_screen(ScreenArgs a)
     __shared__ unsigned tmem_base;
     __shared__ __align__(16) float rowr[2][kTcRows];   // xnorm alpha_max - xn (1 - kappa') per buffer
     __shared__ unsigned s_amax;                       // bits of the CTA's largest alpha
-    __shared__ int s_fail;
+    __shared__ volatile int s_fail;
     const unsigned len = a.len;
     constexpr unsigned ck = KS * 16;
     const unsigned nch = len / ck;
@@ -420,7 +430,10 @@ k_tc_screen(ScreenArgs a)
         }
     } else if (warp == kTcMmaWarp) {
         // ------------------------------------------------ MMA issuer
-        if (lane == 0 && nt > 0) {
+        // The whole warp meets the relay once per chunk (so neither warp can
+        // wait at the named barrier for one that has left: both run every
+        // iteration, and after a failure lane 0 only stops issuing).
+        if (nt > 0) {
             const unsigned idesc = tc_idesc_f16(kTcQ, kTcRows);
             const unsigned sq = smem_u32(qbuf), sr = smem_u32(ring);
             const unsigned sbo_q = (len / 8) * 128, sbo_r = (ck / 8) * 128;
@@ -430,28 +443,46 @@ k_tc_screen(ScreenArgs a)
             // address here is below 256 KB
             const unsigned long long ad0 = tc_desc(sq, 128, sbo_q), bd0 = tc_desc(sr, 128, sbo_r);
             const unsigned qstride16 = qtile_bytes >> 4, cstride16 = chunk_bytes >> 4;
-            bool ok = mbar_wait_bounded(&bar_q, 0);
-            unsigned st = 0, fpar = 0;          // ring stage and the parity of its current fill
-            for (unsigned long long j = 0; j < nt && ok && !s_fail; ++j) {
+            unsigned st = 0;
+            for (unsigned long long j = 0; j < nt; ++j) {
                 const unsigned ab = (unsigned)(j & 1);
-                if (j >= 2 && !mbar_wait_issuer(&bar_acce[ab], (unsigned)(((j >> 1) - 1) & 1))) { ok = false; break; }
-                tc_fence_after();
                 for (unsigned c = 0; c < nch; ++c) {
-                    if (!mbar_wait_issuer(&bar_full[st], fpar)) { ok = false; break; }
+                    relay_bar_sync();
                     tc_fence_after();
-                    const unsigned long long ad = ad0 + c * (KS * 16u), bd = bd0 + st * cstride16;
-                    if (nq == 2) mma_chunk<KS, 2>(tmem + ab * acc_cols, ad, bd, qstride16, idesc, c != 0);
-                    else mma_chunk<KS, 1>(tmem + ab * acc_cols, ad, bd, qstride16, idesc, c != 0);
-                    tc_commit(&bar_empty[st]);
+                    if (lane == 0 && !s_fail) {
+                        const unsigned long long ad = ad0 + c * (KS * 16u), bd = bd0 + st * cstride16;
+                        if (nq == 2) mma_chunk<KS, 2>(tmem + ab * acc_cols, ad, bd, qstride16, idesc, c != 0);
+                        else mma_chunk<KS, 1>(tmem + ab * acc_cols, ad, bd, qstride16, idesc, c != 0);
+                        tc_commit(&bar_empty[st]);
+                    }
+                    __syncwarp();
+                    if (++st == NS) st = 0;
+                }
+                if (lane == 0 && !s_fail) tc_commit(&bar_accf[ab]);
+                __syncwarp();
+            }
+        }
+    } else if (warp == kTcRelayWarp) {
+        // ------------------------------------------------ relay
+        if (nt > 0) {
+            if (lane == 0 && !mbar_wait_bounded(&bar_q, 0)) s_fail = 1;
+            unsigned st = 0, fpar = 0;          // ring stage and the parity of its current fill
+            for (unsigned long long j = 0; j < nt; ++j) {
+                const unsigned ab = (unsigned)(j & 1);
+                // accumulator buffer ab drained by the epilogue (tile j - 2)
+                if (lane == 0 && j >= 2 && !s_fail &&
+                    !mbar_wait_bounded(&bar_acce[ab], (unsigned)(((j >> 1) - 1) & 1)))
+                    s_fail = 1;
+                for (unsigned c = 0; c < nch; ++c) {
+                    if (lane == 0 && !s_fail && !mbar_wait_bounded(&bar_full[st], fpar)) s_fail = 1;
+                    __syncwarp();
+                    relay_bar_sync();
                     if (++st == NS) {
                         st = 0;
                         fpar ^= 1u;
                     }
                 }
-                if (!ok) break;
-                tc_commit(&bar_accf[ab]);
             }
-            if (!ok) s_fail = 1;
         }
     } else {
         // ------------------------------------------------ epilogue

@@ -245,7 +245,7 @@ def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists, dist=
         pg.barrier()
     clocks = ClockSampler(dev.index or 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    agg = {"kern_ms": 0.0, "kern_launches": 0, "launches": 0, "survivors": 0, "rows": 0, "lat": []}
+    agg = {"kern_ms": 0.0, "kern_launches": 0, "launches": 0, "survivors": 0, "rows": 0, "words": 0, "lat": []}
     torch.cuda.synchronize()
     e0.record(stream)
     for s in range(W, W + K):
@@ -256,6 +256,7 @@ def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists, dist=
         agg["launches"] += st["kernel_launches"]
         agg["survivors"] += st["lb_survivors"]
         agg["rows"] += st["refined"] + st["abandoned"]
+        agg["words"] += st["lb_evaluated"]
         agg["lat"] += [st["query_ms_p50"], st["query_ms_p99"]]
     e1.record(stream)
     torch.cuda.synchronize()
@@ -335,10 +336,16 @@ def run_messi(args, ws, rank, local):
         r = time_form(m, ix, qpool, form, B, K, W, args.k, stream, pg, dev, ids, dists, dist_code, window)
         nqt = B * K
         kern_avg_s = r["kern_ms"] * 1e-3 / max(r["kern_launches"], 1)
+        n_leaves = m.messi_index_get_info(ix)["n_leaves"]
+        ntiles = (args.n + 1023) // 1024
         if form == "plain":
-            kernel, algo = "k_lb_scan", 16.0 * args.n
+            # the timed scan group: leaf boxes + leaf offsets (40 B per leaf), the
+            # tile stamps (4 B per tile), and 16 B per word of the live tiles
+            kernel = "k_lb_scan"
+            algo = 40.0 * n_leaves + 4.0 * ntiles + 16.0 * r["words"] / max(r["kern_launches"], 1)
             roof = {"bound": "hbm", "achieved": algo / kern_avg_s / 1e9, "peak": peak, "unit": "GB/s",
-                    "frac": algo / kern_avg_s / 1e9 / peak, "peak_kind": peak_kind}
+                    "frac": algo / kern_avg_s / 1e9 / peak, "peak_kind": peak_kind,
+                    "timed": "k_leaf_prune + k_live_tiles + k_lb_scan per query"}
         elif batch_mode == "tc_screen":
             # the screen's dense work: 2 * len flops per (series, query) pair, B queries per launch
             kernel, algo = "k_tc_screen", 2.0 * args.len * args.n * B
@@ -350,13 +357,16 @@ def run_messi(args, ws, rank, local):
             algo = 16.0 * args.n + 4.0 * args.len * r["rows"] / max(r["kern_launches"], 1)
             roof = {"bound": "hbm", "achieved": algo / kern_avg_s / 1e9, "peak": peak, "unit": "GB/s",
                     "frac": algo / kern_avg_s / 1e9 / peak, "peak_kind": peak_kind}
-        q_bytes = 16.0 * args.n + 8.0 * r["survivors"] / nqt + 4.0 * args.len * r["rows"] / nqt
+        words_q = r["words"] / nqt if form == "plain" else float(args.n)
+        q_bytes = (40.0 * n_leaves + 4.0 * ntiles + 16.0 * words_q + 8.0 * r["survivors"] / nqt
+                   + 4.0 * args.len * r["rows"] / nqt)
         forms[form] = {
             "value": ws * nqt / (r["elapsed_ms"] * 1e-3), "ms_per_step": r["elapsed_ms"] / K,
             "p50_ms": r["p50"], "p99_ms": r["p99"], "gpu_launches": r["launches"], "clocks": r["clocks"],
             "roofline": dict(roof, kernel=kernel, algorithmic_per_launch=algo, avg_launch_ms=kern_avg_s * 1e3,
                              launches=r["kern_launches"]),
-            "counters": {"lb_survivors_per_query": r["survivors"] / nqt, "rows_read_per_query": r["rows"] / nqt},
+            "counters": {"lb_survivors_per_query": r["survivors"] / nqt, "rows_read_per_query": r["rows"] / nqt,
+                         "words_scanned_per_query": r["words"] / nqt},
             "query_roofline_frac": q_bytes / (r["elapsed_ms"] * 1e-3 / nqt) / 1e9 / peak,
         }
     head_form = max(forms, key=lambda f: forms[f]["value"])

@@ -78,7 +78,8 @@ typedef struct {
     double scan_ms;           /* summed scan durations, CUDA events (profiling) */
     double query_ms_p50;      /* per-query device latency (profiling mode)    */
     double query_ms_p99;
-    uint64_t reserved[6];
+    uint64_t leaves_live;     /* leaves whose symbol box did not prune them   */
+    uint64_t reserved[5];
 } messi_stats;
 
 typedef struct {

@@ -57,6 +57,19 @@ bool ensure_stage(Workspace *ws, size_t bytes)
     return true;
 }
 
+// Stamp for the next query's live-tile marks on this workspace.  Stamps only
+// need to differ from every earlier one on the same array; after 2^32 - 1
+// queries the array is cleared and the stamps start again.
+unsigned next_epoch(Workspace *ws, cudaStream_t s)
+{
+    if (++ws->epoch == 0u) {
+        const unsigned long long n = ws->tile_count;
+        cudaMemsetAsync(ws->slot.tile_epoch, 0, n * 4, s);
+        ws->epoch = 1u;
+    }
+    return ws->epoch;
+}
+
 // Plain-path workspace: one query slot with survivor arrays of N entries.
 messi_status ensure_workspace(messi_index *ix, Workspace *ws)
 {
@@ -75,8 +88,13 @@ messi_status ensure_workspace(messi_index *ix, Workspace *ws)
     // entries cannot overflow
     const size_t log_cap = N + kSeedMax;
     const size_t o_karr = take(kMaxK * 8), o_log = take(log_cap * 8), o_seed = take(kSeedMax * 8);
-    const size_t o_sp = take(N * 4), o_sl = take(N * 4), o_s2 = take(N * 4), o_s2l = take(N * 4);
+    // scan survivors: CTA c writes region c of ceil(live tiles / grid) tiles,
+    // so the arrays hold ntiles + kMaxScanGrid tiles of words
+    const size_t ntiles = (N + kScanTileWordsHost - 1) / kScanTileWordsHost;
+    const size_t nsurv = (ntiles + kMaxScanGrid) * kScanTileWordsHost;
+    const size_t o_sp = take(nsurv * 4), o_sl = take(nsurv * 4), o_s2 = take(N * 4), o_s2l = take(N * 4);
     const size_t o_bk = take(2 * kOrderBuckets * 4);
+    const size_t o_te = take(ntiles * 4), o_ll = take(ntiles * 4);
     const size_t o_dtw = take(32 * 3 * len * 8);
     const size_t o_rc = take(kMaxScanGrid * 4);
     const size_t o_acc = take(sizeof(QueryCounters));
@@ -102,13 +120,18 @@ messi_status ensure_workspace(messi_index *ix, Workspace *ws)
     s.surv2 = reinterpret_cast<unsigned *>(base + o_s2);
     s.surv2_lb = reinterpret_cast<float *>(base + o_s2l);
     s.bucket = reinterpret_cast<unsigned *>(base + o_bk);
+    s.tile_epoch = reinterpret_cast<unsigned *>(base + o_te);
+    s.live_list = reinterpret_cast<unsigned *>(base + o_ll);
     s.dtw64 = reinterpret_cast<double *>(base + o_dtw);
     s.region_count = reinterpret_cast<unsigned *>(base + o_rc);
     s.acc = reinterpret_cast<QueryCounters *>(base + o_acc);
     s.log_cap = (unsigned)std::min<size_t>(log_cap, 0xffffffffu);
     // bucket counts start at zero; every ordering step leaves them cleared
-    if (!cuda_ok(cudaMemset(s.bucket, 0, kOrderBuckets * 4), "messi_query: clear the bound buckets"))
+    if (!cuda_ok(cudaMemset(s.bucket, 0, kOrderBuckets * 4), "messi_query: clear the bound buckets") ||
+        !cuda_ok(cudaMemset(s.tile_epoch, 0, ntiles * 4), "messi_query: clear the tile stamps"))
         return MESSI_ECUDA;
+    ws->epoch = 0;
+    ws->tile_count = ntiles;
     return MESSI_OK;
 }
 
@@ -255,6 +278,7 @@ IndexView view_of(const messi_index *ix)
     v.pos_of_id = ix->pos_of_id;
     v.leaf_off = ix->leaf_off;
     v.leaf_key = ix->leaf_key;
+    v.leaf_box = ix->leaf_box;
     v.beta64 = ix->beta64;
     v.N = ix->N;
     v.L = ix->L;
@@ -399,7 +423,8 @@ void messi_free(messi_index *ix)
 {
     if (!ix) return;
     void *ptrs[] = {ix->raw,      ix->sax,        ix->ids,    ix->pos_of_id, ix->leaf_off,
-                    ix->leaf_key, ix->leaf_depth, ix->beta64, ix->status,    ix->screen16};
+                    ix->leaf_key, ix->leaf_depth, ix->beta64, ix->status,    ix->screen16,
+                    ix->leaf_box};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_workspace(ix->ws);
@@ -601,7 +626,7 @@ messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uin
             es0 = (int)evn;
             cudaEventRecord(pool_event(ws, evn++), s);
         }
-        launch_scan(iv, qp, slot, s);
+        launch_scan(iv, qp, slot, next_epoch(ws, s), s);
         if (ix->profiling) {
             cudaEventRecord(pool_event(ws, evn++), s);
             ws->scan_ev.push_back({es0, es0 + 1});
@@ -717,7 +742,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
                 MESSI_CUDA(cudaMemsetAsync(one.acc, 0, sizeof(QueryCounters), s));
                 launch_prep(iv, q1, one, dq + (size_t)(g + b) * ix->len, s);
                 launch_seed(iv, q1, one, s, &ws->launches);
-                launch_scan(iv, q1, one, s);
+                launch_scan(iv, q1, one, next_epoch(ws, s), s);
                 launch_refine(iv, q1, one, s, &ws->launches);
                 launch_finalize(iv, q1, one, did + (size_t)(g + b) * k, ddist + (size_t)(g + b) * k, s);
                 ws->launches += 3;
@@ -799,6 +824,7 @@ messi_status messi_query_stats(const messi_index *cix, messi_stats *out)
     out->abandoned = c.abandoned;
     out->bsf_updates = c.bsf_updates;
     out->tie_rechecks = c.tie_rechecks;
+    out->leaves_live = c.leaves_live;
     if (ix->profiling) {
         double sum = 0.0;
         for (auto &pr : ws->scan_ev) {

@@ -94,6 +94,43 @@ __global__ void k_make_leaves(const unsigned *__restrict__ flags, const unsigned
     leaf_depth[l] = depth_at[i];
 }
 
+// Per-leaf symbol box: for every segment the smallest and largest symbol of
+// the leaf's words (one warp per leaf, bytewise min / max over its rows).
+// Every word of the leaf lies in the box, so the table minimum over the box
+// bounds all of them from below.
+__global__ void __launch_bounds__(256)
+k_leaf_boxes(const uint4 *__restrict__ sax, const unsigned long long *__restrict__ leaf_off, unsigned long long L,
+             uint4 *__restrict__ box)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long l = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); l < L;
+         l += nw) {
+        const unsigned long long a = leaf_off[l], b = leaf_off[l + 1];
+        uint4 mn = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu), mx = make_uint4(0, 0, 0, 0);
+        for (unsigned long long i = a + lane; i < b; i += 32) {
+            const uint4 w = sax[i];
+            mn = make_uint4(__vminu4(mn.x, w.x), __vminu4(mn.y, w.y), __vminu4(mn.z, w.z), __vminu4(mn.w, w.w));
+            mx = make_uint4(__vmaxu4(mx.x, w.x), __vmaxu4(mx.y, w.y), __vmaxu4(mx.z, w.z), __vmaxu4(mx.w, w.w));
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            mn.x = __vminu4(mn.x, __shfl_xor_sync(0xffffffffu, mn.x, off));
+            mn.y = __vminu4(mn.y, __shfl_xor_sync(0xffffffffu, mn.y, off));
+            mn.z = __vminu4(mn.z, __shfl_xor_sync(0xffffffffu, mn.z, off));
+            mn.w = __vminu4(mn.w, __shfl_xor_sync(0xffffffffu, mn.w, off));
+            mx.x = __vmaxu4(mx.x, __shfl_xor_sync(0xffffffffu, mx.x, off));
+            mx.y = __vmaxu4(mx.y, __shfl_xor_sync(0xffffffffu, mx.y, off));
+            mx.z = __vmaxu4(mx.z, __shfl_xor_sync(0xffffffffu, mx.z, off));
+            mx.w = __vmaxu4(mx.w, __shfl_xor_sync(0xffffffffu, mx.w, off));
+        }
+        if (lane == 0) {
+            box[2 * l] = mn;
+            box[2 * l + 1] = mx;
+        }
+    }
+}
+
 __global__ void k_max_leaf(const unsigned long long *__restrict__ leaf_off, unsigned long long L,
                            unsigned long long *__restrict__ out)
 {
@@ -206,12 +243,12 @@ messi_status build_leaves(messi_index *ix, const uint4 *keys, const uint4 *sax_u
     ix->L = L;
     if (cudaMalloc(&ix->leaf_off, (L + 1) * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&ix->leaf_key, L * sizeof(uint4)) != cudaSuccess ||
-        cudaMalloc(&ix->leaf_depth, L) != cudaSuccess) {
+        cudaMalloc(&ix->leaf_depth, L) != cudaSuccess || cudaMalloc(&ix->leaf_box, L * 2 * sizeof(uint4)) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
         return fail(MESSI_ENOMEM, "messi_build: cannot allocate the leaf table");
     }
-    ix->device_bytes += (L + 1) * 8 + L * 17;
+    ix->device_bytes += (L + 1) * 8 + L * 17 + L * 32;
     k_make_leaves<<<nblk, tpb, 0, s>>>(flags, idx, depth_at, keys, n, ix->leaf_off, ix->leaf_key,
                                        ix->leaf_depth, L);
     unsigned long long *dmax = reinterpret_cast<unsigned long long *>(counts);
@@ -224,7 +261,9 @@ messi_status build_leaves(messi_index *ix, const uint4 *keys, const uint4 *sax_u
     unsigned long long capb = (unsigned long long)num_sms() * 16;
     k_permute<<<(unsigned)std::min(want, capb), 256, 0, s>>>(series, ix->ids, sax_unsorted, n, ix->len,
                                                              ix->raw, ix->sax, ix->pos_of_id);
-    ix->launches += 3;
+    const unsigned long long bw = (L + 7) / 8;
+    k_leaf_boxes<<<(unsigned)std::min(bw, capb), 256, 0, s>>>(ix->sax, ix->leaf_off, L, ix->leaf_box);
+    ix->launches += 4;
     MESSI_CUDA(cudaStreamSynchronize(s));
     cleanup();
     return MESSI_OK;

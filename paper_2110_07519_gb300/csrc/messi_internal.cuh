@@ -31,6 +31,7 @@ constexpr int kMaxLen = 4096;
 constexpr int kMaxK = 1024;
 constexpr int kLogCap = 8192;        // candidates the final step resolves at once (shared memory)
 constexpr int kBatchLogCap = 20480;  // log entries of a batched query slot
+constexpr int kScanTileWordsHost = 1024;   // words per lower-bound scan tile (see query.cu)
 constexpr int kOrderBuckets = 4096;  // survivors bucketed by the top 12 bits of their FP32 bound
 constexpr int kSeedMax = 4096;       // series of the seed leaf refined up front
 constexpr unsigned long long kEmpty = ~0ull;   // packed "no candidate"
@@ -47,7 +48,7 @@ constexpr unsigned kSpinLimit = 1u << 22;
 // ------------------------------------------------------- per-query state
 struct QueryCounters {
     unsigned long long lb_evaluated, lb_survivors, lbk_survivors, seeded, refined, abandoned,
-        bsf_updates, tie_rechecks;
+        bsf_updates, tie_rechecks, leaves_live;
 };
 
 struct QueryState {
@@ -63,6 +64,8 @@ struct QueryState {
     unsigned int scan_grid;     // CTAs of the last scan: survivor regions
     unsigned int region_words;  // words (and survivor slots) per scan CTA
     unsigned int ord_count;     // survivors in the bound-ordered list
+    unsigned int live_tiles;    // scan tiles holding a leaf that its box did not prune
+    uint4 qsym;                 // per segment (byte s) a symbol where the table is 0
     uint4 qkey;                 // interleaved key of the query word
     QueryCounters c;
 };
@@ -82,6 +85,8 @@ struct QuerySlot {
     unsigned int *surv2;        // [N] compact LB_Keogh survivors, or the bound-ordered ED survivors
     float *surv2_lb;            // [N] their lower bounds
     unsigned int *bucket;       // [2][kOrderBuckets] bucket counts, then write cursors
+    unsigned int *tile_epoch;   // [scan tiles] last query epoch that found the tile live
+    unsigned int *live_list;    // [scan tiles] live tiles of the current query
     double *dtw64;              // [32 warps][3][len] FP64 DTW diagonals (finalize)
     QueryCounters *acc;         // per-call counter accumulator
     unsigned log_cap;           // entries of `log`
@@ -95,6 +100,7 @@ struct IndexView {
     const unsigned int *pos_of_id;
     const unsigned long long *leaf_off;
     const uint4 *leaf_key;
+    const uint4 *leaf_box;      // [L][2]: per segment (byte s) the smallest, then the largest symbol
     const double *beta64;       // [card-1] breakpoints
     unsigned long long N;
     unsigned long long L;
@@ -138,6 +144,8 @@ struct Workspace {
     // statistics of the last call
     messi_stats last{};
     cudaStream_t last_stream = nullptr;
+    unsigned epoch = 0;               // per-query stamp of the live-tile marks
+    unsigned long long tile_count = 0;   // scan tiles of the plain slot's stamp array
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, int>> scan_ev, query_ev;   // pairs of event indices
     unsigned long long launches = 0;
@@ -177,6 +185,7 @@ struct messi_index {
     unsigned long long *leaf_off = nullptr;
     uint4 *leaf_key = nullptr;
     unsigned char *leaf_depth = nullptr;
+    uint4 *leaf_box = nullptr;
     double *beta64 = nullptr;
     unsigned int *status = nullptr;
     double beta_host[256] = {0};
@@ -231,7 +240,10 @@ void launch_prep(const IndexView &iv, const QueryParams &qp, QuerySlot slot, con
                  cudaStream_t s);
 void launch_seed(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s,
                  unsigned long long *launches);
-void launch_scan(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s);
+// Leaf boxes against the query's table (live tiles stamped with `epoch`,
+// which must differ from every earlier query's on this slot), then the
+// lower-bound scan of the live tiles.
+void launch_scan(const IndexView &iv, const QueryParams &qp, QuerySlot slot, unsigned epoch, cudaStream_t s);
 void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s,
                    unsigned long long *launches);
 void launch_finalize(const IndexView &iv, const QueryParams &qp, QuerySlot slot, long long *ids,

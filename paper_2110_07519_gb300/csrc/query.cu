@@ -7,13 +7,17 @@
 //               Sec. 3.1).
 //   k_seed_dist distances to every series of the seed range.
 //   k_seed_sel  the k best of them become the initial best-so-far.
-//   k_lb_scan   streams every iSAX word through TMA bulk copies into shared
-//               memory, sums its table entries and compacts the survivors
-//               (LB^2 <= widened k-th best) warp by warp.
-//   k_refine_ed warp per survivor: re-checks its bound against the live
-//               best-so-far, then ED with early abandoning (Algorithm 9).
-//   k_lbk/k_dtw DTW: LB_Keogh on the raw survivor, then banded DTW
-//               (Algorithm 10).
+//   k_leaf_prune bounds every leaf from its symbol box and marks the scan
+//               tiles of the leaves it cannot prune (k_live_tiles lists them).
+//   k_lb_scan   streams the iSAX words of the live tiles through TMA bulk
+//               copies into shared memory, sums their table entries and
+//               compacts the survivors (LB^2 <= widened k-th best) warp by warp.
+//   k_order_*   counting-sorts the survivors by lower-bound bucket (order.cu).
+//   k_refine_ed warp per survivor, in bound order: re-checks its bound against
+//               the live best-so-far, then ED with early abandoning
+//               (Algorithm 9).
+//   k_lbk/k_dtw_thread  DTW: LB_Keogh both ways on the raw survivor, bound
+//               order, then banded DTW one candidate per thread (Algorithm 10).
 //   k_finalize  resolves near-ties in FP64 and writes ids / distances.
 //
 // Exactness.  Lower bounds are summed with rounding toward -inf from table
@@ -38,6 +42,7 @@ constexpr int kPrepThreads = 256;
 constexpr int kScanThreads = 512;
 constexpr int kScanWpt = 2;
 constexpr int kScanTileWords = kScanThreads * kScanWpt;   // 1024 words, 16 KB
+static_assert(kScanTileWords == kScanTileWordsHost, "scan tile size shared with the workspace layout");
 constexpr int kScanStages = 4;
 constexpr int kScanCtasPerSm = 2;
 constexpr int kScanSmem = kMaxSegments * kMaxCard * 4 + kScanStages * kScanTileWords * 16;
@@ -82,6 +87,7 @@ __device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams
         st->log_count = 0u;
         st->seed_count = 0u;
         st->invalid = 0u;
+        st->live_tiles = 0u;
         st->c = QueryCounters{};
     }
     for (int i = tid; i < kMaxCard; i += blockDim.x) sbeta[i] = i < card - 1 ? iv.beta64[i] : 0.0;
@@ -168,6 +174,11 @@ __device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams
         }
         const uint4 qk = make_uint4((unsigned)(khi >> 32), (unsigned)khi, (unsigned)(klo >> 32), (unsigned)klo);
         st->qkey = qk;
+        // per segment a symbol where the table is 0: the query's own symbol
+        // (for DTW it lies between the envelope's symbols, where the table is 0)
+        unsigned qs[4] = {0u, 0u, 0u, 0u};
+        for (int s = 0; s < w; ++s) qs[s >> 2] |= (unsigned)sym[s] << (8 * (s & 3));
+        st->qsym = make_uint4(qs[0], qs[1], qs[2], qs[3]);
         // seed leaf: the last leaf whose first key is <= the query key
         unsigned long long lo = 0, hi = iv.L;   // count of leaves with key <= qk
         while (lo < hi) {
@@ -306,13 +317,86 @@ k_seed_select_batch(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ 
 // Persistent CTAs; CTA c owns the contiguous tiles [c*tpc, (c+1)*tpc) and
 // writes its survivors into its own region of the survivor arrays (the same
 // index range as its words), so compaction needs only a shared-memory counter.
+// ------------------------------------------------------- leaf pruning
+// Every word of a leaf lies in the leaf's symbol box, and each segment's table
+// row is non-increasing up to the query's symbol and non-decreasing after it
+// (the distance to a region grows with the region's distance from the
+// query's value, and rounding down keeps that order), so the smallest entry
+// over the box's range [lo, hi] sits at clamp(qsym, lo, hi).  Their sum,
+// added rounding down, bounds every word of the leaf from below: a leaf above
+// the threshold is skipped without reading its words -- the subtree pruning
+// of the paper's traversal (Sec. 3, ED query answering), on leaf boxes.  One
+// thread per leaf; the scan tiles a surviving leaf touches are stamped with
+// the query's epoch.
+__global__ void __launch_bounds__(256)
+k_leaf_prune(IndexView iv, QueryParams qp, QuerySlot slot, unsigned epoch)
+{
+    __shared__ unsigned live;
+    QueryState *st = slot.st;
+    if (ld_volatile_u32(&st->invalid)) return;
+    if (threadIdx.x == 0) live = 0;
+    __syncthreads();
+    const float thrp = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+    const uint4 q = st->qsym;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned mine = 0;
+    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < iv.L; l += stride) {
+        const uint4 lo = iv.leaf_box[2 * l], hi = iv.leaf_box[2 * l + 1];
+        const unsigned c[4] = {__vminu4(__vmaxu4(q.x, lo.x), hi.x), __vminu4(__vmaxu4(q.y, lo.y), hi.y),
+                               __vminu4(__vmaxu4(q.z, lo.z), hi.z), __vminu4(__vmaxu4(q.w, lo.w), hi.w)};
+        float lb = 0.f;
+#pragma unroll
+        for (int s = 0; s < kMaxSegments; ++s)
+            lb = __fadd_rd(lb, __ldg(slot.lut + s * kMaxCard + ((c[s >> 2] >> (8 * (s & 3))) & 0xffu)));
+        if (lb <= thrp) {
+            ++mine;
+            const unsigned long long a = iv.leaf_off[l], b = iv.leaf_off[l + 1];
+            for (unsigned long long t = a / kScanTileWords; t <= (b - 1) / kScanTileWords; ++t)
+                slot.tile_epoch[t] = epoch;
+        }
+    }
+    if (mine) atomicAdd(&live, mine);
+    __syncthreads();
+    if (threadIdx.x == 0 && live) atomicAdd(&st->c.leaves_live, (unsigned long long)live);
+}
+
+// Compact the tiles stamped with this query's epoch into live_list.
+__global__ void __launch_bounds__(256)
+k_live_tiles(QuerySlot slot, unsigned long long ntiles, unsigned epoch)
+{
+    __shared__ unsigned wcount[8], wbase[8], bbase;
+    QueryState *st = slot.st;
+    if (ld_volatile_u32(&st->invalid)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x; t0 < ntiles;
+         t0 += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long t = t0 + threadIdx.x;
+        const bool live = t < ntiles && slot.tile_epoch[t] == epoch;
+        const unsigned ballot = __ballot_sync(0xffffffffu, live);
+        if (lane == 0) wcount[warp] = __popc(ballot);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned run = 0;
+            for (int w = 0; w < 8; ++w) {
+                wbase[w] = run;
+                run += wcount[w];
+            }
+            bbase = run ? atomicAdd(&st->live_tiles, run) : 0u;
+        }
+        __syncthreads();
+        if (live) slot.live_list[bbase + wbase[warp] + __popc(ballot & ((1u << lane) - 1u))] = (unsigned)t;
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kScanThreads, kScanCtasPerSm)
-k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot, unsigned tpc)
+k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bars[kScanStages];
     __shared__ int timed_out;
     __shared__ unsigned s_count;
+    __shared__ unsigned long long s_words;
     float *lut = reinterpret_cast<float *>(smem);
     uint4 *stage = reinterpret_cast<uint4 *>(smem + kMaxSegments * kMaxCard * 4);
     QueryState *st = slot.st;
@@ -322,13 +406,15 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot, unsigned tpc)
     const float thrp = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
     const unsigned long long seed_lo = st->seed_lo, seed_hi = st->seed_hi;
     const unsigned long long N = iv.N;
-    const unsigned long long ntiles = (N + kScanTileWords - 1) / kScanTileWords;
-    const unsigned long long t0 = (unsigned long long)blockIdx.x * tpc;
-    const unsigned long long t1 = min(t0 + tpc, ntiles);
-    const unsigned long long region = t0 * kScanTileWords;
+    // this CTA's share of the live tiles; its survivors go to its own region
+    const unsigned nlive = st->live_tiles;
+    const unsigned tpc = (nlive + gridDim.x - 1) / gridDim.x;
+    const unsigned i0 = min(nlive, blockIdx.x * tpc), i1 = min(nlive, i0 + tpc);
+    const unsigned long long region = (unsigned long long)blockIdx.x * tpc * kScanTileWords;
     if (tid == 0) {
         timed_out = 0;
         s_count = 0;
+        s_words = 0;
         for (int s = 0; s < kScanStages; ++s) mbar_init(&bars[s], 1);
         fence_barrier_init();
         fence_proxy_async();
@@ -338,17 +424,17 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot, unsigned tpc)
         }
     }
     __syncthreads();
-    auto issue = [&](unsigned long long tile, int s) {
-        const unsigned long long first = tile * kScanTileWords;
+    auto issue = [&](unsigned idx, int s) {
+        const unsigned long long first = (unsigned long long)slot.live_list[idx] * kScanTileWords;
         const unsigned long long cnt = min((unsigned long long)kScanTileWords, N - first);
         const unsigned bytes = (unsigned)(cnt * 16);
         mbar_arrive_expect_tx(&bars[s], bytes);
         bulk_g2s(stage + s * kScanTileWords, iv.sax + first, bytes, &bars[s]);
     };
     if (tid == 0)
-        for (int s = 0; s < kScanStages && t0 + s < t1; ++s) issue(t0 + s, s);
+        for (int s = 0; s < kScanStages && i0 + s < i1; ++s) issue(i0 + s, s);
     unsigned iter = 0;
-    for (unsigned long long tile = t0; tile < t1; ++tile, ++iter) {
+    for (unsigned idx = i0; idx < i1; ++idx, ++iter) {
         const int s = iter % kScanStages;
         const unsigned parity = (iter / kScanStages) & 1u;
         const bool ok = mbar_wait_bounded(&bars[s], parity);
@@ -357,8 +443,9 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot, unsigned tpc)
             timed_out = 1;
             break;
         }
-        const unsigned long long first = tile * kScanTileWords;
+        const unsigned long long first = (unsigned long long)slot.live_list[idx] * kScanTileWords;
         const unsigned cnt = (unsigned)min((unsigned long long)kScanTileWords, N - first);
+        if (tid == 0) s_words += cnt;
 #pragma unroll
         for (int r = 0; r < kScanWpt; ++r) {
             const unsigned j = tid + r * kScanThreads;
@@ -382,13 +469,13 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot, unsigned tpc)
             }
         }
         __syncthreads();
-        if (tid == 0 && tile + kScanStages < t1) issue(tile + kScanStages, s);
+        if (tid == 0 && idx + kScanStages < i1) issue(idx + kScanStages, s);
     }
     if (timed_out) {
         // let the copies still in flight (iterations iter .. iter+S-1) land
         // before the block's shared memory is released
         if (tid == 0)
-            for (unsigned it = iter; it < iter + kScanStages && t0 + it < t1; ++it)
+            for (unsigned it = iter; it < iter + kScanStages && i0 + it < i1; ++it)
                 mbar_wait_bounded(&bars[it % kScanStages], (it / kScanStages) & 1u);
         if (tid == 0) slot.region_count[blockIdx.x] = 0;
         return;
@@ -397,7 +484,7 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot, unsigned tpc)
     if (tid == 0) {
         slot.region_count[blockIdx.x] = s_count;
         if (s_count) atomicAdd(&st->c.lb_survivors, (unsigned long long)s_count);
-        atomicAdd(&st->c.lb_evaluated, (t1 > t0) ? min(N, t1 * kScanTileWords) - t0 * kScanTileWords : 0ull);
+        if (s_words) atomicAdd(&st->c.lb_evaluated, s_words);
     }
 }
 
@@ -1154,6 +1241,7 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
         atomicAdd(&acc->abandoned, st->c.abandoned);
         atomicAdd(&acc->bsf_updates, st->c.bsf_updates);
         atomicAdd(&acc->tie_rechecks, st->c.tie_rechecks);
+        atomicAdd(&acc->leaves_live, st->c.leaves_live);
     }
 }
 
@@ -1232,14 +1320,19 @@ void launch_seed(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cud
     if (launches) *launches += 2;
 }
 
-void launch_scan(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s)
+void launch_scan(const IndexView &iv, const QueryParams &qp, QuerySlot slot, unsigned epoch, cudaStream_t s)
 {
     const unsigned long long ntiles = (iv.N + kScanTileWords - 1) / kScanTileWords;
+    const unsigned long long lg = std::min<unsigned long long>((iv.L + 255) / 256, (unsigned long long)num_sms() * 8);
+    k_leaf_prune<<<(unsigned)std::max(1ull, lg), 256, 0, s>>>(iv, qp, slot, epoch);
+    const unsigned long long tg = std::min<unsigned long long>((ntiles + 255) / 256, (unsigned long long)num_sms() * 4);
+    k_live_tiles<<<(unsigned)std::max(1ull, tg), 256, 0, s>>>(slot, ntiles, epoch);
+    // the live tiles are shared out on the device; survivors of CTA c go to
+    // region c of ceil(live / grid) tiles, which the survivor arrays hold
+    // for any live count (they have room for ntiles + kMaxScanGrid tiles)
     unsigned long long g = std::min<unsigned long long>(ntiles, (unsigned long long)num_sms() * kScanCtasPerSm);
     g = std::min<unsigned long long>(g, kMaxScanGrid);
-    const unsigned long long tpc = (ntiles + g - 1) / g;
-    g = (ntiles + tpc - 1) / tpc;
-    k_lb_scan<<<(unsigned)g, kScanThreads, kScanSmem, s>>>(iv, qp, slot, (unsigned)tpc);
+    k_lb_scan<<<(unsigned)std::max(1ull, g), kScanThreads, kScanSmem, s>>>(iv, qp, slot);
 }
 
 void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s,

@@ -26,25 +26,52 @@ constexpr int kOrderThreads = 256;
 
 // Visit the survivors of SRC: 0 = scan regions (surv_pos / surv_lb, region g
 // at g * region_words holding region_count[g] entries), 1 = compact list
-// (surv2 / surv2_lb, surv2_count entries).  A block visits the same entries
-// in the same order every time it is called within one launch.
+// (surv2 / surv2_lb, surv2_count entries).  Whole warps step together (so
+// warp collectives see all 32 lanes); a lane past the end gets valid = false.
+// A block visits the same entries in the same order every time it is called
+// within one launch.
 template <int SRC, typename F>
 __device__ __forceinline__ void for_each_survivor(const QuerySlot &slot, F f)
 {
     const QueryState *st = slot.st;
+    const unsigned lane = threadIdx.x & 31, wbase = threadIdx.x & ~31u;
     if (SRC == 0) {
         const unsigned G = st->scan_grid;
         const unsigned long long RW = st->region_words;
         for (unsigned g = blockIdx.x; g < G; g += gridDim.x) {
             const unsigned n = slot.region_count[g];
             const unsigned long long base = g * RW;
-            for (unsigned i = threadIdx.x; i < n; i += blockDim.x) f(slot.surv_pos[base + i], slot.surv_lb[base + i]);
+            for (unsigned i0 = wbase; i0 < n; i0 += blockDim.x) {
+                const unsigned i = i0 + lane;
+                const bool valid = i < n;
+                f(valid, valid ? slot.surv_pos[base + i] : 0u, valid ? slot.surv_lb[base + i] : 0.f);
+            }
         }
     } else {
         const unsigned n = st->surv2_count;
-        for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-            f(slot.surv2[i], slot.surv2_lb[i]);
+        for (unsigned i0 = blockIdx.x * blockDim.x + wbase; i0 < n; i0 += gridDim.x * blockDim.x) {
+            const unsigned i = i0 + lane;
+            const bool valid = i < n;
+            f(valid, valid ? slot.surv2[i] : 0u, valid ? slot.surv2_lb[i] : 0.f);
+        }
     }
+}
+
+// Shared-memory counter bump aggregated over the lanes of a warp that hit the
+// same bucket: one atomic per distinct bucket, each lane gets its own slot.
+// Returns the lane's slot (the counter's old value plus its rank), or 0 for
+// a lane that takes part with take = false.
+__device__ __forceinline__ unsigned bump_bucket(unsigned *h, bool take, unsigned b)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned want = __ballot_sync(0xffffffffu, take);
+    const unsigned key = take ? b : 0xffffffffu;
+    const unsigned same = __match_any_sync(0xffffffffu, key) & want;
+    unsigned base = 0;
+    const int leader = same ? __ffs(same) - 1 : -1;
+    if (take && (int)lane == leader) base = atomicAdd(&h[b], (unsigned)__popc(same));
+    base = __shfl_sync(0xffffffffu, base, leader < 0 ? (int)lane : leader);
+    return take ? base + __popc(same & ((1u << lane) - 1u)) : 0u;
 }
 
 template <int SRC>
@@ -57,8 +84,9 @@ k_order_count(QueryParams qp, QuerySlot slot)
     for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) h[b] = 0u;
     __syncthreads();
     const float thr = prune_threshold(st->thr, qp.F);
-    for_each_survivor<SRC>(slot, [&](unsigned, float lb) {
-        if (lb <= thr) atomicAdd(&h[order_bucket(lb)], 1u);
+    for_each_survivor<SRC>(slot, [&](bool valid, unsigned, float lb) {
+        const bool take = valid && lb <= thr;
+        bump_bucket(h, take, take ? order_bucket(lb) : 0u);
     });
     __syncthreads();
     for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
@@ -118,16 +146,18 @@ k_order_scatter(QueryParams qp, QuerySlot slot, unsigned *__restrict__ dst_pos, 
     for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) h[b] = 0u;
     __syncthreads();
     const float thr = prune_threshold(st->thr, qp.F);
-    for_each_survivor<SRC>(slot, [&](unsigned, float lb) {
-        if (lb <= thr) atomicAdd(&h[order_bucket(lb)], 1u);
+    for_each_survivor<SRC>(slot, [&](bool valid, unsigned, float lb) {
+        const bool take = valid && lb <= thr;
+        bump_bucket(h, take, take ? order_bucket(lb) : 0u);
     });
     __syncthreads();
     for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
         if (h[b]) h[b] = atomicAdd(&cursor[b], h[b]);
     __syncthreads();
-    for_each_survivor<SRC>(slot, [&](unsigned pos, float lb) {
-        if (lb <= thr) {
-            const unsigned o = atomicAdd(&h[order_bucket(lb)], 1u);
+    for_each_survivor<SRC>(slot, [&](bool valid, unsigned pos, float lb) {
+        const bool take = valid && lb <= thr;
+        const unsigned o = bump_bucket(h, take, take ? order_bucket(lb) : 0u);
+        if (take) {
             dst_pos[o] = pos;
             dst_lb[o] = lb;
         }

@@ -67,6 +67,7 @@ def _load():
         "orc_lb_keogh2": (D, [P, P, P, I]),
         "orc_mindist_dtw2": (D, [P, P, P, I, I, I, P]),
         "orc_dtw2": (D, [P, P, I, I]),
+        "orc_lb_improved2": (D, [P, P, P, P, I, I]),
         "orc_knn": (None, [P, I64, I, P, I, I, I, I, I64, I, P, P]),
         "orc_max_threads": (I, []),
     }
@@ -168,6 +169,14 @@ def envelope(q, r: int):
 def lb_keogh2(U, L, x) -> float:
     U, L, x = _f64(U), _f64(L), _f32(x)
     return float(_load().orc_lb_keogh2(_ptr(U), _ptr(L), _ptr(x), x.shape[-1]))
+
+
+def lb_improved2(q, x, r: int) -> float:
+    """LB_Improved (squared): LB_Keogh of x against q's envelope plus q against
+    the envelope of x clamped into q's envelope (window r)."""
+    q, x = _f32(q), _f32(x)
+    U, L = envelope(q, r)
+    return float(_load().orc_lb_improved2(_ptr(q), _ptr(U), _ptr(L), _ptr(x), q.shape[-1], r))
 
 
 def mindist_dtw2(paa_u, paa_l, sym, m: int, card: int, beta=None) -> float:

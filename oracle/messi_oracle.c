@@ -177,6 +177,37 @@ double orc_mindist_dtw2(const double *paaU, const double *paaL, const uint8_t *s
     return (double)m * s;
 }
 
+/* LB_Improved (Lemire): LB_Keogh of x against the query's envelope [L, U],
+ * plus the query against the envelope (same window) of h = x clamped into
+ * [L, U].  A lower bound of the banded squared DTW; the DTW filter of the
+ * query path uses it after LB_Keogh (Sec. 3.4 lower-bounds before real
+ * distances).  Plain loops over the definition. */
+double orc_lb_improved2(const float *q, const double *U, const double *L, const float *x, int n, int r)
+{
+    double first = orc_lb_keogh2(U, L, x, n), second = 0.0;
+    double *h = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!h) return first;
+    for (int i = 0; i < n; ++i) {
+        double c = (double)x[i];
+        h[i] = c > U[i] ? U[i] : (c < L[i] ? L[i] : c);
+    }
+    for (int i = 0; i < n; ++i) {
+        int a = i - r < 0 ? 0 : i - r;
+        int b = i + r > n - 1 ? n - 1 : i + r;
+        double hi = h[a], lo = h[a];
+        for (int j = a + 1; j <= b; ++j) {
+            if (h[j] > hi) hi = h[j];
+            if (h[j] < lo) lo = h[j];
+        }
+        double v = (double)q[i], d = 0.0;
+        if (v > hi) d = v - hi;
+        else if (v < lo) d = v - lo;
+        second += d * d;
+    }
+    free(h);
+    return first + second;
+}
+
 double orc_dtw2(const float *q, const float *x, int n, int r)
 {
     /* D is an n x n table; only cells inside the window are ever written or

@@ -74,6 +74,9 @@ double orc_mindist_dtw2(const double *paaU, const double *paaL, const uint8_t *s
 /* DTW under a Sakoe-Chiba window r (Sec. 3.4), squared cost:
  * D(i,j) = (q_i - x_j)^2 + min(D(i-1,j), D(i,j-1), D(i-1,j-1)) for
  * |i-j| <= r, +inf outside; result D(n-1, n-1). */
+/* LB_Improved: LB_Keogh(x; L, U) + the query against the envelope of x
+ * clamped into [L, U] (window r).  Squared. */
+double orc_lb_improved2(const float *q, const double *U, const double *L, const float *x, int n, int r);
 double orc_dtw2(const float *q, const float *x, int n, int r);
 
 /* Exact k-NN by brute force (problem statement, Sec. 2.1; k-NN as a sorted

@@ -16,7 +16,7 @@
 //   k_refine_ed warp per survivor, in bound order: re-checks its bound against
 //               the live best-so-far, then ED with early abandoning
 //               (Algorithm 9).
-//   k_lbk/k_dtw_thread  DTW: LB_Keogh both ways on the raw survivor, bound
+//   k_lbk/k_dtw_thread  DTW: LB_Keogh, then LB_Improved, on the raw survivor, bound
 //               order, then banded DTW one candidate per thread (Algorithm 10).
 //   k_finalize  resolves near-ties in FP64 and writes ids / distances.
 //
@@ -600,14 +600,18 @@ k_refine_ed(IndexView iv, QueryParams qp, QuerySlot slot)
 }
 
 // ------------------------------------------------------ DTW: LB_Keogh
-// Warp per survivor.  First LB_Keogh of the candidate against the query's
-// envelope (Sec. 3.4); if that does not prune, the same bound with the roles
-// swapped -- the candidate's envelope against the query -- which is also a
-// lower bound of the banded DTW (the band is symmetric, so DTW(Q, C) =
-// DTW(C, Q)) and is tight exactly where the first is loose: a noisy query has
-// a wide envelope, a smooth candidate a narrow one.  The candidate's envelope
-// comes from van Herk / Gil-Werman block prefix and suffix maxima (minima)
-// in the warp's shared-memory buffer.  Every operation of both bounds rounds
+// Warp per survivor.  First LB_Keogh of the candidate C against the query's
+// envelope [L, U] (Sec. 3.4); if that does not prune, Lemire's LB_Improved
+// adds a second term: H = C clamped into [L, U], and the query against the
+// envelope [L^H, U^H] of H (same window).  Why the sum still bounds the
+// banded DTW from below: every cell (i, j) of a warping path has |i - j| <= r,
+// so q_i lies in [L_j, U_j] and h_j lies between q_i and c_j; then
+// (q_i - c_j)^2 >= (q_i - h_j)^2 + (h_j - c_j)^2.  Summed over the path, the
+// second parts cover every j at least once (>= LB_Keogh(C; L, U)) and the
+// first parts every i at least once, each with h_j inside [L^H_i, U^H_i]
+// (>= the distance of q_i to that interval, squared).  The envelope of H
+// comes from van Herk / Gil-Werman block prefix and suffix maxima (minima) in
+// the warp's shared-memory buffer.  Every operation of both terms rounds
 // toward -inf.
 __device__ __forceinline__ float lbk_tail(float acc)
 {
@@ -667,7 +671,7 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
                 for (int t = lane; t < 256 && base + t < len; t += 32) {
                     const int idx = base + t;
                     const float c = __ldg(x + idx);
-                    P[idx] = c;                               // keep the row for the second bound
+                    P[idx] = fminf(fmaxf(c, Ls[idx]), Us[idx]);   // H: C clamped into [L, U]
                     float d = 0.f;
                     if (c > Us[idx]) d = __fsub_rd(c, Us[idx]);
                     else if (c < Ls[idx]) d = __fsub_rd(Ls[idx], c);
@@ -678,7 +682,7 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
             }
             if (!pruned && r > 0) {
                 __syncwarp();
-                // block prefix / suffix extrema of the candidate (blocks of w points)
+                // block prefix / suffix extrema of H (blocks of w points)
                 for (int blk = lane; blk < nblk; blk += 32) {
                     const int b0 = blk * w, b1 = min(len, b0 + w);
                     float mx = -f_inf(), mn = f_inf();
@@ -702,6 +706,7 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
                     }
                 }
                 __syncwarp();
+                const float fwd = lbv;            // LB_Keogh(C; L, U)
                 float acc2 = 0.f;
                 for (int base = 0; base < len && !pruned; base += 256) {
                     for (int t = lane; t < 256 && base + t < len; t += 32) {
@@ -726,9 +731,9 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
                         else if (c < L) d = __fsub_rd(L, c);
                         acc2 = __fadd_rd(acc2, __fmul_rd(d, d));
                     }
-                    const float lb2v = lbk_tail(acc2);
-                    if (lb2v > thr) pruned = true;
-                    lbv = fmaxf(lbv, lb2v);
+                    // LB_Improved so far: the first term plus the query's part
+                    lbv = __fadd_rd(fwd, lbk_tail(acc2));
+                    if (lbv > thr) pruned = true;
                 }
             }
             __syncwarp();

@@ -253,6 +253,48 @@ def test_dtw_vs_all_warping_paths(r):
         assert oracle.dtw2(q, x, r) == pytest.approx(best, rel=1e-13)
 
 
+def test_lb_improved_hand_worked():
+    # q = (0, 0, 0), x = (3, 0, -3), r = 1: the envelope of q is 0 everywhere,
+    # so LB_Keogh = 9 + 0 + 9 and h = (0, 0, 0); q sits inside h's envelope,
+    # so the second term is 0.  The r = 1 DTW is 18 too (every path pays both
+    # ends), so the bound is tight here.
+    q = np.zeros(3, dtype=np.float32)
+    x = np.array([3.0, 0.0, -3.0], dtype=np.float32)
+    assert oracle.lb_improved2(q, x, 1) == 18.0
+    assert oracle.dtw2(q, x, 1) == 18.0
+    # q = (0, 5, 0), x = (0, 0, 0), r = 0: U = L = q, h = q, second term 0:
+    # the bound is LB_Keogh = ED = 25
+    q2 = np.array([0.0, 5.0, 0.0], dtype=np.float32)
+    assert oracle.lb_improved2(q2, np.zeros(3, np.float32), 0) == 25.0
+    # q = (0, 4, 0, 0), x = (0, 0, 0, 4), r = 1: U = (4, 4, 4, 0),
+    # L = (0, 0, 0, 0); x_3 = 4 > U_3 = 0 costs 16, h = (0, 0, 0, 0), whose
+    # envelope is 0, and q_1 = 4 above it costs 16: bound 32
+    q3 = np.array([0.0, 4.0, 0.0, 0.0], dtype=np.float32)
+    x3 = np.array([0.0, 0.0, 0.0, 4.0], dtype=np.float32)
+    assert oracle.lb_improved2(q3, x3, 1) == 32.0
+    assert oracle.dtw2(q3, x3, 1) >= 32.0
+
+
+@pytest.mark.parametrize("n,r", [(16, 0), (16, 1), (16, 3), (32, 5), (64, 6), (64, 63), (37, 4)])
+def test_lb_keogh_le_lb_improved_le_dtw(n, r):
+    rng = np.random.default_rng(40 + n + r)
+    for t in range(60):
+        q = rng.standard_normal(n).astype(np.float32)
+        # smooth, noisy and shifted candidates
+        if t % 3 == 0:
+            x = np.cumsum(rng.standard_normal(n)).astype(np.float32)
+        elif t % 3 == 1:
+            x = (q + rng.normal(0, 1.0, n)).astype(np.float32)
+        else:
+            x = np.roll(q, rng.integers(-r - 1, r + 2)).astype(np.float32)
+        U, L = oracle.envelope(q, r)
+        lk = oracle.lb_keogh2(U, L, x)
+        li = oracle.lb_improved2(q, x, r)
+        d = oracle.dtw2(q, x, r)
+        assert lk <= li * (1 + 1e-12) + 1e-12
+        assert li <= d * (1 + 1e-12) + 1e-9
+
+
 def test_dtw_invariants():
     n = 128
     x = synth.random_walks(40, n, seed=37)

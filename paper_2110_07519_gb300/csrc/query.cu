@@ -1043,6 +1043,122 @@ k_dtw_thread(IndexView iv, QueryParams qp, QuerySlot slot)
     }
 }
 
+// LB_Keogh + LB_Improved of one candidate, one thread, one pass over the row
+// (the bounds of k_lbk, in the same FP32 operations, all rounded toward
+// -inf).  Step i reads c_i, adds its LB_Keogh term and pushes h_i = c_i
+// clamped into [L_i, U_i] into a register window of the last 2R + 1 h values;
+// from step r on it adds the query term of position p = i - r, which needs
+// the extremes of h over [p - r, p + r] = the newest 2r + 1 window slots.
+// The window starts filled with h_0 and the steps past the end push h_{n-1}
+// again: both are in every clipped window they stand in for, so the extremes
+// are those of the clipped window.  Returns the bound, or a value above thr
+// once the partial sum (a lower bound of the full one) exceeds it.
+template <int R>
+__device__ __forceinline__ float lbk_improved_thread(const float *__restrict__ qs, const float *__restrict__ Us,
+                                                     const float *__restrict__ Ls, const float *__restrict__ x,
+                                                     int n, int r, float thr)
+{
+    constexpr int W = 2 * R + 1;
+    float hw[W];
+    {
+        const float c0 = __ldg(x);
+        const float h0 = fminf(fmaxf(c0, Ls[0]), Us[0]);
+#pragma unroll
+        for (int b = 0; b < W; ++b) hw[b] = h0;
+    }
+    const int lo_b = 2 * (R - r);       // first window slot inside [p - r, p + r]
+    float acc1 = 0.f, acc2 = 0.f;
+    for (int i = 0; i < n + r; ++i) {
+        float h = hw[W - 1];
+        if (i < n) {
+            const float c = __ldg(x + i), u = Us[i], l = Ls[i];
+            float d = 0.f;
+            if (c > u) d = __fsub_rd(c, u);
+            else if (c < l) d = __fsub_rd(l, c);
+            acc1 = __fadd_rd(acc1, __fmul_rd(d, d));
+            h = fminf(fmaxf(c, l), u);
+        }
+#pragma unroll
+        for (int b = 0; b + 1 < W; ++b) hw[b] = hw[b + 1];
+        hw[W - 1] = h;
+        const int p = i - r;
+        if (p >= 0) {
+            float mx = h, mn = h;
+#pragma unroll
+            for (int b = 0; b + 1 < W; ++b) {
+                const float v = (b >= lo_b) ? hw[b] : h;
+                mx = fmaxf(mx, v);
+                mn = fminf(mn, v);
+            }
+            const float qv = qs[p];
+            float d = 0.f;
+            if (qv > mx) d = __fsub_rd(qv, mx);
+            else if (qv < mn) d = __fsub_rd(mn, qv);
+            acc2 = __fadd_rd(acc2, __fmul_rd(d, d));
+        }
+        if (__fadd_rd(acc1, acc2) > thr) return __fadd_rd(acc1, acc2);
+    }
+    return __fadd_rd(acc1, acc2);
+}
+
+// The DTW filter with one candidate per lane: a warp takes 32 scan survivors
+// at a time, each lane bounds its own; passing candidates are appended to
+// surv2 / surv2_lb with one atomic per warp.
+template <int R>
+__global__ void __launch_bounds__(256)
+k_lbk_thread(IndexView iv, QueryParams qp, QuerySlot slot)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ unsigned prefix[kMaxScanGrid + 1];
+    __shared__ unsigned counts[kMaxScanGrid];
+    QueryState *st = slot.st;
+    if (ld_volatile_u32(&st->invalid)) return;
+    const int len = iv.len;
+    float *Us = reinterpret_cast<float *>(dsm);
+    float *Ls = Us + len;
+    float *qs = Ls + len;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        Us[i] = slot.U[i];
+        Ls[i] = slot.L[i];
+        qs[i] = slot.q[i];
+    }
+    const unsigned G = st->scan_grid;
+    const unsigned long long RW = st->region_words;
+    const unsigned nchunks = chunk_prefix(slot, G, prefix, counts);   // also publishes the arrays above
+    const int lane = threadIdx.x & 31;
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    unsigned long long pass = 0;
+    for (unsigned ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += nw) {
+        const unsigned rg = region_of(ch, prefix, G);
+        const unsigned within = (ch - prefix[rg]) * 32 + lane;
+        const bool valid = within < counts[rg];
+        const unsigned long long i = rg * RW + within;
+        const unsigned pos = valid ? slot.surv_pos[i] : 0u;
+        const float lb = valid ? slot.surv_lb[i] : f_inf();
+        const float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+        bool keep = valid && lb <= thr;
+        float lbv = 0.f;
+        if (keep) {
+            lbv = lbk_improved_thread<R>(qs, Us, Ls, iv.raw + (unsigned long long)pos * len, len, qp.r, thr);
+            keep = lbv <= thr;
+        }
+        const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+        if (ballot) {
+            unsigned o = 0;
+            if (lane == 0) o = atomicAdd(&st->surv2_count, (unsigned)__popc(ballot));
+            o = __shfl_sync(0xffffffffu, o, 0) + __popc(ballot & ((1u << lane) - 1u));
+            if (keep) {
+                slot.surv2[o] = pos;
+                slot.surv2_lb[o] = lbv;
+            }
+            pass += (lane == 0) ? (unsigned long long)__popc(ballot) : 0ull;
+        }
+    }
+    if (lane == 0 && pass) atomicAdd(&st->c.lbk_survivors, pass);
+}
+
+bool launch_lbk_thread(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot, cudaStream_t s);
+
 // smallest instantiated band reach >= r (or -1: use the warp wavefront)
 int dtw_thread_reach(int r)
 {
@@ -1073,6 +1189,30 @@ bool launch_dtw_thread(const IndexView &iv, const QueryParams &qp, const QuerySl
         MESSI_DTW_CASE(25)
         MESSI_DTW_CASE(32)
 #undef MESSI_DTW_CASE
+        default: return false;
+    }
+}
+
+bool launch_lbk_thread(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot, cudaStream_t s)
+{
+    const int R = dtw_thread_reach(qp.r);
+    const unsigned grid = num_sms() * 8;
+    const size_t sm = (size_t)iv.len * 12;
+    switch (R) {
+#define MESSI_LBK_CASE(RR) \
+    case RR: k_lbk_thread<RR><<<grid, 256, sm, s>>>(iv, qp, slot); return true;
+        MESSI_LBK_CASE(0)
+        MESSI_LBK_CASE(1)
+        MESSI_LBK_CASE(2)
+        MESSI_LBK_CASE(4)
+        MESSI_LBK_CASE(6)
+        MESSI_LBK_CASE(8)
+        MESSI_LBK_CASE(12)
+        MESSI_LBK_CASE(16)
+        MESSI_LBK_CASE(20)
+        MESSI_LBK_CASE(25)
+        MESSI_LBK_CASE(32)
+#undef MESSI_LBK_CASE
         default: return false;
     }
 }
@@ -1348,9 +1488,12 @@ void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, c
         k_refine_ed<<<num_sms() * 8, 256, iv.len * 4, s>>>(iv, qp, slot);
         if (launches) *launches += 4;
     } else {
-        // per warp 4 rows of len floats (row / extrema), plus the query and its envelope
-        const int wpb = std::max(1, std::min(8, (int)((96 * 1024 - 12 * iv.len) / (16 * iv.len))));
-        k_lbk<<<num_sms() * 4, wpb * 32, (size_t)iv.len * 12 + (size_t)wpb * 16 * iv.len, s>>>(iv, qp, slot, wpb);
+        if (!launch_lbk_thread(iv, qp, slot, s)) {
+            // windows wider than the register forms: warp per candidate, per
+            // warp 4 rows of len floats (row / extrema), plus the query and its envelope
+            const int wpb = std::max(1, std::min(8, (int)((96 * 1024 - 12 * iv.len) / (16 * iv.len))));
+            k_lbk<<<num_sms() * 4, wpb * 32, (size_t)iv.len * 12 + (size_t)wpb * 16 * iv.len, s>>>(iv, qp, slot, wpb);
+        }
         launch_order(qp, slot, 1, slot.surv_pos, slot.surv_lb, s);
         if (!launch_dtw_thread<0>(iv, qp, slot, s)) {
             const int wpb = dtw_warps_per_block(iv.len);

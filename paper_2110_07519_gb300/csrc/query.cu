@@ -1101,6 +1101,72 @@ __device__ __forceinline__ float lbk_improved_thread(const float *__restrict__ q
     return __fadd_rd(acc1, acc2);
 }
 
+// The same bound when the window is exactly R (r == R), with the extremes of
+// each window from van Herk / Gil-Werman blocks of W = 2R + 1 steps instead of
+// a scan of the window: within a block, a running prefix extreme; from the
+// previous block, its suffix extremes (a window ending at block slot k is the
+// previous block's slots k + 1 .. W - 1 and the current slots 0 .. k).  The
+// previous block's slot k is last read at step k - 1, so step k overwrites it
+// with the new value, and the block's end turns the new values into suffix
+// extremes in place.  About six min / max per step instead of 3W.
+template <int R>
+__device__ __forceinline__ float lbk_improved_blocks(const float *__restrict__ qs, const float *__restrict__ Us,
+                                                     const float *__restrict__ Ls, const float *__restrict__ x,
+                                                     int n, float thr)
+{
+    constexpr int W = 2 * R + 1;
+    float smx[W], smn[W];
+    float hlast;
+    {
+        const float c0 = __ldg(x);
+        hlast = fminf(fmaxf(c0, Ls[0]), Us[0]);
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            smx[b] = hlast;
+            smn[b] = hlast;
+        }
+    }
+    float acc1 = 0.f, acc2 = 0.f;
+    for (int j0 = 0; j0 < n + R; j0 += W) {
+        float pmx = 0.f, pmn = 0.f;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const int j = j0 + k;
+            float h = hlast;
+            if (j < n) {
+                const float c = __ldg(x + j), u = Us[j], l = Ls[j];
+                float d = 0.f;
+                if (c > u) d = __fsub_rd(c, u);
+                else if (c < l) d = __fsub_rd(l, c);
+                acc1 = __fadd_rd(acc1, __fmul_rd(d, d));
+                h = fminf(fmaxf(c, l), u);
+                hlast = h;
+            }
+            pmx = (k == 0) ? h : fmaxf(pmx, h);
+            pmn = (k == 0) ? h : fminf(pmn, h);
+            const float mx = (k + 1 < W) ? fmaxf(smx[k + 1 < W ? k + 1 : 0], pmx) : pmx;
+            const float mn = (k + 1 < W) ? fminf(smn[k + 1 < W ? k + 1 : 0], pmn) : pmn;
+            smx[k] = h;
+            smn[k] = h;
+            const int p = j - R;
+            if (p >= 0 && p < n) {
+                const float qv = qs[p];
+                float d = 0.f;
+                if (qv > mx) d = __fsub_rd(qv, mx);
+                else if (qv < mn) d = __fsub_rd(mn, qv);
+                acc2 = __fadd_rd(acc2, __fmul_rd(d, d));
+            }
+        }
+#pragma unroll
+        for (int k = W - 2; k >= 0; --k) {
+            smx[k] = fmaxf(smx[k], smx[k + 1]);
+            smn[k] = fminf(smn[k], smn[k + 1]);
+        }
+        if (__fadd_rd(acc1, acc2) > thr) break;
+    }
+    return __fadd_rd(acc1, acc2);
+}
+
 // The DTW filter with one candidate per lane: a warp takes 32 scan survivors
 // at a time, each lane bounds its own; passing candidates are appended to
 // surv2 / surv2_lb with one atomic per warp.
@@ -1139,7 +1205,9 @@ k_lbk_thread(IndexView iv, QueryParams qp, QuerySlot slot)
         bool keep = valid && lb <= thr;
         float lbv = 0.f;
         if (keep) {
-            lbv = lbk_improved_thread<R>(qs, Us, Ls, iv.raw + (unsigned long long)pos * len, len, qp.r, thr);
+            const float *x = iv.raw + (unsigned long long)pos * len;
+            lbv = (qp.r == R) ? lbk_improved_blocks<R>(qs, Us, Ls, x, len, thr)
+                              : lbk_improved_thread<R>(qs, Us, Ls, x, len, qp.r, thr);
             keep = lbv <= thr;
         }
         const unsigned ballot = __ballot_sync(0xffffffffu, keep);

@@ -183,6 +183,30 @@ messi_status messi_query_stats(const messi_index *ix, messi_stats *out);
 enum { MESSI_BATCH_LB_REFINE = 0, MESSI_BATCH_TC_SCREEN = 1 };
 messi_status messi_set_batch_mode(messi_index *ix, int mode);
 
+/* Shapes of the batched forms.  The paper has no counterpart: it answers one
+ * query at a time (Sec. 5.1); batching is this library's addition. */
+typedef struct {
+    uint32_t batch;         /* queries per batch when messi_query_batched gets batch = 0 */
+    uint32_t chunk_tiles;   /* lower-bound form: scan tiles a CTA claims at a time      */
+    uint32_t ctas_per_sm;   /* lower-bound form: resident CTAs per SM (1 or 2)         */
+    uint32_t mode;          /* MESSI_BATCH_LB_REFINE or MESSI_BATCH_TC_SCREEN          */
+    double ms_per_query;    /* device time per query of the chosen shape (autotune)    */
+    uint32_t reserved[4];
+} messi_tuning;
+
+/* Time the index's current batch mode on `queries` (device pointer, nq rows,
+ * nq >= 32) for a set of shapes -- lower-bound form: batch 32..256, chunk
+ * tiles 16/32/64, 1 or 2 CTAs per SM; screened form: batch 128..1024 -- with
+ * CUDA events on `stream`, one warm-up batch and one timed batch per shape,
+ * and keep the fastest per query.  Writes the choice to *out (may be NULL).
+ * Synchronises `stream`.  EINVAL for host queries or nq < 32. */
+messi_status messi_autotune(messi_index *ix, const float *queries, uint32_t nq, uint32_t k, messi_stream stream,
+                            messi_tuning *out);
+
+/* Apply shapes (for instance a cached autotune result); mode is ignored.
+ * EINVAL for batch 0 or > 65535, chunk_tiles 0 or > 1024, ctas_per_sm not 1 or 2. */
+messi_status messi_set_tuning(messi_index *ix, const messi_tuning *t);
+
 /* Diagnostic of the tensor-core operand layout used by the screen: one
  * 128 x n x k f16 GEMM tile, D = A * B^T with FP32 accumulation, through the
  * same tcgen05 instructions.  a_tile (128 x k) and b_tile (n x k) are f16 bit

@@ -59,6 +59,14 @@ class MessiIndexInfo(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class MessiTuning(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_uint32), ("chunk_tiles", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("mode", ctypes.c_uint32), ("ms_per_query", ctypes.c_double), ("reserved", ctypes.c_uint32 * 4)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
+
+
 class MessiServerConfig(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_uint32), ("max_k", ctypes.c_uint32), ("streams", ctypes.c_uint32),
                 ("max_queued", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
@@ -85,6 +93,8 @@ _SIGS = {
     "messi_query_stats": [_P, ctypes.POINTER(MessiStats)],
     "messi_set_profiling": [_P, _I],
     "messi_set_batch_mode": [_P, _I],
+    "messi_autotune": [_P, _P, _U32, _U32, _P, ctypes.POINTER(MessiTuning)],
+    "messi_set_tuning": [_P, ctypes.POINTER(MessiTuning)],
     "messi_debug_tc_gemm": [_P, _P, _U32, _U32, _U32, _U32, _P],
     "messi_check": [_P, _P],
     "messi_summarize": [_P, _U64, _U32, _U32, _U32, _P, _P],
@@ -160,6 +170,7 @@ class Index:
     len: int
     segments: int
     cardinality: int
+    _batch_mode: int = 1            # the library's default: MESSI_BATCH_TC_SCREEN
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -301,6 +312,57 @@ def messi_set_profiling(index: Index, enable: bool = True):
 
 def messi_set_batch_mode(index: Index, mode: int):
     _check(_lib.messi_set_batch_mode(index.handle, mode), "messi_set_batch_mode")
+    index._batch_mode = mode
+
+
+def messi_autotune(index: Index, queries, k: int = 1, stream=None) -> dict:
+    """Time the batched shapes of the index's batch mode on `queries` (device
+    rows) and keep the fastest; returns the choice."""
+    queries = _f32(queries)
+    qp, qkeep, qcuda = _ptr(queries)
+    if not qcuda:
+        raise MessiError(1, "messi_autotune: queries must be a device tensor")
+    t = MessiTuning()
+    _check(_lib.messi_autotune(index.handle, qp, queries.shape[0], k, _stream(stream), ctypes.byref(t)),
+           "messi_autotune")
+    return t.as_dict()
+
+
+def messi_set_tuning(index: Index, batch: int, chunk_tiles: int = 32, ctas_per_sm: int = 2):
+    t = MessiTuning(batch=batch, chunk_tiles=chunk_tiles, ctas_per_sm=ctas_per_sm)
+    _check(_lib.messi_set_tuning(index.handle, ctypes.byref(t)), "messi_set_tuning")
+
+
+def autotune_cached(index: Index, queries, k: int = 1, cache: str | None = None, stream=None) -> dict:
+    """messi_autotune with a JSON cache keyed by collection shape, batch mode,
+    k and device name: a cached choice is applied without timing."""
+    import json
+
+    info = messi_index_get_info(index)
+    key = None
+    if cache:
+        try:
+            import torch
+
+            dev = torch.cuda.get_device_name()
+        except Exception:
+            dev = "cuda"
+        key = f"{info['n_series']}x{info['len']}:mode{index._batch_mode}:k{k}:{dev}"
+        try:
+            with open(cache) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+        if key in table:
+            t = table[key]
+            messi_set_tuning(index, t["batch"], t["chunk_tiles"], t["ctas_per_sm"])
+            return t
+    t = messi_autotune(index, queries, k, stream)
+    if cache:
+        table[key] = t
+        with open(cache, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+    return t
 
 
 def messi_debug_tc_gemm(a_tile: np.ndarray, b_tile: np.ndarray, k: int, n: int, lbo: int, sbo: int) -> np.ndarray:

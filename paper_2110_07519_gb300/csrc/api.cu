@@ -335,9 +335,13 @@ bool cuda_ok(cudaError_t e, const char *what)
 
 void free_workspace(Workspace &w)
 {
-    void *ptrs[] = {w.ws_block, w.stage_block, w.bws_block, w.tcws_block};
+    void *ptrs[] = {w.ws_block, w.stage_block, w.bws_block, w.tcws_block, w.gargs_dev, w.gcursor};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (w.gargs_host) cudaFreeHost(w.gargs_host);
+    if (w.graph) cudaGraphExecDestroy(w.graph);
+    if (w.gargs_done) cudaEventDestroy(w.gargs_done);
+    if (w.capture_stream) cudaStreamDestroy(w.capture_stream);
     for (cudaEvent_t e : w.ev_pool) cudaEventDestroy(e);
     w = Workspace{};
 }
@@ -651,6 +655,71 @@ messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uin
     return MESSI_OK;
 }
 
+// The lower-bound batch form as a CUDA graph: one batch (prep, seed, fused
+// scan-and-refine, finalize, cursor advance) is captured once per shape on a
+// private stream, with its query rows and result rows read from an argument
+// table; every full batch of a call is then one graph launch on the caller's
+// stream, the table advancing by one entry per replay.
+static messi_status replay_lb_batches(messi_index *ix, Workspace *ws, const IndexView &iv, const QueryParams &qp,
+                                      unsigned B, unsigned nfull, const float *dq, long long *did, float *ddist,
+                                      cudaStream_t s)
+{
+    if (!ws->capture_stream && !cuda_ok(cudaStreamCreateWithFlags(&ws->capture_stream, cudaStreamNonBlocking),
+                                        "messi_query_batched: capture stream"))
+        return MESSI_ECUDA;
+    if (!ws->gargs_done && !cuda_ok(cudaEventCreateWithFlags(&ws->gargs_done, cudaEventDisableTiming),
+                                    "messi_query_batched: event"))
+        return MESSI_ECUDA;
+    if (ws->gargs_cap < nfull) {
+        if (ws->gargs_dev) cudaFree(ws->gargs_dev);
+        if (ws->gargs_host) cudaFreeHost(ws->gargs_host);
+        ws->gargs_dev = nullptr;
+        ws->gargs_host = nullptr;
+        ws->gargs_cap = 0;
+        if (cudaMalloc(&ws->gargs_dev, nfull * sizeof(BatchArgs)) != cudaSuccess ||
+            cudaMallocHost(&ws->gargs_host, nfull * sizeof(BatchArgs)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate the batch argument table");
+        }
+        ws->gargs_cap = nfull;
+    }
+    if (!ws->gcursor && cudaMalloc(&ws->gcursor, 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate the batch cursor");
+    }
+    const unsigned long long key[4] = {B, (unsigned long long)qp.k,
+                                       ((unsigned long long)ix->tune_chunk_tiles << 8) | ix->tune_ctas_per_sm,
+                                       (unsigned long long)(uintptr_t)ws->bslots_dev};
+    if (!ws->graph || std::memcmp(key, ws->graph_key, sizeof(key)) != 0) {
+        if (ws->graph) cudaGraphExecDestroy(ws->graph);
+        ws->graph = nullptr;
+        cudaGraph_t graph = nullptr;
+        MESSI_CUDA(cudaStreamBeginCapture(ws->capture_stream, cudaStreamCaptureModeThreadLocal));
+        launch_batch_args(iv, qp, ws->bslots_dev, B, ws->gargs_dev, ws->gcursor, ix->tune_chunk_tiles,
+                          ix->tune_ctas_per_sm, ws->bcounter, ws->capture_stream);
+        MESSI_CUDA(cudaStreamEndCapture(ws->capture_stream, &graph));
+        const cudaError_t e = cudaGraphInstantiate(&ws->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (!cuda_ok(e, "messi_query_batched: graph instantiation")) {
+            ws->graph = nullptr;
+            return MESSI_ECUDA;
+        }
+        std::memcpy(ws->graph_key, key, sizeof(key));
+    }
+    // the staging table may still feed the previous call's copy
+    MESSI_CUDA(cudaEventSynchronize(ws->gargs_done));
+    for (unsigned b = 0; b < nfull; ++b)
+        ws->gargs_host[b] = BatchArgs{dq + (size_t)b * B * ix->len, did + (size_t)b * B * qp.k,
+                                      ddist + (size_t)b * B * qp.k, 0ull};
+    MESSI_CUDA(cudaMemcpyAsync(ws->gargs_dev, ws->gargs_host, nfull * sizeof(BatchArgs), cudaMemcpyHostToDevice, s));
+    MESSI_CUDA(cudaEventRecord(ws->gargs_done, s));
+    MESSI_CUDA(cudaMemsetAsync(ws->gcursor, 0, 4, s));
+    for (unsigned b = 0; b < nfull; ++b) MESSI_CUDA(cudaGraphLaunch(ws->graph, s));
+    ws->launches += 7ull * nfull;
+    ws->graph_replays += nfull;
+    return MESSI_OK;
+}
+
 messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, uint32_t nq, uint32_t k,
                          messi_dist dist, uint32_t window, uint32_t batch, int64_t *ids, float *dists,
                          messi_stream stream)
@@ -753,7 +822,14 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
             for (unsigned r = 0; r < nb; ++r) ws->query_ev.push_back({eq0, (int)evn - 1});
         }
     }
-    for (uint32_t g = 0; g < nq && !use_tc; g += B) {
+    // full batches of the lower-bound form replay one captured graph
+    uint32_t g_first = 0;
+    if (!use_tc && !ix->profiling && nq / B >= 2) {
+        chk = replay_lb_batches(ix, ws, iv, qp, B, nq / B, dq, did, ddist, s);
+        if (chk != MESSI_OK) return chk;
+        g_first = (nq / B) * B;
+    }
+    for (uint32_t g = g_first; g < nq && !use_tc; g += B) {
         const unsigned nb = std::min<unsigned>(B, nq - g);
         int eq0 = -1, es0 = -1;
         cudaEvent_t f0 = nullptr, f1 = nullptr;
@@ -858,6 +934,99 @@ messi_status messi_set_batch_mode(messi_index *ix, int mode)
     if (!ix || (mode != MESSI_BATCH_LB_REFINE && mode != MESSI_BATCH_TC_SCREEN))
         return fail(MESSI_EINVAL, "messi_set_batch_mode: unknown mode");
     ix->batch_mode = mode;
+    return MESSI_OK;
+}
+
+messi_status messi_set_tuning(messi_index *ix, const messi_tuning *t)
+{
+    if (!ix || !t) return fail(MESSI_EINVAL, "messi_set_tuning: null argument");
+    if (t->batch == 0 || t->batch > 65535 || t->chunk_tiles == 0 || t->chunk_tiles > 1024 ||
+        (t->ctas_per_sm != 1 && t->ctas_per_sm != 2))
+        return fail(MESSI_EINVAL, "messi_set_tuning: batch 1..65535, chunk_tiles 1..1024, ctas_per_sm 1 or 2");
+    ix->tune_batch = t->batch;
+    ix->tune_chunk_tiles = t->chunk_tiles;
+    ix->tune_ctas_per_sm = t->ctas_per_sm;
+    return MESSI_OK;
+}
+
+messi_status messi_autotune(messi_index *ix, const float *queries, uint32_t nq, uint32_t k, messi_stream stream,
+                            messi_tuning *out)
+{
+    if (!ix || !queries) return fail(MESSI_EINVAL, "messi_autotune: null argument");
+    if (nq < 32) return fail(MESSI_EINVAL, "messi_autotune: needs at least 32 queries");
+    if (!is_device_ptr(queries)) return fail(MESSI_EINVAL, "messi_autotune: queries must be a device pointer");
+    if (k == 0 || k > (uint32_t)kMaxK || k > ix->N) return fail(MESSI_EINVAL, "messi_autotune: bad k");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    struct Shape { unsigned B, ct, cps; };
+    std::vector<Shape> cand;
+    if (ix->batch_mode == MESSI_BATCH_TC_SCREEN) {
+        for (unsigned B : {128u, 256u, 512u, 1024u})
+            if (B <= nq) cand.push_back({B, ix->tune_chunk_tiles, ix->tune_ctas_per_sm});
+    } else {
+        for (unsigned B : {32u, 64u, 128u, 256u})
+            for (unsigned ct : {16u, 32u, 64u})
+                for (unsigned cps : {1u, 2u})
+                    if (B <= nq) cand.push_back({B, ct, cps});
+    }
+    if (cand.empty()) cand.push_back({std::min(nq, 32u), ix->tune_chunk_tiles, ix->tune_ctas_per_sm});
+    const unsigned Bmax = std::max_element(cand.begin(), cand.end(), [](const Shape &a, const Shape &b) {
+                              return a.B < b.B;
+                          })->B;
+    char *buf = nullptr;
+    if (cudaMalloc(&buf, (size_t)Bmax * k * 12) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MESSI_ENOMEM, "messi_autotune: cannot allocate result buffers");
+    }
+    int64_t *ids = reinterpret_cast<int64_t *>(buf);
+    float *dists = reinterpret_cast<float *>(buf + (size_t)Bmax * k * 8);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool prof = ix->profiling;
+    ix->profiling = false;
+    double best = 1e300;
+    Shape pick = cand.front();
+    messi_status st = MESSI_OK;
+    for (const Shape &c : cand) {
+        ix->tune_chunk_tiles = c.ct;
+        ix->tune_ctas_per_sm = c.cps;
+        // warm-up, then one timed batch of c.B queries (the last rows, so warm-up and
+        // timing see different queries when nq allows)
+        st = run_batched(ix, &ix->ws, queries, c.B, k, MESSI_ED, 0, c.B, ids, dists, stream);
+        if (st != MESSI_OK) break;
+        const float *tq = queries + (size_t)(nq - c.B) * ix->len;
+        cudaEventRecord(e0, s);
+        st = run_batched(ix, &ix->ws, tq, c.B, k, MESSI_ED, 0, c.B, ids, dists, stream);
+        if (st != MESSI_OK) break;
+        cudaEventRecord(e1, s);
+        if (!cuda_ok(cudaEventSynchronize(e1), "messi_autotune: timing")) {
+            st = MESSI_ECUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / c.B;
+        if (per < best) {
+            best = per;
+            pick = c;
+        }
+    }
+    ix->profiling = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (st != MESSI_OK) return st;
+    ix->tune_batch = pick.B;
+    ix->tune_chunk_tiles = pick.ct;
+    ix->tune_ctas_per_sm = pick.cps;
+    if (out) {
+        *out = messi_tuning{};
+        out->batch = pick.B;
+        out->chunk_tiles = pick.ct;
+        out->ctas_per_sm = pick.cps;
+        out->mode = (uint32_t)ix->batch_mode;
+        out->ms_per_query = best;
+    }
     return MESSI_OK;
 }
 

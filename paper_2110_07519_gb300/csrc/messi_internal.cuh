@@ -121,6 +121,15 @@ namespace messi {
 // Mutable per-call state of the query paths.  The index owns one; a server
 // owns one per stream so that batches in flight on different streams never
 // share scratch memory.
+// One batch of a graph-replayed call: where its query rows are read and its
+// results written (device pointers).
+struct BatchArgs {
+    const float *queries;
+    long long *ids;
+    float *dists;
+    unsigned long long pad;
+};
+
 struct Workspace {
     // plain path: one query slot with survivor arrays of N entries
     void *ws_block = nullptr;
@@ -145,6 +154,15 @@ struct Workspace {
     messi_stats last{};
     cudaStream_t last_stream = nullptr;
     unsigned epoch = 0;               // per-query stamp of the live-tile marks
+    // graph of one fused lower-bound batch, replayed once per batch of a call
+    cudaGraphExec_t graph = nullptr;
+    unsigned long long graph_key[4] = {0, 0, 0, 0};
+    BatchArgs *gargs_dev = nullptr, *gargs_host = nullptr;   // argument table (device, pinned staging)
+    unsigned *gcursor = nullptr;
+    size_t gargs_cap = 0;
+    unsigned long long graph_replays = 0;
+    cudaEvent_t gargs_done = nullptr;     // the staging table's last copy
+    cudaStream_t capture_stream = nullptr;
     unsigned long long tile_count = 0;   // scan tiles of the plain slot's stamp array
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, int>> scan_ev, query_ev;   // pairs of event indices
@@ -269,6 +287,9 @@ void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm,
 void launch_tc_recheck(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots, unsigned B,
                        const unsigned *cand_count, const unsigned *cand_pos, unsigned cap, const unsigned *active,
                        cudaStream_t s);
+void launch_batch_args(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
+                       const BatchArgs *args, unsigned *cursor, unsigned chunk_tiles, unsigned ctas_per_sm,
+                       unsigned *counter, cudaStream_t s);
 void launch_batch_seed(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
                        const float *queries, cudaStream_t s, unsigned long long *launches);
 void launch_batch_finalize(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,

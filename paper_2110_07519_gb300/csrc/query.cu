@@ -215,6 +215,16 @@ k_prep_batch(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, 
     prep_body(iv, qp, slots[blockIdx.x], queries + (size_t)blockIdx.x * iv.len);
 }
 
+// Graph-replayed form: the batch's query rows come from the argument table
+// entry the cursor points at.
+__global__ void __launch_bounds__(kPrepThreads)
+k_prep_batch_args(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots,
+                  const BatchArgs *__restrict__ args, const unsigned *__restrict__ cursor)
+{
+    const BatchArgs a = args[*cursor];
+    prep_body(iv, qp, slots[blockIdx.x], a.queries + (size_t)blockIdx.x * iv.len);
+}
+
 // ------------------------------------------------------------------ seed
 template <int DIST>
 __device__ __forceinline__ void seed_dist_body(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot,
@@ -1470,6 +1480,17 @@ k_finalize_batch(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slo
     finalize_body(iv, qp, slots[blockIdx.x], ids + (size_t)blockIdx.x * qp.k, dists + (size_t)blockIdx.x * qp.k);
 }
 
+__global__ void __launch_bounds__(kFinThreads)
+k_finalize_batch_args(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots,
+                      const BatchArgs *__restrict__ args, const unsigned *__restrict__ cursor)
+{
+    const BatchArgs a = args[*cursor];
+    finalize_body(iv, qp, slots[blockIdx.x], a.ids + (size_t)blockIdx.x * qp.k, a.dists + (size_t)blockIdx.x * qp.k);
+}
+
+// Last node of a replayed batch: the next replay reads the next table entry.
+__global__ void k_advance_cursor(unsigned *cursor) { *cursor += 1u; }
+
 // lower bound of every series, written in original id order
 __global__ void __launch_bounds__(256)
 k_lb_all(IndexView iv, QuerySlot slot, float *__restrict__ out)
@@ -1505,6 +1526,7 @@ void init_kernel_attributes()
     cudaFuncSetAttribute(k_lb_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
     cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinSmem);
     cudaFuncSetAttribute(k_finalize_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinSmem);
+    cudaFuncSetAttribute(k_finalize_batch_args, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinSmem);
     cudaFuncSetAttribute(k_fused_ed, cudaFuncAttributeMaxDynamicSharedMemorySize, kFuSmemFixed + kMaxLen * 4);
     init_screen_attributes();
     cudaFuncSetAttribute(k_dtw, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
@@ -1593,6 +1615,20 @@ void launch_batch(const IndexView &iv, const QueryParams &qp, const QuerySlot *s
     if (ev1) cudaEventRecord(ev1, s);
     k_finalize_batch<<<B, kFinThreads, kFinSmem, s>>>(iv, qp, slots_dev, ids, dists);
     if (launches) *launches += 5;
+}
+
+void launch_batch_args(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
+                       const BatchArgs *args, unsigned *cursor, unsigned chunk_tiles, unsigned ctas_per_sm,
+                       unsigned *counter, cudaStream_t s)
+{
+    k_prep_batch_args<<<B, kPrepThreads, 0, s>>>(iv, qp, slots_dev, args, cursor);
+    k_seed_dist_batch<0><<<dim3(8, B), 256, iv.len * 4, s>>>(iv, qp, slots_dev);
+    k_seed_select_batch<<<B, kFinThreads, 0, s>>>(iv, qp, slots_dev);
+    cudaMemsetAsync(counter, 0, 4, s);
+    const size_t sm = kFuSmemFixed + (size_t)iv.len * 4;
+    k_fused_ed<<<num_sms() * ctas_per_sm, kFuThreads, sm, s>>>(iv, qp, slots_dev, B, chunk_tiles, counter);
+    k_finalize_batch_args<<<B, kFinThreads, kFinSmem, s>>>(iv, qp, slots_dev, args, cursor);
+    k_advance_cursor<<<1, 1, 0, s>>>(cursor);
 }
 
 void launch_batch_seed(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,

@@ -39,12 +39,17 @@ def check(ids, d, ref_ids, ref_d2):
     assert err.max() <= RTOL
 
 
+@pytest.mark.parametrize("mode", ["lb", "tc"])
 @pytest.mark.parametrize("k", [1, 10])
 @pytest.mark.parametrize("batch", [1, 16, 64, 0])
-def test_batched_matches_oracle_and_plain(m, coll, k, batch):
+def test_batched_matches_oracle_and_plain(m, coll, k, batch, mode):
     x, ix, q = coll
     qd = torch.from_numpy(q).cuda()
-    ids, d = m.messi_query_batched(ix, qd, k=k, batch=batch)
+    m.messi_set_batch_mode(ix, m.MESSI_BATCH_LB_REFINE if mode == "lb" else m.MESSI_BATCH_TC_SCREEN)
+    try:
+        ids, d = m.messi_query_batched(ix, qd, k=k, batch=batch)
+    finally:
+        m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN)
     m.messi_check(ix)
     ref = oracle.knn(x, q, k)
     check(ids, d, *ref)
@@ -73,3 +78,47 @@ def test_batched_dtw_takes_per_query_kernels(m, coll):
     ids, d = m.messi_query_batched(iy, torch.from_numpy(q[:6]).cuda(), k=2, dist=m.MESSI_DTW, window=12)
     m.messi_check(iy)
     check(ids, d, *oracle.knn(sub, q[:6], 2, oracle.DTW, 12))
+
+
+def test_lb_form_graph_replay_matches_oracle(m, coll):
+    # the lower-bound form replays one captured graph per full batch; two calls
+    # with different query buffers reuse it with new argument tables
+    x, ix, _ = coll
+    m.messi_set_batch_mode(ix, m.MESSI_BATCH_LB_REFINE)
+    try:
+        for seed, nq in ((synth.QUERY_SEED + 300, 16 * 5 + 7), (synth.QUERY_SEED + 301, 16 * 3)):
+            q = synth.query_mix(x, nq, seed=seed)
+            ids, d = m.messi_query_batched(ix, torch.from_numpy(q).cuda(), k=3, batch=16)
+            m.messi_check(ix)
+            check(ids, d, *oracle.knn(x, q, 3))
+            st = m.messi_query_stats(ix)
+            assert st["queries"] == nq
+            assert st["kernel_launches"] >= 7 * (nq // 16)
+    finally:
+        m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN)
+
+
+@pytest.mark.parametrize("mode", ["lb", "tc"])
+def test_autotune_picks_a_valid_shape_and_stays_exact(m, coll, mode):
+    x, ix, _ = coll
+    m.messi_set_batch_mode(ix, m.MESSI_BATCH_LB_REFINE if mode == "lb" else m.MESSI_BATCH_TC_SCREEN)
+    try:
+        qt = synth.query_mix(x, 256, seed=synth.QUERY_SEED + 400)
+        t = m.messi_autotune(ix, torch.from_numpy(qt).cuda(), k=1)
+        assert t["batch"] in ((32, 64, 128, 256) if mode == "lb" else (128, 256))
+        assert t["chunk_tiles"] in (16, 32, 64) and t["ctas_per_sm"] in (1, 2)
+        assert t["ms_per_query"] > 0
+        q = synth.query_mix(x, 40, seed=synth.QUERY_SEED + 401)
+        ids, d = m.messi_query_batched(ix, torch.from_numpy(q).cuda(), k=2)   # batch 0: the tuned one
+        m.messi_check(ix)
+        check(ids, d, *oracle.knn(x, q, 2))
+    finally:
+        m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN)
+        m.messi_set_tuning(ix, 64, 32, 2)
+
+
+def test_set_tuning_rejects_bad_shapes(m, coll):
+    _, ix, _ = coll
+    for bad in ((0, 32, 2), (64, 0, 2), (64, 32, 3)):
+        with pytest.raises(m.MessiError):
+            m.messi_set_tuning(ix, *bad)

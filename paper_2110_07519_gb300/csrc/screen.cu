@@ -211,7 +211,8 @@ struct ScreenArgs {
 //                      stage and each finished tile to its accumulator buffer;
 //   warp 11 (relay)    waits on the mbarriers the MMA warp depends on (chunk
 //                      loaded, accumulator buffer drained) and meets the MMA
-//                      warp at a named barrier once per chunk: an mbarrier
+//                      warp at a named barrier once per two chunks (once per
+//                      chunk when a tile has an odd number): an mbarrier
 //                      wait in the thread that issues the MMAs costs it
 //                      hundreds of cycles even when the phase is complete,
 //                      a named barrier does not;
@@ -444,10 +445,11 @@ k_tc_screen(ScreenArgs a)
             const unsigned long long ad0 = tc_desc(sq, 128, sbo_q), bd0 = tc_desc(sr, 128, sbo_r);
             const unsigned qstride16 = qtile_bytes >> 4, cstride16 = chunk_bytes >> 4;
             unsigned st = 0;
+            const unsigned G = (nch % 2 == 0) ? 2u : 1u;    // chunks per meeting with the relay
             for (unsigned long long j = 0; j < nt; ++j) {
                 const unsigned ab = (unsigned)(j & 1);
                 for (unsigned c = 0; c < nch; ++c) {
-                    relay_bar_sync();
+                    if (c % G == 0) relay_bar_sync();
                     tc_fence_after();
                     if (lane == 0 && !s_fail) {
                         const unsigned long long ad = ad0 + c * (KS * 16u), bd = bd0 + st * cstride16;
@@ -473,10 +475,11 @@ k_tc_screen(ScreenArgs a)
                 if (lane == 0 && j >= 2 && !s_fail &&
                     !mbar_wait_bounded(&bar_acce[ab], (unsigned)(((j >> 1) - 1) & 1)))
                     s_fail = 1;
+                const unsigned G = (nch % 2 == 0) ? 2u : 1u;
                 for (unsigned c = 0; c < nch; ++c) {
                     if (lane == 0 && !s_fail && !mbar_wait_bounded(&bar_full[st], fpar)) s_fail = 1;
                     __syncwarp();
-                    relay_bar_sync();
+                    if (c % G == G - 1) relay_bar_sync();
                     if (++st == NS) {
                         st = 0;
                         fpar ^= 1u;

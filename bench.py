@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000, 10000, 100000])
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-max", type=int, default=60000)
+    ap.add_argument("--serve-streams", type=int, default=2, help="server worker streams")
     ap.add_argument("--batch-mode", default="tc", choices=["tc", "lb"],
                     help="batched kernels: tensor-core screen (tc) or fused lower bound + refine (lb)")
     ap.add_argument("--mix", default="mixed", choices=["mixed", "fresh", "s0.1", "s0.5", "s1.0"],
@@ -145,6 +146,23 @@ def profiled_traffic(n_series: int, kernel: str):
     if not sha or not per or sha.group(1) != scan_source_sha(kernel):
         return None
     return float(per.group(1)) * n_series
+
+
+def replica_elapsed_ms(pg, elapsed_ms, device="cpu"):
+    """Replicas only: every rank answers its own queries on its own copy of the
+    index; the job's time is the slowest rank's (max over ranks)."""
+    if not pg:
+        return elapsed_ms
+    import torch
+
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world_size, units_per_rank, elapsed_ms):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return world_size * units_per_rank / (elapsed_ms * 1e-3)
 
 
 def dist_env():
@@ -263,10 +281,7 @@ def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists, dist=
     clk = clocks.stop()
     elapsed_ms = e0.elapsed_time(e1)
     m.messi_check(ix)
-    if pg:
-        t = torch.tensor([elapsed_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = replica_elapsed_ms(pg, elapsed_ms, dev)
     # per-query latency percentiles over every timed query in one call
     if form == "plain":
         m.messi_query(ix, qpool[W * B:(W + K) * B], k=k, dist=dist, window=window)
@@ -361,7 +376,7 @@ def run_messi(args, ws, rank, local):
         q_bytes = (40.0 * n_leaves + 4.0 * ntiles + 16.0 * words_q + 8.0 * r["survivors"] / nqt
                    + 4.0 * args.len * r["rows"] / nqt)
         forms[form] = {
-            "value": ws * nqt / (r["elapsed_ms"] * 1e-3), "ms_per_step": r["elapsed_ms"] / K,
+            "value": replica_throughput(ws, nqt, r["elapsed_ms"]), "ms_per_step": r["elapsed_ms"] / K,
             "p50_ms": r["p50"], "p99_ms": r["p99"], "gpu_launches": r["launches"], "clocks": r["clocks"],
             "roofline": dict(roof, kernel=kernel, algorithmic_per_launch=algo, avg_launch_ms=kern_avg_s * 1e3,
                              launches=r["kern_launches"]),
@@ -445,7 +460,7 @@ def run_serve(args, ws, rank, local):
         m.messi_set_batch_mode(ix, mode)
         res_mode = {}
         for rate in args.serve_rates:
-            srv = m.messi_server_create(ix, max_batch=1024, max_k=16, streams=2)
+            srv = m.messi_server_create(ix, max_batch=1024, max_k=16, streams=args.serve_streams)
             rng = np.random.default_rng(int(rate))
             total = int(min(args.serve_seconds * rate, args.serve_max))
             kinds = rng.random(total) < 0.2
@@ -484,6 +499,7 @@ def run_serve(args, ws, rank, local):
         out[mode_name] = res_mode
     print(json.dumps({"mode": "serve", "config": {"workload": f"{n} x {length} fp32 random walks, 80% ED / 20% DTW "
                                                               f"(window {r_dtw}), k in {{1,10}}, Poisson arrivals",
+                                                  "streams": args.serve_streams,
                                                   "data": DATA_DESC},
                       "results": out}), flush=True)
 

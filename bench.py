@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000, 10000, 100000])
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-max", type=int, default=60000)
-    ap.add_argument("--serve-streams", type=int, default=2, help="server worker streams")
+    ap.add_argument("--serve-streams", type=int, default=4, help="server worker streams")
     ap.add_argument("--batch-mode", default="tc", choices=["tc", "lb"],
                     help="batched kernels: tensor-core screen (tc) or fused lower bound + refine (lb)")
     ap.add_argument("--mix", default="mixed", choices=["mixed", "fresh", "s0.1", "s0.5", "s1.0"],

@@ -52,7 +52,7 @@ typedef enum {
     MESSI_ECUDA = 3,    /* a CUDA runtime call failed                         */
     MESSI_ETIMEOUT = 4, /* a device-side bounded wait ran out                 */
     MESSI_EBUSY = 5,    /* result not ready yet (server poll) / queue full    */
-    MESSI_ETIES = 6     /* more near-ties than the exact tie resolver holds   */
+    MESSI_ETIES = 6     /* accepted near-ties were dropped (a full log)       */
 } messi_status;
 
 /* Build options.  Zero-initialised fields take their defaults. */
@@ -143,7 +143,12 @@ messi_status messi_query(const messi_index *ix, const float *queries, uint32_t n
  *     (an f16 copy of the rows, 2*len bytes per series, is built on first
  *     use); otherwise, or for DTW, the call takes the other kernels.
  *   MESSI_BATCH_LB_REFINE: a persistent fused lower-bound-then-refine kernel
- *     where the queries of a batch share each pass over the iSAX words.
+ *     where the queries of a batch share each pass over the iSAX words; every
+ *     full batch of a call replays one captured CUDA graph.
+ * A query a batch cannot settle exactly (a screen that keeps overflowing, or
+ * more accepted near-ties than a batch slot logs) is answered again by the
+ * per-query kernels, so results equal messi_query's.  Both modes synchronise
+ * `stream` (they read per-batch outcomes on the host).
  * DTW queries are answered by the per-query kernels. */
 messi_status messi_query_batched(const messi_index *ix, const float *queries, uint32_t nq,
                                  uint32_t k, messi_dist dist, uint32_t window, uint32_t batch,

@@ -335,10 +335,11 @@ bool cuda_ok(cudaError_t e, const char *what)
 
 void free_workspace(Workspace &w)
 {
-    void *ptrs[] = {w.ws_block, w.stage_block, w.bws_block, w.tcws_block, w.gargs_dev, w.gcursor};
+    void *ptrs[] = {w.ws_block, w.stage_block, w.bws_block, w.tcws_block, w.gargs_dev, w.gcursor, w.redo_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.gargs_host) cudaFreeHost(w.gargs_host);
+    if (w.redo_host) cudaFreeHost(w.redo_host);
     if (w.graph) cudaGraphExecDestroy(w.graph);
     if (w.gargs_done) cudaEventDestroy(w.gargs_done);
     if (w.capture_stream) cudaStreamDestroy(w.capture_stream);
@@ -655,6 +656,41 @@ messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uin
     return MESSI_OK;
 }
 
+// One query on the per-query kernels (the plain slot), for queries a batch
+// could not settle.
+static messi_status answer_one(messi_index *ix, Workspace *ws, const IndexView &iv, const QueryParams &qp,
+                               const float *q, long long *ids, float *dists, cudaStream_t s)
+{
+    messi_status chk = ensure_workspace(ix, ws);
+    if (chk != MESSI_OK) return chk;
+    const QuerySlot one = ws->slot;
+    MESSI_CUDA(cudaMemsetAsync(one.acc, 0, sizeof(QueryCounters), s));
+    launch_prep(iv, qp, one, q, s);
+    launch_seed(iv, qp, one, s, &ws->launches);
+    launch_scan(iv, qp, one, next_epoch(ws, s), s);
+    launch_refine(iv, qp, one, s, &ws->launches);
+    launch_finalize(iv, qp, one, ids, dists, s);
+    ws->launches += 3;
+    return MESSI_OK;
+}
+
+// Per-query redo flags of a batched call (device, pinned host copy).
+static messi_status ensure_redo(Workspace *ws, size_t nq)
+{
+    if (ws->redo_cap >= nq) return MESSI_OK;
+    if (ws->redo_dev) cudaFree(ws->redo_dev);
+    if (ws->redo_host) cudaFreeHost(ws->redo_host);
+    ws->redo_dev = nullptr;
+    ws->redo_host = nullptr;
+    ws->redo_cap = 0;
+    if (cudaMalloc(&ws->redo_dev, nq * 4) != cudaSuccess || cudaMallocHost(&ws->redo_host, nq * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate the redo flags");
+    }
+    ws->redo_cap = nq;
+    return MESSI_OK;
+}
+
 // The lower-bound batch form as a CUDA graph: one batch (prep, seed, fused
 // scan-and-refine, finalize, cursor advance) is captured once per shape on a
 // private stream, with its query rows and result rows read from an argument
@@ -662,7 +698,7 @@ messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uin
 // stream, the table advancing by one entry per replay.
 static messi_status replay_lb_batches(messi_index *ix, Workspace *ws, const IndexView &iv, const QueryParams &qp,
                                       unsigned B, unsigned nfull, const float *dq, long long *did, float *ddist,
-                                      cudaStream_t s)
+                                      unsigned *redo, cudaStream_t s)
 {
     if (!ws->capture_stream && !cuda_ok(cudaStreamCreateWithFlags(&ws->capture_stream, cudaStreamNonBlocking),
                                         "messi_query_batched: capture stream"))
@@ -710,7 +746,7 @@ static messi_status replay_lb_batches(messi_index *ix, Workspace *ws, const Inde
     MESSI_CUDA(cudaEventSynchronize(ws->gargs_done));
     for (unsigned b = 0; b < nfull; ++b)
         ws->gargs_host[b] = BatchArgs{dq + (size_t)b * B * ix->len, did + (size_t)b * B * qp.k,
-                                      ddist + (size_t)b * B * qp.k, 0ull};
+                                      ddist + (size_t)b * B * qp.k, redo + (size_t)b * B};
     MESSI_CUDA(cudaMemcpyAsync(ws->gargs_dev, ws->gargs_host, nfull * sizeof(BatchArgs), cudaMemcpyHostToDevice, s));
     MESSI_CUDA(cudaEventRecord(ws->gargs_done, s));
     MESSI_CUDA(cudaMemsetAsync(ws->gcursor, 0, 4, s));
@@ -765,6 +801,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
     if (use_tc && (chk = ensure_screen_copy(ix, s)) != MESSI_OK) return chk;
     use_tc = use_tc && ix->screen_state == 1;
     if (use_tc && (chk = ensure_tc_workspace(ix, ws, B)) != MESSI_OK) return chk;
+    if ((chk = ensure_redo(ws, nq)) != MESSI_OK) return chk;
     for (uint32_t g = 0; g < nq && use_tc; g += B) {
         const unsigned nb = std::min<unsigned>(B, nq - g);
         int eq0 = -1, es0 = -1;
@@ -796,27 +833,21 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
             MESSI_CUDA(cudaMemcpyAsync(&more, w.n_active, 4, cudaMemcpyDeviceToHost, s));
             MESSI_CUDA(cudaStreamSynchronize(s));
         }
-        launch_batch_finalize(iv, qp, ws->bslots_dev, nb, did + (size_t)g * k, ddist + (size_t)g * k, s, &ws->launches);
-        // queries the screen could not settle (values outside f16 range, or
-        // still overflowing after three passes): the per-query kernels
-        std::vector<unsigned> hflags(nb), hact(nb);
+        launch_batch_finalize(iv, qp, ws->bslots_dev, nb, did + (size_t)g * k, ddist + (size_t)g * k,
+                              ws->redo_dev + g, s, &ws->launches);
+        // queries the screen could not settle (values outside f16 range, still
+        // overflowing after three passes, or a near-tie log that overflowed):
+        // the per-query kernels
+        std::vector<unsigned> hflags(nb), hact(nb), hredo(nb);
         MESSI_CUDA(cudaMemcpyAsync(hflags.data(), w.flags, nb * 4, cudaMemcpyDeviceToHost, s));
         MESSI_CUDA(cudaMemcpyAsync(hact.data(), w.active, nb * 4, cudaMemcpyDeviceToHost, s));
+        MESSI_CUDA(cudaMemcpyAsync(hredo.data(), ws->redo_dev + g, nb * 4, cudaMemcpyDeviceToHost, s));
         MESSI_CUDA(cudaStreamSynchronize(s));
-        for (unsigned b = 0; b < nb; ++b) {
-            if ((hflags[b] & 4u) || hact[b]) {
-                if ((chk = ensure_workspace(ix, ws)) != MESSI_OK) return chk;
-                QueryParams q1 = qp;
-                const QuerySlot one = ws->slot;
-                MESSI_CUDA(cudaMemsetAsync(one.acc, 0, sizeof(QueryCounters), s));
-                launch_prep(iv, q1, one, dq + (size_t)(g + b) * ix->len, s);
-                launch_seed(iv, q1, one, s, &ws->launches);
-                launch_scan(iv, q1, one, next_epoch(ws, s), s);
-                launch_refine(iv, q1, one, s, &ws->launches);
-                launch_finalize(iv, q1, one, did + (size_t)(g + b) * k, ddist + (size_t)(g + b) * k, s);
-                ws->launches += 3;
-            }
-        }
+        for (unsigned b = 0; b < nb; ++b)
+            if ((hflags[b] & 4u) || hact[b] || hredo[b])
+                if ((chk = answer_one(ix, ws, iv, qp, dq + (size_t)(g + b) * ix->len, did + (size_t)(g + b) * k,
+                                      ddist + (size_t)(g + b) * k, s)) != MESSI_OK)
+                    return chk;
         if (ix->profiling) {
             cudaEventRecord(pool_event(ws, evn++), s);
             for (unsigned r = 0; r < nb; ++r) ws->query_ev.push_back({eq0, (int)evn - 1});
@@ -825,7 +856,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
     // full batches of the lower-bound form replay one captured graph
     uint32_t g_first = 0;
     if (!use_tc && !ix->profiling && nq / B >= 2) {
-        chk = replay_lb_batches(ix, ws, iv, qp, B, nq / B, dq, did, ddist, s);
+        chk = replay_lb_batches(ix, ws, iv, qp, B, nq / B, dq, did, ddist, ws->redo_dev, s);
         if (chk != MESSI_OK) return chk;
         g_first = (nq / B) * B;
     }
@@ -841,12 +872,24 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
             f1 = pool_event(ws, evn++);
         }
         launch_batch(iv, qp, ws->bslots_dev, nb, dq + (size_t)g * ix->len, did + (size_t)g * k, ddist + (size_t)g * k,
-                     ix->tune_chunk_tiles, ix->tune_ctas_per_sm, ws->bcounter, s, &ws->launches, f0, f1);
+                     ws->redo_dev + g, ix->tune_chunk_tiles, ix->tune_ctas_per_sm, ws->bcounter, s, &ws->launches,
+                     f0, f1);
         if (ix->profiling) {
             ws->scan_ev.push_back({es0, es0 + 1});
             cudaEventRecord(pool_event(ws, evn++), s);
             for (unsigned r = 0; r < nb; ++r) ws->query_ev.push_back({eq0, (int)evn - 1});
         }
+    }
+    if (!use_tc) {
+        // the lower-bound form runs without host decisions; queries whose
+        // near-tie log overflowed (a mass tie) are answered again here
+        MESSI_CUDA(cudaMemcpyAsync(ws->redo_host, ws->redo_dev, (size_t)nq * 4, cudaMemcpyDeviceToHost, s));
+        MESSI_CUDA(cudaStreamSynchronize(s));
+        for (uint32_t i = 0; i < nq; ++i)
+            if (ws->redo_host[i])
+                if ((chk = answer_one(ix, ws, iv, qp, dq + (size_t)i * ix->len, did + (size_t)i * k,
+                                      ddist + (size_t)i * k, s)) != MESSI_OK)
+                    return chk;
     }
     MESSI_CUDA(cudaGetLastError());
     ws->last = messi_stats{};
@@ -1045,7 +1088,7 @@ messi_status messi_check(const messi_index *ix, messi_stream stream)
     MESSI_CUDA(cudaMemcpy(&st, ix->status, 4, cudaMemcpyDeviceToHost));
     MESSI_CUDA(cudaMemset(ix->status, 0, 4));
     if (st & kStTimeout) return fail(MESSI_ETIMEOUT, "a device-side bounded wait ran out");
-    if (st & kStTieOverflow) return fail(MESSI_ETIES, "more near-tied candidates than the tie log holds");
+    if (st & kStTieOverflow) return fail(MESSI_ETIES, "accepted near-tie candidates were dropped from a full log");
     if (st & kStInvalidQuery) return fail(MESSI_EINVAL, "a query held a non-finite value");
     return MESSI_OK;
 }

@@ -127,7 +127,7 @@ struct BatchArgs {
     const float *queries;
     long long *ids;
     float *dists;
-    unsigned long long pad;
+    unsigned *redo;     // per query: 1 when the batch could not answer it exactly
 };
 
 struct Workspace {
@@ -158,6 +158,8 @@ struct Workspace {
     cudaGraphExec_t graph = nullptr;
     unsigned long long graph_key[4] = {0, 0, 0, 0};
     BatchArgs *gargs_dev = nullptr, *gargs_host = nullptr;   // argument table (device, pinned staging)
+    unsigned *redo_dev = nullptr, *redo_host = nullptr;       // per-query redo flags of a batched call
+    size_t redo_cap = 0;
     unsigned *gcursor = nullptr;
     size_t gargs_cap = 0;
     unsigned long long graph_replays = 0;
@@ -293,11 +295,11 @@ void launch_batch_args(const IndexView &iv, const QueryParams &qp, const QuerySl
 void launch_batch_seed(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
                        const float *queries, cudaStream_t s, unsigned long long *launches);
 void launch_batch_finalize(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
-                           long long *ids, float *dists, cudaStream_t s, unsigned long long *launches);
+                           long long *ids, float *dists, unsigned *redo, cudaStream_t s, unsigned long long *launches);
 void launch_batch(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
-                  const float *queries, long long *ids, float *dists, unsigned chunk_tiles, unsigned ctas_per_sm,
-                  unsigned *counter, cudaStream_t s, unsigned long long *launches, cudaEvent_t ev0 = nullptr,
-                  cudaEvent_t ev1 = nullptr);
+                  const float *queries, long long *ids, float *dists, unsigned *redo, unsigned chunk_tiles,
+                  unsigned ctas_per_sm, unsigned *counter, cudaStream_t s, unsigned long long *launches,
+                  cudaEvent_t ev0, cudaEvent_t ev1);
 void launch_reset_state(QuerySlot slot, cudaStream_t s);
 float band_factor(int dist, int len);
 

@@ -1314,10 +1314,132 @@ __device__ void block_bitonic(unsigned npow, Less less, Swap swap)
         }
 }
 
-constexpr int kFinSmem = kLogCap * (8 + 8);
+// candidates and their FP64 distances (kLogCap each), then a running top-k
+// (kMaxK each) for band populations larger than one pass
+constexpr int kFinSmem = kLogCap * (8 + 8) + kMaxK * (8 + 8);
 
+// FP64 squared distance of each of the c candidates, in the operation order of
+// the FP64 reference evaluation (ED: a thread per candidate; DTW: a warp).
+__device__ __forceinline__ void fin_fp64(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot,
+                                         const unsigned long long *cand, double *d64, unsigned c)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    if (qp.dist == 0) {
+        for (unsigned e = tid; e < c; e += blockDim.x) {
+            const unsigned pos = iv.pos_of_id[cand_id(cand[e])];
+            const float *x = iv.raw + (unsigned long long)pos * iv.len;
+            double s = 0.0;
+            for (int t = 0; t < iv.len; ++t) {
+                const double d = __dsub_rn((double)slot.q[t], (double)x[t]);
+                s = __dadd_rn(s, __dmul_rn(d, d));
+            }
+            d64[e] = s;
+        }
+    } else {
+        double *diag = slot.dtw64 + (size_t)wib * 3 * iv.len;
+        for (unsigned e = wib; e < c; e += blockDim.x >> 5) {
+            const unsigned pos = iv.pos_of_id[cand_id(cand[e])];
+            const double v = warp_dtw<double>(slot.q, iv.raw + (unsigned long long)pos * iv.len, iv.len, qp.r, diag,
+                                              (double)f_inf());
+            if (lane == 0) d64[e] = v;
+            __syncwarp();
+        }
+    }
+}
+
+// Sort n (power of two) entries by (FP64 distance, id).
+__device__ __forceinline__ void fin_sort64(unsigned long long *cand, double *d64, unsigned n)
+{
+    block_bitonic(
+        n,
+        [&](unsigned i, unsigned j) {
+            return d64[i] < d64[j] || (d64[i] == d64[j] && cand_id(cand[i]) < cand_id(cand[j]));
+        },
+        [&](unsigned i, unsigned j) {
+            const double td = d64[i];
+            d64[i] = d64[j];
+            d64[j] = td;
+            const unsigned long long t = cand[i];
+            cand[i] = cand[j];
+            cand[j] = t;
+        });
+}
+
+// More candidates in the band than one pass holds (a mass tie, e.g. many
+// identical rows): the log is taken in windows of kLogCap entries; each
+// window's in-band candidates are ranked in FP64 and merged with a running
+// top-k, the same row never counted twice.  Exact for any band population.
+__device__ void fin_streamed(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot, float band,
+                             unsigned nlog, unsigned long long *cand, double *d64, unsigned long long *rp, double *rd,
+                             long long *ids, float *dists)
+{
+    __shared__ unsigned ncw, rc;
+    __shared__ unsigned long long seen;
+    const int tid = threadIdx.x;
+    const unsigned k = (unsigned)qp.k;
+    if (tid == 0) {
+        rc = 0;
+        seen = 0;
+    }
+    __syncthreads();
+    for (unsigned w0 = 0; w0 < nlog; w0 += kLogCap) {
+        if (tid == 0) ncw = 0;
+        __syncthreads();
+        const unsigned w1 = min(nlog, w0 + (unsigned)kLogCap);
+        for (unsigned i = w0 + tid; i < w1; i += blockDim.x) {
+            const unsigned long long P = slot.log[i];
+            if (cand_d2(P) <= band) cand[atomicAdd(&ncw, 1u)] = P;
+        }
+        __syncthreads();
+        const unsigned c = ncw;
+        if (tid == 0) seen += c;
+        fin_fp64(iv, qp, slot, cand, d64, c);
+        unsigned npow = 1;
+        while (npow < c) npow <<= 1;
+        for (unsigned i = c + tid; i < npow; i += blockDim.x) {
+            cand[i] = kEmpty;
+            d64[i] = (double)f_inf();
+        }
+        __syncthreads();
+        fin_sort64(cand, d64, npow);
+        // the window's best k, then the running top-k, ranked together
+        const unsigned m = min(k, c), r0 = rc, tot = m + r0;
+        for (unsigned i = tid; i < r0; i += blockDim.x) {
+            cand[m + i] = rp[i];
+            d64[m + i] = rd[i];
+        }
+        unsigned np2 = 1;
+        while (np2 < tot) np2 <<= 1;
+        for (unsigned i = tot + tid; i < np2; i += blockDim.x) {
+            cand[i] = kEmpty;
+            d64[i] = (double)f_inf();
+        }
+        __syncthreads();
+        fin_sort64(cand, d64, np2);
+        if (tid == 0) {
+            unsigned out = 0;
+            for (unsigned i = 0; i < tot && out < k; ++i) {
+                if (i > 0 && cand[i] == cand[i - 1]) continue;   // the same row logged twice
+                rp[out] = cand[i];
+                rd[out] = d64[i];
+                ++out;
+            }
+            rc = out;
+        }
+        __syncthreads();
+    }
+    for (unsigned i = tid; i < k; i += blockDim.x) {
+        ids[i] = i < rc ? (long long)cand_id(rp[i]) : -1;
+        dists[i] = i < rc ? (float)sqrt(rd[i]) : f_inf();
+    }
+    if (tid == 0) slot.st->c.tie_rechecks += seen;
+}
+
+// redo (batched slots, may be null): instead of reporting a log overflow in the
+// status word, mark the query so the caller answers it again on the per-query
+// path, whose log cannot overflow.
 __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot,
-                                              long long *ids, float *dists)
+                                              long long *ids, float *dists, unsigned *redo = nullptr)
 {
     extern __shared__ __align__(16) unsigned char fsm[];
     unsigned long long *cand = reinterpret_cast<unsigned long long *>(fsm);
@@ -1337,11 +1459,12 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
     const unsigned long long T = st->thr;
     const float band = prune_threshold(T, qp.F);
     const unsigned logged = st->log_count;
-    __shared__ int overflow;
+    __shared__ int lost, many;
     if (tid == 0) {
         ncand = 0;
         ambiguous = 0;
-        overflow = logged > slot.log_cap;
+        lost = logged > slot.log_cap;    // accepted candidates were dropped: cannot be exact
+        many = 0;
     }
     __syncthreads();
     const unsigned nlog = min(logged, slot.log_cap);
@@ -1350,11 +1473,33 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
         if (cand_d2(P) <= band) {
             const unsigned o = atomicAdd(&ncand, 1u);
             if (o < (unsigned)kLogCap) cand[o] = P;
-            else overflow = 1;
+            else many = 1;
         }
     }
     __syncthreads();
-    if (tid == 0 && overflow) atomicOr(iv.status, kStTieOverflow);
+    if (tid == 0) {
+        if (redo) *redo = lost ? 1u : 0u;
+        else if (lost) atomicOr(iv.status, kStTieOverflow);
+    }
+    if (many) {
+        unsigned long long *rp = reinterpret_cast<unsigned long long *>(fsm + kLogCap * 16);
+        double *rd = reinterpret_cast<double *>(fsm + kLogCap * 16 + kMaxK * 8);
+        fin_streamed(iv, qp, slot, band, nlog, cand, d64, rp, rd, ids, dists);
+        __syncthreads();
+        QueryCounters *acc = slot.acc;
+        if (tid == 0 && acc) {
+            atomicAdd(&acc->lb_evaluated, st->c.lb_evaluated);
+            atomicAdd(&acc->lb_survivors, st->c.lb_survivors);
+            atomicAdd(&acc->lbk_survivors, st->c.lbk_survivors);
+            atomicAdd(&acc->seeded, st->c.seeded);
+            atomicAdd(&acc->refined, st->c.refined);
+            atomicAdd(&acc->abandoned, st->c.abandoned);
+            atomicAdd(&acc->bsf_updates, st->c.bsf_updates);
+            atomicAdd(&acc->tie_rechecks, st->c.tie_rechecks);
+            atomicAdd(&acc->leaves_live, st->c.leaves_live);
+        }
+        return;
+    }
     const unsigned c = min(ncand, (unsigned)kLogCap);
     unsigned npow = 1;
     while (npow < c) npow <<= 1;
@@ -1410,43 +1555,10 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
     } else {
         // FP64 recomputation of every candidate in the band, in the operation
         // order of the FP64 reference evaluation
-        const int lane = tid & 31, wib = tid >> 5;
-        if (qp.dist == 0) {
-            for (unsigned e = tid; e < cu; e += blockDim.x) {
-                const unsigned pos = iv.pos_of_id[cand_id(cand[e])];
-                const float *x = iv.raw + (unsigned long long)pos * iv.len;
-                double s = 0.0;
-                for (int t = 0; t < iv.len; ++t) {
-                    const double d = __dsub_rn((double)slot.q[t], (double)x[t]);
-                    s = __dadd_rn(s, __dmul_rn(d, d));
-                }
-                d64[e] = s;
-            }
-        } else {
-            double *diag = slot.dtw64 + (size_t)wib * 3 * iv.len;
-            for (unsigned e = wib; e < cu; e += blockDim.x >> 5) {
-                const unsigned pos = iv.pos_of_id[cand_id(cand[e])];
-                const double v = warp_dtw<double>(slot.q, iv.raw + (unsigned long long)pos * iv.len, iv.len,
-                                                  qp.r, diag, (double)f_inf());
-                if (lane == 0) d64[e] = v;
-                __syncwarp();
-            }
-        }
+        fin_fp64(iv, qp, slot, cand, d64, cu);
         for (unsigned i = cu + tid; i < npow; i += blockDim.x) d64[i] = (double)f_inf();
         __syncthreads();
-        block_bitonic(
-            npow,
-            [&](unsigned i, unsigned j) {
-                return d64[i] < d64[j] || (d64[i] == d64[j] && cand_id(cand[i]) < cand_id(cand[j]));
-            },
-            [&](unsigned i, unsigned j) {
-                const double td = d64[i];
-                d64[i] = d64[j];
-                d64[j] = td;
-                const unsigned long long t = cand[i];
-                cand[i] = cand[j];
-                cand[j] = t;
-            });
+        fin_sort64(cand, d64, npow);
         for (unsigned i = tid; i < k; i += blockDim.x) {
             ids[i] = i < cu ? (long long)cand_id(cand[i]) : -1;
             dists[i] = i < cu ? (float)sqrt(d64[i]) : f_inf();
@@ -1475,9 +1587,11 @@ k_finalize(IndexView iv, QueryParams qp, QuerySlot slot, long long *ids, float *
 }
 
 __global__ void __launch_bounds__(kFinThreads)
-k_finalize_batch(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, long long *ids, float *dists)
+k_finalize_batch(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, long long *ids, float *dists,
+                 unsigned *redo)
 {
-    finalize_body(iv, qp, slots[blockIdx.x], ids + (size_t)blockIdx.x * qp.k, dists + (size_t)blockIdx.x * qp.k);
+    finalize_body(iv, qp, slots[blockIdx.x], ids + (size_t)blockIdx.x * qp.k, dists + (size_t)blockIdx.x * qp.k,
+                  redo + blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kFinThreads)
@@ -1485,7 +1599,8 @@ k_finalize_batch_args(IndexView iv, QueryParams qp, const QuerySlot *__restrict_
                       const BatchArgs *__restrict__ args, const unsigned *__restrict__ cursor)
 {
     const BatchArgs a = args[*cursor];
-    finalize_body(iv, qp, slots[blockIdx.x], a.ids + (size_t)blockIdx.x * qp.k, a.dists + (size_t)blockIdx.x * qp.k);
+    finalize_body(iv, qp, slots[blockIdx.x], a.ids + (size_t)blockIdx.x * qp.k, a.dists + (size_t)blockIdx.x * qp.k,
+                  a.redo + blockIdx.x);
 }
 
 // Last node of a replayed batch: the next replay reads the next table entry.
@@ -1601,9 +1716,9 @@ void launch_finalize(const IndexView &iv, const QueryParams &qp, QuerySlot slot,
 }
 
 void launch_batch(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
-                  const float *queries, long long *ids, float *dists, unsigned chunk_tiles, unsigned ctas_per_sm,
-                  unsigned *counter, cudaStream_t s, unsigned long long *launches, cudaEvent_t ev0,
-                  cudaEvent_t ev1)
+                  const float *queries, long long *ids, float *dists, unsigned *redo, unsigned chunk_tiles,
+                  unsigned ctas_per_sm, unsigned *counter, cudaStream_t s, unsigned long long *launches,
+                  cudaEvent_t ev0, cudaEvent_t ev1)
 {
     k_prep_batch<<<B, kPrepThreads, 0, s>>>(iv, qp, slots_dev, queries);
     k_seed_dist_batch<0><<<dim3(8, B), 256, iv.len * 4, s>>>(iv, qp, slots_dev);
@@ -1613,7 +1728,7 @@ void launch_batch(const IndexView &iv, const QueryParams &qp, const QuerySlot *s
     if (ev0) cudaEventRecord(ev0, s);
     k_fused_ed<<<num_sms() * ctas_per_sm, kFuThreads, sm, s>>>(iv, qp, slots_dev, B, chunk_tiles, counter);
     if (ev1) cudaEventRecord(ev1, s);
-    k_finalize_batch<<<B, kFinThreads, kFinSmem, s>>>(iv, qp, slots_dev, ids, dists);
+    k_finalize_batch<<<B, kFinThreads, kFinSmem, s>>>(iv, qp, slots_dev, ids, dists, redo);
     if (launches) *launches += 5;
 }
 
@@ -1641,9 +1756,9 @@ void launch_batch_seed(const IndexView &iv, const QueryParams &qp, const QuerySl
 }
 
 void launch_batch_finalize(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots_dev, unsigned B,
-                           long long *ids, float *dists, cudaStream_t s, unsigned long long *launches)
+                           long long *ids, float *dists, unsigned *redo, cudaStream_t s, unsigned long long *launches)
 {
-    k_finalize_batch<<<B, kFinThreads, kFinSmem, s>>>(iv, qp, slots_dev, ids, dists);
+    k_finalize_batch<<<B, kFinThreads, kFinSmem, s>>>(iv, qp, slots_dev, ids, dists, redo);
     if (launches) *launches += 1;
 }
 

@@ -160,6 +160,29 @@ def test_ties_go_to_lowest_id(m):
     assert d.cpu().numpy()[0].tolist() == [0.0, 0.0, 0.0]
 
 
+def test_mass_ties_resolved_exactly(m):
+    # 10,001 identical rows (more than one pass of the tie resolver holds) and
+    # an all-zero query, against which every z-normalised row lies at nearly
+    # the same distance: both resolve exactly, in every query form
+    x = synth.random_walks(30_000, 128, seed=51)
+    x[10_000:20_000] = x[123]
+    ix = m.messi_build(cuda(x), 16, 256)
+    q = np.stack([x[123], np.zeros(128, np.float32)])
+    for k in (1, 7):
+        ref = oracle.knn(x, q, k)
+        ids, d = m.messi_query(ix, cuda(q), k=k)
+        m.messi_check(ix)
+        check_knn(ids, d, *ref)
+        for mode in (m.MESSI_BATCH_LB_REFINE, m.MESSI_BATCH_TC_SCREEN):
+            m.messi_set_batch_mode(ix, mode)
+            ids, d = m.messi_query_batched(ix, cuda(q), k=k)
+            m.messi_check(ix)
+            check_knn(ids, d, *ref)
+    ids, d = m.messi_query(ix, cuda(q[:1]), k=3)
+    assert ids.cpu().numpy()[0].tolist() == [123, 10_000, 10_001]
+    assert d.cpu().numpy()[0].tolist() == [0.0, 0.0, 0.0]
+
+
 @pytest.mark.parametrize("N,k", [(1, 1), (2, 2), (50, 50), (1037, 7), (4099, 1024)])
 def test_ed_edge_sizes(m, N, k):
     x = synth.random_walks(N, 64, seed=N)

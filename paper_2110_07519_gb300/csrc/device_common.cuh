@@ -314,6 +314,62 @@ __device__ T warp_dtw(const float *__restrict__ q, const float *__restrict__ x, 
     return diag[(last % 3) * n + (n - 1)];
 }
 
+// Survivors are stored in per-scan-CTA regions; a refine block turns the
+// region counts into a prefix over 32-entry chunks so warps can take chunks
+// by index.  Returns the number of chunks.
+__device__ __forceinline__ unsigned chunk_prefix(const QuerySlot &slot, unsigned G, unsigned *prefix, unsigned *counts)
+{
+    __shared__ unsigned part[32];
+    const unsigned per = (G + blockDim.x - 1) / blockDim.x;
+    const unsigned lo = threadIdx.x * per, hi = min(lo + per, G);
+    unsigned sum = 0;
+    for (unsigned c = lo; c < hi; ++c) {
+        const unsigned n = slot.region_count[c];
+        counts[c] = n;
+        sum += (n + 31) >> 5;
+    }
+    // block-wide exclusive scan of the per-thread sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned inc = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) part[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        unsigned v = lane < nw ? part[lane] : 0u;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += y;
+        }
+        if (lane < nw) part[lane] = v;
+    }
+    __syncthreads();
+    unsigned run = (warp ? part[warp - 1] : 0u) + inc - sum;
+    for (unsigned c = lo; c < hi; ++c) {
+        prefix[c] = run;
+        run += (counts[c] + 31) >> 5;
+    }
+    if (threadIdx.x == blockDim.x - 1) prefix[G] = run;
+    __syncthreads();
+    return prefix[G];
+}
+
+// region holding chunk `ch`: the last c with prefix[c] <= ch
+__device__ __forceinline__ unsigned region_of(unsigned ch, const unsigned *prefix, unsigned G)
+{
+    unsigned lo = 0, hi = G;
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (prefix[mid] <= ch) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // ------------------------------------------------------- bound ordering
 // Bucket of a non-negative FP32 lower bound: its exponent and top 4 mantissa
 // bits, monotone in the bound.  order_floor(b) is the smallest bound in b.

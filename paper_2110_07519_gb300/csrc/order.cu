@@ -26,35 +26,47 @@ constexpr int kOrderThreads = 256;
 
 // Visit the survivors of SRC: 0 = scan regions (surv_pos / surv_lb, region g
 // at g * region_words holding region_count[g] entries), 1 = compact list
-// (surv2 / surv2_lb, surv2_count entries).  Whole warps step together (so
-// warp collectives see all 32 lanes); a lane past the end gets valid = false.
-// A block visits the same entries in the same order every time it is called
-// within one launch.
+// (surv2 / surv2_lb, surv2_count entries).  A warp takes 32 entries at a time
+// (for regions: 32-entry chunks numbered across all regions, so every block
+// has work however the survivors are spread), and all 32 lanes step
+// together (warp collectives see the whole warp); a lane past the end gets
+// valid = false.  A block visits the same entries in the same order every
+// time it is called within one launch.  `prefix` / `counts` hold the chunk
+// prefix of the regions (chunk_prefix) for SRC 0.
 template <int SRC, typename F>
-__device__ __forceinline__ void for_each_survivor(const QuerySlot &slot, F f)
+__device__ __forceinline__ void for_each_survivor(const QuerySlot &slot, unsigned nchunks, const unsigned *prefix,
+                                                  const unsigned *counts, F f)
 {
     const QueryState *st = slot.st;
-    const unsigned lane = threadIdx.x & 31, wbase = threadIdx.x & ~31u;
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     if (SRC == 0) {
         const unsigned G = st->scan_grid;
         const unsigned long long RW = st->region_words;
-        for (unsigned g = blockIdx.x; g < G; g += gridDim.x) {
-            const unsigned n = slot.region_count[g];
-            const unsigned long long base = g * RW;
-            for (unsigned i0 = wbase; i0 < n; i0 += blockDim.x) {
-                const unsigned i = i0 + lane;
-                const bool valid = i < n;
-                f(valid, valid ? slot.surv_pos[base + i] : 0u, valid ? slot.surv_lb[base + i] : 0.f);
-            }
+        for (unsigned ch = blockIdx.x * wpb + wib; ch < nchunks; ch += gridDim.x * wpb) {
+            const unsigned rg = region_of(ch, prefix, G);
+            const unsigned within = (ch - prefix[rg]) * 32 + lane;
+            const bool valid = within < counts[rg];
+            const unsigned long long i = rg * RW + within;
+            f(valid, valid ? slot.surv_pos[i] : 0u, valid ? slot.surv_lb[i] : 0.f);
         }
     } else {
         const unsigned n = st->surv2_count;
-        for (unsigned i0 = blockIdx.x * blockDim.x + wbase; i0 < n; i0 += gridDim.x * blockDim.x) {
+        for (unsigned i0 = blockIdx.x * blockDim.x + wib * 32; i0 < n; i0 += gridDim.x * blockDim.x) {
             const unsigned i = i0 + lane;
             const bool valid = i < n;
             f(valid, valid ? slot.surv2[i] : 0u, valid ? slot.surv2_lb[i] : 0.f);
         }
     }
+}
+
+// chunk prefix of the scan regions (SRC 0); also the block barrier that
+// publishes the zeroed histogram
+template <int SRC>
+__device__ __forceinline__ unsigned survivor_chunks(const QuerySlot &slot, unsigned *prefix, unsigned *counts)
+{
+    if (SRC == 0) return chunk_prefix(slot, slot.st->scan_grid, prefix, counts);
+    __syncthreads();
+    return 0u;
 }
 
 // Shared-memory counter bump aggregated over the lanes of a warp that hit the
@@ -79,12 +91,13 @@ __global__ void __launch_bounds__(kOrderThreads)
 k_order_count(QueryParams qp, QuerySlot slot)
 {
     __shared__ unsigned h[kOrderBuckets];
+    __shared__ unsigned prefix[kMaxScanGrid + 1], counts[kMaxScanGrid];
     const QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
     for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) h[b] = 0u;
-    __syncthreads();
+    const unsigned nch = survivor_chunks<SRC>(slot, prefix, counts);
     const float thr = prune_threshold(st->thr, qp.F);
-    for_each_survivor<SRC>(slot, [&](bool valid, unsigned, float lb) {
+    for_each_survivor<SRC>(slot, nch, prefix, counts, [&](bool valid, unsigned, float lb) {
         const bool take = valid && lb <= thr;
         bump_bucket(h, take, take ? order_bucket(lb) : 0u);
     });
@@ -140,13 +153,14 @@ __global__ void __launch_bounds__(kOrderThreads)
 k_order_scatter(QueryParams qp, QuerySlot slot, unsigned *__restrict__ dst_pos, float *__restrict__ dst_lb)
 {
     __shared__ unsigned h[kOrderBuckets];
+    __shared__ unsigned prefix[kMaxScanGrid + 1], counts[kMaxScanGrid];
     const QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
     unsigned *cursor = slot.bucket + kOrderBuckets;
     for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) h[b] = 0u;
-    __syncthreads();
+    const unsigned nch = survivor_chunks<SRC>(slot, prefix, counts);
     const float thr = prune_threshold(st->thr, qp.F);
-    for_each_survivor<SRC>(slot, [&](bool valid, unsigned, float lb) {
+    for_each_survivor<SRC>(slot, nch, prefix, counts, [&](bool valid, unsigned, float lb) {
         const bool take = valid && lb <= thr;
         bump_bucket(h, take, take ? order_bucket(lb) : 0u);
     });
@@ -154,7 +168,7 @@ k_order_scatter(QueryParams qp, QuerySlot slot, unsigned *__restrict__ dst_pos, 
     for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
         if (h[b]) h[b] = atomicAdd(&cursor[b], h[b]);
     __syncthreads();
-    for_each_survivor<SRC>(slot, [&](bool valid, unsigned pos, float lb) {
+    for_each_survivor<SRC>(slot, nch, prefix, counts, [&](bool valid, unsigned pos, float lb) {
         const bool take = valid && lb <= thr;
         const unsigned o = bump_bucket(h, take, take ? order_bucket(lb) : 0u);
         if (take) {

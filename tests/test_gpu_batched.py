@@ -122,3 +122,17 @@ def test_set_tuning_rejects_bad_shapes(m, coll):
     for bad in ((0, 32, 2), (64, 0, 2), (64, 32, 3)):
         with pytest.raises(m.MessiError):
             m.messi_set_tuning(ix, *bad)
+
+
+@pytest.mark.parametrize("n", [72, 512])
+def test_batched_lengths_outside_the_screen(m, n):
+    # the tensor-core screen needs len % 16 == 0 and len <= 256; other lengths
+    # take the lower-bound form in either batch mode and stay exact
+    x = synth.random_walks(8_000, n, seed=60 + n)
+    ix = m.messi_build(torch.from_numpy(x).cuda(), 8, 256)
+    q = synth.query_mix(x, 20, seed=61 + n)
+    for mode in (m.MESSI_BATCH_TC_SCREEN, m.MESSI_BATCH_LB_REFINE):
+        m.messi_set_batch_mode(ix, mode)
+        ids, d = m.messi_query_batched(ix, torch.from_numpy(q).cuda(), k=4, batch=8)
+        m.messi_check(ix)
+        check(ids, d, *oracle.knn(x, q, 4))

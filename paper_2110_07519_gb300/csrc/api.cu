@@ -446,7 +446,7 @@ messi_status messi_index_get_info(const messi_index *ix, messi_index_info *out)
     out->leaf_capacity = ix->cap;
     out->n_leaves = ix->L;
     out->max_leaf_size = ix->max_leaf;
-    out->device_bytes = ix->device_bytes;
+    out->device_bytes = ix->device_bytes.load();
     out->build_ms = ix->build_ms;
     return MESSI_OK;
 }

@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <atomic>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -212,7 +213,7 @@ struct messi_index {
     // default workspace of messi_query / messi_query_batched
     messi::Workspace ws;
     // bookkeeping
-    size_t device_bytes = 0;
+    std::atomic<size_t> device_bytes{0};   // workspaces of server workers grow it concurrently
     double build_ms = 0.0;
     bool profiling = false;
     unsigned long long launches = 0;

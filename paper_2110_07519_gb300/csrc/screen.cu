@@ -182,7 +182,6 @@ __global__ void k_tc_next_pass(const QuerySlot *__restrict__ slots, unsigned B, 
 struct ScreenArgs {
     const __half *rtiles;     // [RT][128 x len] f16 rows
     const float *xn, *xnorm;  // [RT * 128]
-    const unsigned *ids_unused;
     const __half *qtiles;     // [QT][128 x len] f16 queries
     const float *qconst;      // [QT*128][4]
     unsigned *Ubits;          // [QT*128] float bits, atomically lowered (k = 1)
@@ -727,7 +726,6 @@ void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm,
     a.rtiles = rtiles;
     a.xn = xn;
     a.xnorm = xnorm;
-    a.ids_unused = nullptr;
     a.qtiles = qtiles;
     a.qconst = qconst;
     a.Ubits = Ubits;

@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--serve-streams", type=int, default=4, help="server worker streams")
     ap.add_argument("--batch-mode", default="tc", choices=["tc", "lb"],
                     help="batched kernels: tensor-core screen (tc) or fused lower bound + refine (lb)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="lower-bound batch form: time its shapes on the warm-up queries first")
     ap.add_argument("--mix", default="mixed", choices=["mixed", "fresh", "s0.1", "s0.5", "s1.0"],
                     help="query class (default: the paper-shaped mix)")
     return ap.parse_args()
@@ -244,15 +246,18 @@ def run_reference(args, ws, rank, local):
 
 
 # -------------------------------------------------------------- GPU arm
-def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists, dist=0, window=0):
-    """W warm-up and K timed steps of one query form; per-step stats."""
+def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists, dist=0, window=0, batch_arg=None):
+    """W warm-up and K timed steps of one query form (B queries a step); per-step stats.
+    batch_arg: queries per batched launch (None: B; 0: the index's tuned batch)."""
     import torch
+
+    launch_batch = B if batch_arg is None else batch_arg
 
     def step(qs):
         if form == "plain":
             m.messi_query(ix, qs, k=k, dist=dist, window=window, ids=ids, dists=dists)
         else:
-            m.messi_query_batched(ix, qs, k=k, dist=dist, window=window, batch=B, ids=ids, dists=dists)
+            m.messi_query_batched(ix, qs, k=k, dist=dist, window=window, batch=launch_batch, ids=ids, dists=dists)
 
     m.messi_set_profiling(ix, True)
     for s in range(W):
@@ -286,7 +291,7 @@ def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists, dist=
     if form == "plain":
         m.messi_query(ix, qpool[W * B:(W + K) * B], k=k, dist=dist, window=window)
     else:
-        m.messi_query_batched(ix, qpool[W * B:(W + K) * B], k=k, dist=dist, window=window, batch=B)
+        m.messi_query_batched(ix, qpool[W * B:(W + K) * B], k=k, dist=dist, window=window, batch=launch_batch)
     st_all = m.messi_query_stats(ix)
     m.messi_set_profiling(ix, False)
     agg.update(elapsed_ms=elapsed_ms, clocks=clk, p50=st_all["query_ms_p50"], p99=st_all["query_ms_p99"])
@@ -346,9 +351,13 @@ def run_messi(args, ws, rank, local):
     window = (args.window if args.window >= 0 else int(0.10 * args.len)) if dist_code else 0
     batch_mode = "tc_screen" if args.batch_mode == "tc" else "lb_refine"
     m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN if args.batch_mode == "tc" else m.MESSI_BATCH_LB_REFINE)
+    tuning = None
+    if args.autotune and args.batch_mode == "lb" and B >= 32:
+        tuning = m.messi_autotune(ix, qpool[:max(256, B)].contiguous(), k=args.k)
     forms = {}
     for form in (["plain", "batched"] if args.form == "both" else [args.form]):
-        r = time_form(m, ix, qpool, form, B, K, W, args.k, stream, pg, dev, ids, dists, dist_code, window)
+        r = time_form(m, ix, qpool, form, B, K, W, args.k, stream, pg, dev, ids, dists, dist_code, window,
+                      batch_arg=0 if tuning else None)
         nqt = B * K
         kern_avg_s = r["kern_ms"] * 1e-3 / max(r["kern_launches"], 1)
         n_leaves = m.messi_index_get_info(ix)["n_leaves"]
@@ -383,6 +392,7 @@ def run_messi(args, ws, rank, local):
             "counters": {"lb_survivors_per_query": r["survivors"] / nqt, "rows_read_per_query": r["rows"] / nqt,
                          "words_scanned_per_query": r["words"] / nqt},
             "query_roofline_frac": q_bytes / (r["elapsed_ms"] * 1e-3 / nqt) / 1e9 / peak,
+            **({"tuning": tuning} if tuning and form == "batched" else {}),
         }
     head_form = max(forms, key=lambda f: forms[f]["value"])
     head = forms[head_form]

@@ -124,15 +124,39 @@ def test_set_tuning_rejects_bad_shapes(m, coll):
             m.messi_set_tuning(ix, *bad)
 
 
-@pytest.mark.parametrize("n", [72, 512])
-def test_batched_lengths_outside_the_screen(m, n):
+@pytest.mark.parametrize("n,w", [(40, 10), (512, 8)])
+def test_batched_lengths_outside_the_screen(m, n, w):
     # the tensor-core screen needs len % 16 == 0 and len <= 256; other lengths
     # take the lower-bound form in either batch mode and stay exact
     x = synth.random_walks(8_000, n, seed=60 + n)
-    ix = m.messi_build(torch.from_numpy(x).cuda(), 8, 256)
+    ix = m.messi_build(torch.from_numpy(x).cuda(), w, 256)
     q = synth.query_mix(x, 20, seed=61 + n)
     for mode in (m.MESSI_BATCH_TC_SCREEN, m.MESSI_BATCH_LB_REFINE):
         m.messi_set_batch_mode(ix, mode)
         ids, d = m.messi_query_batched(ix, torch.from_numpy(q).cuda(), k=4, batch=8)
         m.messi_check(ix)
         check(ids, d, *oracle.knn(x, q, 4))
+
+
+@pytest.mark.parametrize("mode", ["lb", "tc"])
+def test_batched_non_finite_query_isolated(m, coll, mode):
+    # a query holding NaN / inf answers -1 / NaN and is reported; its batch
+    # neighbours are unaffected
+    x, ix, _ = coll
+    q = synth.query_mix(x, 12, seed=synth.QUERY_SEED + 500)
+    q[3, 40] = np.nan
+    q[7, 0] = np.inf
+    m.messi_set_batch_mode(ix, m.MESSI_BATCH_LB_REFINE if mode == "lb" else m.MESSI_BATCH_TC_SCREEN)
+    try:
+        ids, d = m.messi_query_batched(ix, torch.from_numpy(q).cuda(), k=3, batch=8)
+        with pytest.raises(m.MessiError) as e:
+            m.messi_check(ix)
+        assert e.value.status == 1
+    finally:
+        m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN)
+    ids, d = ids.cpu().numpy(), d.cpu().numpy()
+    bad = [3, 7]
+    good = [i for i in range(12) if i not in bad]
+    assert (ids[bad] == -1).all() and np.isnan(d[bad]).all()
+    check(ids[good], d[good], *oracle.knn(x, q[good], 3))
+    m.messi_check(ix)

@@ -111,6 +111,8 @@ messi_status messi_build(const float *series, uint64_t n, uint32_t len, uint32_t
 /* Release every device allocation of the index.  NULL is a no-op. */
 void messi_free(messi_index *ix);
 
+/* Sizes of a built index (collection shape, leaf count and largest leaf,
+ * device bytes held, build time).  Host-side only; out must not be NULL. */
 messi_status messi_index_get_info(const messi_index *ix, messi_index_info *out);
 
 /* ---------------------------------------------------------------- query --
@@ -185,6 +187,8 @@ messi_status messi_lower_bounds_noalloc(const messi_index *ix, const float *quer
 /* Counters of the last query call.  Synchronises the index's last stream. */
 messi_status messi_query_stats(const messi_index *ix, messi_stats *out);
 
+/* Kernels messi_query_batched uses for ED (see there); EINVAL for other modes.
+ * Not thread-safe against concurrent batched calls on the same index. */
 enum { MESSI_BATCH_LB_REFINE = 0, MESSI_BATCH_TC_SCREEN = 1 };
 messi_status messi_set_batch_mode(messi_index *ix, int mode);
 
@@ -294,6 +298,9 @@ messi_status messi_server_submit(messi_server *srv, const float *query, uint32_t
 messi_status messi_server_poll(messi_server *srv, uint64_t ticket, int64_t *ids, float *dists,
                                double *latency_ms, uint64_t wait_us);
 
+/* Counters of a server since creation: requests submitted / completed /
+ * rejected, batches run, the largest number in flight, and submit-to-result
+ * latency percentiles (ms) over completed requests. */
 messi_status messi_server_get_stats(messi_server *srv, messi_server_stats *out);
 
 /* Stop the workers after the queued requests and release everything. */

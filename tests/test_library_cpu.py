@@ -91,3 +91,19 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.messi_query(None, None, 1, 1, 0, 0, None, None, None) == 1
     assert lib.messi_query_stats(None, None) == 1
     lib.messi_free(None)
+
+
+def test_every_declared_entry_point_is_documented():
+    # each C-ABI declaration is preceded by a comment block stating what it
+    # does (the passage it implements, or that the paper has no counterpart)
+    text = open(HEADER).read()
+    decls = list(re.finditer(r"\n(?:messi_status|void|const char \*)\s+\*?(messi_\w+)\s*\(", text))
+    assert decls
+    undocumented = []
+    for d in decls:
+        before = text[: d.start()].rstrip()
+        # an enum line may sit between the comment and the declaration
+        before = re.sub(r"\n\s*enum\s*\{[^}]*\};\s*$", "", before).rstrip()
+        if not before.endswith("*/"):
+            undocumented.append(d.group(1))
+    assert not undocumented, undocumented

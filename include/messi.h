@@ -120,9 +120,12 @@ messi_status messi_index_get_info(const messi_index *ix, messi_index_info *out);
  * of the k best, Sec. 5.4), one query after another as in the paper's
  * protocol (Sec. 5.1).  Per query: summarise the query (its PAA, or the PAA
  * of its LB_Keogh envelope for DTW), seed the best-so-far from the query's
- * own leaf (approxSearch, Sec. 3.1), stream every iSAX word through the
- * lower bound, compact the survivors, refine them with ED (Algorithm 9) or
- * LB_Keogh-filtered DTW (Algorithm 10), and resolve near-ties in FP64.
+ * own leaf (approxSearch, Sec. 3.1), prune whole leaves by the symbol box of
+ * their words (the subtree pruning of Sec. 3), stream the iSAX words of the
+ * remaining leaves through the lower bound, compact the survivors, refine
+ * them in increasing bound order (the priority-queue order of Sec. 3) with ED
+ * (Algorithm 9) or LB_Keogh / LB_Improved-filtered DTW (Algorithm 10), and
+ * resolve near-ties in FP64.
  *
  * queries     device or host, nq*len float32.
  * window      DTW Sakoe-Chiba reach r in points (ignored for ED); r < len.

@@ -296,8 +296,14 @@ struct CandidateSink {
     int k;
 };
 
+// k <= kTcTopK: the thread keeps the k smallest upper ends it has seen for
+// its query (topk, ascending; each from a different row, since a pass meets
+// every (query, row) pair once), and the k-th of them bounds the query's k-th
+// squared distance from above just as the single best does for k = 1.
+constexpr int kTcTopK = 16;
+
 __device__ __noinline__ float screen_candidate(CandidateSink a, unsigned qj, unsigned long long row, float acc,
-                                               float qn, float alpha, float gamma, float E, float U)
+                                               float qn, float alpha, float gamma, float E, float U, float *topk)
 {
     if (row >= a.N) return U;
     const float one_m_kappa = 1.f - kKappaP;
@@ -306,14 +312,25 @@ __device__ __noinline__ float screen_candidate(CandidateSink a, unsigned qj, uns
     if (!(lhs >= E)) return U;
     const unsigned o = atomicAdd(&a.cand_count[qj], 1u);
     if (o < a.cap) a.cand_pos[(unsigned long long)qj * a.cap + o] = (unsigned)row;
-    if (a.k == 1) {
+    if (a.k <= kTcTopK) {
         // upper end of the estimate: s + eps, rounded up
         const float shat = fmaf(-2.f, acc, xn + qn);
         const float eps = fmaf(xnrm, alpha, gamma + kKappaP * xn);
         const float up = fmaxf(__fmul_ru(__fadd_ru(shat, eps), 1.0000003f), 0.f);
-        if (up < U) {
-            atomicMin(&a.Ubits[qj], __float_as_uint(up));
-            return up;
+        float bound = up;
+        if (a.k > 1) {
+            if (!(up < topk[a.k - 1])) return U;
+            int j = a.k - 1;
+            while (j > 0 && topk[j - 1] > up) {
+                topk[j] = topk[j - 1];
+                --j;
+            }
+            topk[j] = up;
+            bound = topk[a.k - 1];
+        }
+        if (bound < U) {
+            atomicMin(&a.Ubits[qj], __float_as_uint(bound));
+            return bound;
         }
     }
     return U;
@@ -500,6 +517,9 @@ k_tc_screen(ScreenArgs a)
         epi_bar_sync();
         const float amax = __uint_as_float(s_amax);
         const CandidateSink sink{a.xn, a.xnorm, a.cand_count, a.cand_pos, a.Ubits, a.N, a.cap, a.k};
+        float topk[kTcTopK];                      // this thread's k smallest upper ends (k <= 16)
+#pragma unroll
+        for (int i = 0; i < kTcTopK; ++i) topk[i] = __int_as_float(0x7f800000);
         // columns of this warp in an accumulator buffer: QPC = 2: all 128 series of
         // its query tile; QPC = 1: half of them
         const unsigned cbeg = (QPC == 2) ? qi * 128 : (unsigned)(warp >> 2) * 64;
@@ -544,7 +564,8 @@ k_tc_screen(ScreenArgs a)
 #pragma unroll
                     for (int i = 0; i < 64; ++i) {
                         if (__fmaf_ru(2.f, acc[i], rowr[ab][rbeg + h + i]) >= E) {
-                            U = screen_candidate(sink, qj, rt * kTcRows + rbeg + h + i, acc[i], qn, alpha, gamma, E, U);
+                            U = screen_candidate(sink, qj, rt * kTcRows + rbeg + h + i, acc[i], qn, alpha, gamma, E, U,
+                                                 topk);
                             E = __fsub_rd(__fsub_rd(qn, gamma), U);
                         }
                     }

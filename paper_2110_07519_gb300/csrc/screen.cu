@@ -198,16 +198,22 @@ struct ScreenArgs {
     unsigned *status;
 };
 
-// Operand roles: A = a query tile (M = 128 queries, TMEM lane = query), B = a
-// tile of 128 series (N = 128, TMEM column = series).  Warp-specialised:
+// Operand roles: A = a tile of 128 series (M = 128, TMEM lane = series), B =
+// the CTA's QPC query tiles side by side (N = QPC * 128, TMEM column =
+// query).  The query tiles are resident next to each other in the same
+// core-matrix layout, so together they are one operand of QPC * 128 rows and
+// one MMA per 16-wide k step covers every query of the CTA: for QPC = 2 it
+// reads 12 KB of operands from shared memory where two MMAs of N = 128 read
+// 16 KB, and the issuing thread issues half as many instructions.
+// Warp-specialised:
 //   warps 8, 10        (producers) stream the series tiles as K-chunks through
 //                      an NS-deep ring of shared-memory stages with TMA bulk
 //                      copies, taking alternate chunks: one thread's bulk
 //                      copies complete one after another, two threads keep
 //                      twice as many in flight;
-//   warp 9 (MMA)       issues tcgen05 MMAs chunk by chunk (one MMA per query
-//                      tile and 16-wide k step), commits each chunk to free its
-//                      stage and each finished tile to its accumulator buffer;
+//   warp 9 (MMA)       issues tcgen05 MMAs chunk by chunk (one MMA per
+//                      16-wide k step), commits each chunk to free its stage
+//                      and each finished tile to its accumulator buffer;
 //   warp 11 (relay)    waits on the mbarriers the MMA warp depends on (chunk
 //                      loaded, accumulator buffer drained) and meets the MMA
 //                      warp at a named barrier once per two chunks (once per
@@ -217,21 +223,24 @@ struct ScreenArgs {
 //                      a named barrier does not;
 //   warps 0-7          read accumulators from TMEM (double-buffered) and test
 //                      every (query, series) pair.
-// A CTA owns QPC (1 or 2) query tiles, so each series tile read from L2 serves
-// QPC * 128 queries.  An epilogue thread owns one query, whose constants stay
-// in registers.  The candidate test, rearranged so that only per-series
-// constants meet the accumulator,
-//     lower <= U  <=>  xnorm * alpha + (2 c - xn (1 - kappa'))  >=  qn - gamma' - U,
-// is first applied with alpha replaced by the largest alpha of the CTA's
-// queries (xnorm >= 0, so the left side only grows): one per-series constant
+// An epilogue thread owns one series of the tile (its TMEM lane; warp w reads
+// lanes 32 (w mod 4) ...) and half of the CTA's queries (warps 0-3 the first
+// half of the columns, warps 4-7 the second).  The candidate test, rearranged
+// so that one per-series and one per-query constant meet the accumulator,
+//     lower <= U_q  <=>  xnorm * alpha_q + (2 c - xn (1 - kappa'))  >=  qn - gamma' - U_q  =: E_q,
+// is first applied with alpha_q replaced by the largest alpha of the CTA's
+// queries (xnorm >= 0, so the left side only grows): the per-series
 //     r = xnorm * alpha_max - xn (1 - kappa')   (rounded up)
-// read four at a time as a shared-memory broadcast, then one FMA (rounded up)
-// and a compare per pair.  A warp vote skips the rare path, which re-tests
-// the pair with its own query's alpha before taking it as a candidate.  The
-// extra 8u in kappa' and gamma' covers the rounding of the exact form.  The
-// tensor core reads both operands from shared memory at close to the full
-// shared-memory bandwidth, so the epilogue keeps its own shared-memory
-// traffic to one broadcast per four pairs.
+// stays in a register, E_q is read four queries at a time from shared memory
+// (every lane of a warp tests the same queries: a broadcast), and each pair
+// costs one FMA (rounded up) and a compare.  A warp vote skips the rare path,
+// which re-tests the pair with its query's own alpha before taking it as a
+// candidate.  The extra 8u in kappa' and gamma' covers the rounding of the
+// exact form.
+// The bounds are per query and shared by the CTA: U_q (float bits, only
+// lowered, by atomicMin) and E_q derived from it.  Two racing stores of E_q
+// may leave the looser one in place; every stored E_q still derives from a
+// valid U_q, so the test stays conservative.
 constexpr int kTcEpiWarps = 8;
 constexpr int kTcCtrlThreads = kTcEpiWarps * 32 + 128;    // + 2 producer warps + MMA warp + relay warp
 constexpr int kTcProdWarp0 = kTcEpiWarps, kTcMmaWarp = kTcEpiWarps + 1, kTcProdWarp1 = kTcEpiWarps + 2,
@@ -284,70 +293,98 @@ __device__ __forceinline__ bool epi_bar_any(bool v)
     return r != 0;
 }
 
-// Rare path of the epilogue: the pair (query qj, series row) passed the test
+// k <= kTcTopK: each query of a CTA keeps the k smallest upper ends met in
+// that CTA (ascending; each from a different row, since a CTA meets every
+// (query, row) pair at most once), and the k-th of them bounds the query's
+// k-th squared distance from above just as the single best does for k = 1.
+// The list lives in shared memory and is updated under a per-query lock
+// taken with a bounded spin; a lane that does not get the lock skips its
+// update, which only leaves the bound looser.
+constexpr int kTcTopK = 16;
+
+__device__ __forceinline__ bool topk_lock(int *l)
+{
+    for (int it = 0; it < 4096; ++it) {
+        if (atomicCAS(l, 0, 1) == 0) {
+            __threadfence_block();
+            return true;
+        }
+        __nanosleep(32);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void topk_unlock(int *l)
+{
+    __threadfence_block();
+    atomicExch(l, 0);
+}
+
+// Rare path of the epilogue: the pair (query, series row) passed the test
 // with the CTA's largest alpha; re-test it with the query's own alpha, record
-// it as a candidate, and for k = 1 lower the query's bound U with the upper
-// end of its estimate.  Returns the (possibly lowered) U.
+// it as a candidate, and for k <= kTcTopK lower the query's bound U with the
+// upper end of its estimate.
 struct CandidateSink {
-    const float *xn, *xnorm;
+    const float *qconst;
     unsigned *cand_count, *cand_pos, *Ubits;
+    float *sE;           // shared: E_q per query of the CTA
+    unsigned *sU;        // shared: U_q bits
+    int *lock;           // shared: top-k list locks
+    float *topk;         // shared: [QPC * 128][k] top-k lists (1 < k <= kTcTopK)
     unsigned long long N;
     unsigned cap;
     int k;
 };
 
-// k <= kTcTopK: the thread keeps the k smallest upper ends it has seen for
-// its query (topk, ascending; each from a different row, since a pass meets
-// every (query, row) pair once), and the k-th of them bounds the query's k-th
-// squared distance from above just as the single best does for k = 1.
-constexpr int kTcTopK = 16;
-
-__device__ __noinline__ float screen_candidate(CandidateSink a, unsigned qj, unsigned long long row, float acc,
-                                               float qn, float alpha, float gamma, float E, float U, float *topk)
+__device__ __noinline__ void screen_candidate(CandidateSink a, unsigned ql, unsigned qj, unsigned long long row,
+                                              float acc, float xn, float xnrm)
 {
-    if (row >= a.N) return U;
+    if (row >= a.N) return;
+    const float qn = a.qconst[4 * qj + 0], alpha = a.qconst[4 * qj + 1], gamma = a.qconst[4 * qj + 2];
     const float one_m_kappa = 1.f - kKappaP;
-    const float xn = a.xn[row], xnrm = a.xnorm[row];
     const float lhs = fmaf(xnrm, alpha, fmaf(2.f, acc, -xn * one_m_kappa));
-    if (!(lhs >= E)) return U;
+    if (!(lhs >= *(volatile float *)&a.sE[ql])) return;
     const unsigned o = atomicAdd(&a.cand_count[qj], 1u);
     if (o < a.cap) a.cand_pos[(unsigned long long)qj * a.cap + o] = (unsigned)row;
-    if (a.k <= kTcTopK) {
-        // upper end of the estimate: s + eps, rounded up
-        const float shat = fmaf(-2.f, acc, xn + qn);
-        const float eps = fmaf(xnrm, alpha, gamma + kKappaP * xn);
-        const float up = fmaxf(__fmul_ru(__fadd_ru(shat, eps), 1.0000003f), 0.f);
-        float bound = up;
-        if (a.k > 1) {
-            if (!(up < topk[a.k - 1])) return U;
-            int j = a.k - 1;
-            while (j > 0 && topk[j - 1] > up) {
-                topk[j] = topk[j - 1];
+    if (a.k > kTcTopK) return;
+    // upper end of the estimate: s + eps, rounded up
+    const float shat = fmaf(-2.f, acc, xn + qn);
+    const float eps = fmaf(xnrm, alpha, gamma + kKappaP * xn);
+    const float up = fmaxf(__fmul_ru(__fadd_ru(shat, eps), 1.0000003f), 0.f);
+    float bound = up;
+    if (a.k > 1) {
+        volatile float *t = a.topk + (size_t)ql * a.k;
+        if (!(up < t[a.k - 1])) return;
+        if (!topk_lock(&a.lock[ql])) return;
+        int j = a.k - 1;
+        if (up < t[j]) {
+            while (j > 0 && t[j - 1] > up) {
+                t[j] = t[j - 1];
                 --j;
             }
-            topk[j] = up;
-            bound = topk[a.k - 1];
+            t[j] = up;
         }
-        if (bound < U) {
-            atomicMin(&a.Ubits[qj], __float_as_uint(bound));
-            return bound;
-        }
+        bound = t[a.k - 1];
+        topk_unlock(&a.lock[ql]);
     }
-    return U;
+    // bounds are >= 0 (or +inf): their bits order like the values
+    const unsigned bb = __float_as_uint(bound);
+    const unsigned old = atomicMin(&a.sU[ql], bb);
+    if (bb < old) {
+        atomicMin(&a.Ubits[qj], bb);
+        a.sE[ql] = __fsub_rd(__fsub_rd(qn, gamma), bound);
+    }
 }
 
-// One chunk of KS 16-wide k-steps for NQ query tiles sharing the series
-// operand; k-step kk starts kk * 256 bytes further in both operands.
-template <int KS, int NQ>
-__device__ __forceinline__ void mma_chunk(unsigned d, unsigned long long ad, unsigned long long bd, unsigned qstride16,
-                                          unsigned idesc, bool accumulate)
+// One chunk of KS 16-wide k-steps: series operand `rd` (ring stage) against
+// the query operand `qd`; k-step kk starts kk * 256 bytes further in both.
+template <int KS>
+__device__ __forceinline__ void mma_chunk(unsigned d, unsigned long long rd, unsigned long long qd, unsigned idesc,
+                                          bool accumulate)
 {
 #pragma unroll
     for (int kk = 0; kk < KS; ++kk)
-#pragma unroll
-        for (int qi = 0; qi < NQ; ++qi)
-            tc_mma_f16(d + qi * 128, ad + qi * qstride16 + kk * 16u, bd + kk * 16u, idesc,
-                       (kk > 0 || accumulate) ? 1u : 0u);
+        tc_mma_f16(d, rd + kk * 16u, qd + kk * 16u, idesc, (kk > 0 || accumulate) ? 1u : 0u);
 }
 
 // KS = chunk width / 16 (1, 2 or 4)
@@ -359,8 +396,10 @@ k_tc_screen(ScreenArgs a)
     __shared__ __align__(8) unsigned long long bar_full[kTcMaxStages], bar_empty[kTcMaxStages];
     __shared__ __align__(8) unsigned long long bar_accf[2], bar_acce[2], bar_q;
     __shared__ unsigned tmem_base;
-    __shared__ __align__(16) float rowr[2][kTcRows];   // xnorm alpha_max - xn (1 - kappa') per buffer
-    __shared__ unsigned s_amax;                       // bits of the CTA's largest alpha
+    __shared__ __align__(16) float sE[2 * kTcQ];     // E_q per query of the CTA (+inf: not tested)
+    __shared__ unsigned sU[2 * kTcQ];                // U_q bits
+    __shared__ int sLock[2 * kTcQ];                  // top-k list locks
+    __shared__ unsigned s_amax;                      // bits of the CTA's largest alpha
     __shared__ volatile int s_fail;
     const unsigned len = a.len;
     constexpr unsigned ck = KS * 16;
@@ -370,6 +409,7 @@ k_tc_screen(ScreenArgs a)
     const unsigned QPC = a.qpc, NS = a.stages;
     unsigned char *qbuf = smem;                               // QPC query tiles
     unsigned char *ring = smem + QPC * qtile_bytes;           // NS chunk stages
+    float *topk = reinterpret_cast<float *>(ring + NS * chunk_bytes);   // [QPC * 128][k] when 1 < k <= kTcTopK
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned QG = (a.QT + QPC - 1) / QPC;               // query-tile groups
     const unsigned groups = gridDim.x / QG;                   // CTAs per query-tile group
@@ -447,15 +487,17 @@ k_tc_screen(ScreenArgs a)
         // wait at the named barrier for one that has left: both run every
         // iteration, and after a failure lane 0 only stops issuing).
         if (nt > 0) {
-            const unsigned idesc = tc_idesc_f16(kTcQ, kTcRows);
+            const unsigned idesc = tc_idesc_f16(kTcRows, nq * kTcQ);
             const unsigned sq = smem_u32(qbuf), sr = smem_u32(ring);
             const unsigned sbo_q = (len / 8) * 128, sbo_r = (ck / 8) * 128;
-            // descriptors of k-step 0 of query tile 0 and of ring stage 0; the
-            // others differ only in the start-address field (address >> 4,
-            // bits 0-13), reached by plain adds since every shared-memory
-            // address here is below 256 KB
-            const unsigned long long ad0 = tc_desc(sq, 128, sbo_q), bd0 = tc_desc(sr, 128, sbo_r);
-            const unsigned qstride16 = qtile_bytes >> 4, cstride16 = chunk_bytes >> 4;
+            // descriptors of k-step 0 of ring stage 0 and of the query
+            // operand; the others differ only in the start-address field
+            // (address >> 4, bits 0-13), reached by plain adds since every
+            // shared-memory address here is below 256 KB.  Query tile 1
+            // starts 16 row groups (16 * sbo_q bytes) after tile 0, so one
+            // descriptor spans both.
+            const unsigned long long rd0 = tc_desc(sr, 128, sbo_r), qd0 = tc_desc(sq, 128, sbo_q);
+            const unsigned cstride16 = chunk_bytes >> 4;
             unsigned st = 0;
             const unsigned G = (nch % 2 == 0) ? 2u : 1u;    // chunks per meeting with the relay
             for (unsigned long long j = 0; j < nt; ++j) {
@@ -464,9 +506,7 @@ k_tc_screen(ScreenArgs a)
                     if (c % G == 0) relay_bar_sync();
                     tc_fence_after();
                     if (lane == 0 && !s_fail) {
-                        const unsigned long long ad = ad0 + c * (KS * 16u), bd = bd0 + st * cstride16;
-                        if (nq == 2) mma_chunk<KS, 2>(tmem + ab * acc_cols, ad, bd, qstride16, idesc, c != 0);
-                        else mma_chunk<KS, 1>(tmem + ab * acc_cols, ad, bd, qstride16, idesc, c != 0);
+                        mma_chunk<KS>(tmem + ab * acc_cols, rd0 + st * cstride16, qd0 + c * (KS * 16u), idesc, c != 0);
                         tc_commit(&bar_empty[st]);
                     }
                     __syncwarp();
@@ -501,72 +541,76 @@ k_tc_screen(ScreenArgs a)
         }
     } else {
         // ------------------------------------------------ epilogue
-        const unsigned qi = (QPC == 2) ? (unsigned)(warp >> 2) : 0u;
-        const unsigned qloc = (unsigned)((warp & 3) * 32 + lane);
-        const unsigned qj = (qt0 + qi) * kTcQ + qloc;
-        const bool have = qt0 + qi < a.QT;
-        const float qn = have ? a.qconst[4 * qj + 0] : 0.f;
-        const float alpha = have ? a.qconst[4 * qj + 1] : 0.f;
-        const float gamma = have ? a.qconst[4 * qj + 2] : 0.f;
-        const bool act = have && a.active[qj] != 0;
-        float U = have ? __uint_as_float(a.Ubits[qj]) : -1.f;
-        float E = act ? __fsub_rd(__fsub_rd(qn, gamma), U) : __int_as_float(0x7f800000);
-        const float one_m_kappa = 1.f - kKappaP;
-        // alpha >= 0: its bits order like the values
-        if (act) atomicMax(&s_amax, __float_as_uint(alpha));
+        const unsigned lg = (unsigned)(warp & 3);             // TMEM lane group of this warp
+        const unsigned srow = lg * 32 + lane;                 // this thread's series within a tile
+        const unsigned ncol = acc_cols / 2;                   // queries (columns) of this warp: 128 or 64
+        const unsigned cbeg = (unsigned)(warp >> 2) * ncol;
+        const bool cols_live = cbeg < nq * kTcQ;              // one query tile in a QPC = 2 CTA: half idle
+        const bool use_topk = a.k > 1 && a.k <= kTcTopK;
+        // thread t sets up (and later refreshes) the bounds of query t of the CTA
+        const unsigned own_qj = qt0 * kTcQ + tid;
+        const bool own_have = (unsigned)tid < nq * kTcQ;
+        const float own_qn = own_have ? a.qconst[4 * own_qj + 0] : 0.f;
+        const float own_gamma = own_have ? a.qconst[4 * own_qj + 2] : 0.f;
+        const bool own_act = own_have && a.active[own_qj] != 0;
+        if ((unsigned)tid < acc_cols) {
+            const float U = own_have ? __uint_as_float(a.Ubits[own_qj]) : -1.f;
+            sU[tid] = __float_as_uint(U);
+            sE[tid] = own_act ? __fsub_rd(__fsub_rd(own_qn, own_gamma), U) : __int_as_float(0x7f800000);
+            sLock[tid] = 0;
+            // alpha >= 0: its bits order like the values
+            if (own_act) atomicMax(&s_amax, __float_as_uint(a.qconst[4 * own_qj + 1]));
+        }
+        if (use_topk)
+            for (unsigned i = tid; i < acc_cols * (unsigned)a.k; i += kTcEpiWarps * 32)
+                topk[i] = __int_as_float(0x7f800000);
         epi_bar_sync();
         const float amax = __uint_as_float(s_amax);
-        const CandidateSink sink{a.xn, a.xnorm, a.cand_count, a.cand_pos, a.Ubits, a.N, a.cap, a.k};
-        float topk[kTcTopK];                      // this thread's k smallest upper ends (k <= 16)
-#pragma unroll
-        for (int i = 0; i < kTcTopK; ++i) topk[i] = __int_as_float(0x7f800000);
-        // columns of this warp in an accumulator buffer: QPC = 2: all 128 series of
-        // its query tile; QPC = 1: half of them
-        const unsigned cbeg = (QPC == 2) ? qi * 128 : (unsigned)(warp >> 2) * 64;
-        const unsigned ncol = (QPC == 2) ? 128u : 64u;
-        const unsigned rbeg = (QPC == 2) ? 0u : (unsigned)(warp >> 2) * 64;   // first series of the tile
+        const float one_m_kappa = 1.f - kKappaP;
+        const CandidateSink sink{a.qconst, a.cand_count, a.cand_pos, a.Ubits, sE, sU, sLock, topk, a.N, a.cap, a.k};
         // series norms of the next tile are fetched one tile ahead
         float nxt_xn = 0.f, nxt_nrm = 0.f;
         auto fetch_norms = [&](unsigned long long j) {
-            const unsigned long long row = (g + j * groups) * kTcRows + tid;
-            const bool rv = tid < kTcRows && j < nt && row < a.N;
+            const unsigned long long row = (g + j * groups) * kTcRows + srow;
+            const bool rv = j < nt && row < a.N;
             nxt_xn = rv ? a.xn[row] : 0.f;
             nxt_nrm = rv ? a.xnorm[row] : 0.f;
         };
         fetch_norms(0);
         for (unsigned long long j = 0; j < nt; ++j) {
             const unsigned ab = (unsigned)(j & 1);
-            const unsigned long long rt = g + j * groups;
-            if (tid < kTcRows) rowr[ab][tid] = __fmaf_ru(nxt_nrm, amax, __fmul_ru(-nxt_xn, one_m_kappa));
+            const unsigned long long row = (g + j * groups) * kTcRows + srow;
+            const float xn = nxt_xn, xnrm = nxt_nrm;
+            // a padding row never passes: r = -inf
+            const float r = row < a.N ? __fmaf_ru(xnrm, amax, __fmul_ru(-xn, one_m_kappa)) : __int_as_float(0xff800000);
             fetch_norms(j + 1);
             const bool okw = mbar_wait_bounded(&bar_accf[ab], (unsigned)((j >> 1) & 1));
-            // also the barrier that publishes rowr to all epilogue warps
             if (epi_bar_any(!okw)) {
                 s_fail = 1;
                 break;
             }
             tc_fence_after();
-            for (unsigned h = 0; h < ncol; h += 64) {
-                float acc[64];
-                tmem_ld64(tmem + ((unsigned)((warp & 3) * 32) << 16) + ab * acc_cols + cbeg + h, acc);
-                const float4 *r4 = reinterpret_cast<const float4 *>(&rowr[ab][rbeg + h]);
-                bool hit = false;
+            if (cols_live) {
+                for (unsigned h = 0; h < ncol; h += 64) {
+                    float acc[64];
+                    tmem_ld64(tmem + ((lg * 32) << 16) + ab * acc_cols + cbeg + h, acc);
+                    const float4 *e4 = reinterpret_cast<const float4 *>(&sE[cbeg + h]);
+                    bool hit = false;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float4 r = r4[i];
-                    hit |= __fmaf_ru(2.f, acc[4 * i + 0], r.x) >= E;
-                    hit |= __fmaf_ru(2.f, acc[4 * i + 1], r.y) >= E;
-                    hit |= __fmaf_ru(2.f, acc[4 * i + 2], r.z) >= E;
-                    hit |= __fmaf_ru(2.f, acc[4 * i + 3], r.w) >= E;
-                }
-                if (__any_sync(0xffffffffu, hit)) {
-                    // unrolled so the accumulators stay in registers
+                    for (int i = 0; i < 16; ++i) {
+                        const float4 e = e4[i];
+                        hit |= __fmaf_ru(2.f, acc[4 * i + 0], r) >= e.x;
+                        hit |= __fmaf_ru(2.f, acc[4 * i + 1], r) >= e.y;
+                        hit |= __fmaf_ru(2.f, acc[4 * i + 2], r) >= e.z;
+                        hit |= __fmaf_ru(2.f, acc[4 * i + 3], r) >= e.w;
+                    }
+                    if (__any_sync(0xffffffffu, hit)) {
+                        // unrolled so the accumulators stay in registers
 #pragma unroll
-                    for (int i = 0; i < 64; ++i) {
-                        if (__fmaf_ru(2.f, acc[i], rowr[ab][rbeg + h + i]) >= E) {
-                            U = screen_candidate(sink, qj, rt * kTcRows + rbeg + h + i, acc[i], qn, alpha, gamma, E, U,
-                                                 topk);
-                            E = __fsub_rd(__fsub_rd(qn, gamma), U);
+                        for (int i = 0; i < 64; ++i) {
+                            const unsigned ql = cbeg + h + i;
+                            if (__fmaf_ru(2.f, acc[i], r) >= sE[ql])
+                                screen_candidate(sink, ql, qt0 * kTcQ + ql, row, acc[i], xn, xnrm);
                         }
                     }
                 }
@@ -575,12 +619,11 @@ k_tc_screen(ScreenArgs a)
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_acce[ab]);
             // pick up bounds lowered by the other CTAs of these query tiles
-            if (act && (j & 63) == 63) {
-                const float G = __uint_as_float(ld_volatile_u32(&a.Ubits[qj]));
-                if (G < U) {
-                    U = G;
-                    E = __fsub_rd(__fsub_rd(qn, gamma), U);
-                }
+            // (and repair an E_q that a race left looser than its U_q)
+            if (own_act && (j & 63) == 63) {
+                const unsigned G = ld_volatile_u32(&a.Ubits[own_qj]);
+                const unsigned old = atomicMin(&sU[tid], G);
+                sE[tid] = __fsub_rd(__fsub_rd(own_qn, own_gamma), __uint_as_float(min(old, G)));
             }
         }
     }
@@ -683,9 +726,6 @@ k_tc_gemm_test(const __half *A, const __half *Bm, float *D, unsigned K, unsigned
 
 }  // namespace
 
-// At least 120 KB so that a single screen CTA fits on an SM: each CTA holds
-// 256 TMEM columns for its whole (persistent) life, and a second or third
-// resident CTA would wait in tcgen05.alloc for columns that never free up.
 // Shared memory is always the full budget (kTcSmemBudget): one screen CTA per
 // SM, because each CTA holds all 512 TMEM columns for its whole (persistent)
 // life and a second resident CTA would wait in tcgen05.alloc forever.
@@ -695,11 +735,17 @@ size_t screen_smem_bytes(int len)
     return kTcSmemBudget;
 }
 
-// ring stages that fit next to `qpc` resident query tiles
-unsigned screen_stages(int len, unsigned qpc)
+// bytes of the per-query top-k lists of a CTA with `qpc` query tiles
+static size_t screen_topk_bytes(unsigned qpc, int k)
+{
+    return (k > 1 && k <= kTcTopK) ? (size_t)qpc * kTcQ * k * sizeof(float) : 0;
+}
+
+// ring stages that fit next to `qpc` resident query tiles and their top-k lists
+unsigned screen_stages(int len, unsigned qpc, int k)
 {
     const size_t chunk = (size_t)kTcRows * chunk_k((unsigned)len) * 2;
-    const size_t q = (size_t)qpc * kTcQ * len * 2;
+    const size_t q = (size_t)qpc * kTcQ * len * 2 + screen_topk_bytes(qpc, k);
     const size_t left = kTcSmemBudget > q ? kTcSmemBudget - q : 0;
     return (unsigned)std::min<size_t>(kTcMaxStages, left / chunk);
 }
@@ -755,8 +801,8 @@ void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm,
     a.QT = (B + kTcQ - 1) / kTcQ;
     a.k = k;
     a.status = status;
-    a.qpc = (a.QT >= 2 && screen_stages(len, 2) >= 4) ? 2u : 1u;
-    a.stages = screen_stages(len, a.qpc);
+    a.qpc = (a.QT >= 2 && screen_stages(len, 2, k) >= 4) ? 2u : 1u;
+    a.stages = screen_stages(len, a.qpc, k);
     const unsigned QG = (a.QT + a.qpc - 1) / a.qpc;
     const unsigned groups = std::max(1u, (unsigned)num_sms() / QG);
     const unsigned ks = chunk_k((unsigned)len) / 16;

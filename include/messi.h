@@ -79,7 +79,9 @@ typedef struct {
     double query_ms_p50;      /* per-query device latency (profiling mode)    */
     double query_ms_p99;
     uint64_t leaves_live;     /* leaves whose symbol box did not prune them   */
-    uint64_t reserved[5];
+    uint64_t screened_queries; /* batched screen: queries over all its passes
+                                  (a query screened again counts again)      */
+    uint64_t reserved[4];
 } messi_stats;
 
 typedef struct {

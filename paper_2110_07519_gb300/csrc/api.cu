@@ -227,9 +227,9 @@ messi_status ensure_screen_copy(messi_index *ix, cudaStream_t s)
 namespace {
 
 struct TcWs {
-    __half *qtiles;
+    __half *qtiles, *qtiles2;       // the batch's query tiles; those screened again, gathered
     float *qconst;
-    unsigned *Ubits, *cand_count, *flags, *active, *cand_pos, *n_active;
+    unsigned *Ubits, *cand_count, *flags, *active, *cand_pos, *n_active, *qmap;
 };
 
 TcWs tc_ws_view(messi_index *ix, Workspace *ws)
@@ -244,6 +244,8 @@ TcWs tc_ws_view(messi_index *ix, Workspace *ws)
     w.flags = reinterpret_cast<unsigned *>(p); p += align256((size_t)P * 4);
     w.active = reinterpret_cast<unsigned *>(p); p += align256((size_t)P * 4);
     w.n_active = reinterpret_cast<unsigned *>(p); p += 256;
+    w.qtiles2 = reinterpret_cast<__half *>(p); p += align256((size_t)P * ix->len * 2);
+    w.qmap = reinterpret_cast<unsigned *>(p); p += align256((size_t)P * 4);
     w.cand_pos = reinterpret_cast<unsigned *>(p);
     return w;
 }
@@ -257,7 +259,8 @@ messi_status ensure_tc_workspace(messi_index *ix, Workspace *ws, unsigned B)
         ws->tcws_block = nullptr;
     }
     const size_t P = (B + 127) / 128 * 128;
-    const size_t bytes = align256(P * ix->len * 2) + align256(P * 16) + 4 * align256(P * 4) + 256 + P * kTcCap * 4;
+    const size_t bytes = 2 * align256(P * ix->len * 2) + align256(P * 16) + 5 * align256(P * 4) + 256 +
+                         P * kTcCap * 4;
     if (cudaMalloc(&ws->tcws_block, bytes) != cudaSuccess) {
         cudaGetLastError();
         ws->tcws_block = nullptr;
@@ -797,6 +800,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
     ws->scan_ev.clear();
     ws->query_ev.clear();
     size_t evn = 0;
+    unsigned long long screened = 0;
     bool use_tc = ix->batch_mode == 1;
     if (use_tc && (chk = ensure_screen_copy(ix, s)) != MESSI_OK) return chk;
     use_tc = use_tc && ix->screen_state == 1;
@@ -814,24 +818,36 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
         launch_tc_qprep(ws->bslots_dev, nb, ix->len, qp, w.qtiles, w.qconst, w.Ubits, w.cand_count, w.flags,
                         w.active, s);
         ++ws->launches;
-        unsigned more = 1;
+        // pass 0 screens the batch; later passes only the queries whose
+        // candidate lists overflowed, gathered into the first query tiles
+        unsigned more = 1, count = nb;
+        const __half *qt = w.qtiles;
+        const unsigned *qm = nullptr;
+        const size_t qtiles_bytes = (size_t)(ws->tcws_B + 127) / 128 * 128 * ix->len * 2;
         for (int pass = 0; pass < 3 && more; ++pass) {
             if (ix->profiling) {
                 es0 = (int)evn;
                 cudaEventRecord(pool_event(ws, evn++), s);
             }
-            launch_tc_screen(ix->screen16, ix->xn, ix->xnorm, w.qtiles, w.qconst, w.Ubits, w.cand_count, w.cand_pos,
-                             w.active, kTcCap, ix->N, ix->len, nb, (int)k, ix->status, s);
+            launch_tc_screen(ix->screen16, ix->xn, ix->xnorm, qt, w.qconst, w.Ubits, w.cand_count, w.cand_pos,
+                             w.active, qm, kTcCap, ix->N, ix->len, count, (int)k, ix->status, s);
+            screened += count;
             if (ix->profiling) {
                 cudaEventRecord(pool_event(ws, evn++), s);
                 ws->scan_ev.push_back({es0, es0 + 1});
             }
             launch_tc_recheck(iv, qp, ws->bslots_dev, nb, w.cand_count, w.cand_pos, kTcCap, w.active, s);
             MESSI_CUDA(cudaMemsetAsync(w.n_active, 0, 4, s));
-            launch_tc_next_pass(ws->bslots_dev, nb, qp, kTcCap, w.Ubits, w.cand_count, w.active, w.n_active, s);
+            // rows past the gathered queries stay zero
+            MESSI_CUDA(cudaMemsetAsync(w.qtiles2, 0, qtiles_bytes, s));
+            launch_tc_next_pass(ws->bslots_dev, nb, qp, kTcCap, w.Ubits, w.cand_count, w.active, w.n_active, w.qtiles,
+                                w.qtiles2, w.qmap, ix->len, s);
             ws->launches += 3;
             MESSI_CUDA(cudaMemcpyAsync(&more, w.n_active, 4, cudaMemcpyDeviceToHost, s));
             MESSI_CUDA(cudaStreamSynchronize(s));
+            count = more;
+            qt = w.qtiles2;
+            qm = w.qmap;
         }
         launch_batch_finalize(iv, qp, ws->bslots_dev, nb, did + (size_t)g * k, ddist + (size_t)g * k,
                               ws->redo_dev + g, s, &ws->launches);
@@ -895,6 +911,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
     ws->last = messi_stats{};
     ws->last.queries = nq;
     ws->last.kernel_launches = ws->launches - launches0;
+    ws->last.screened_queries = screened;
     ws->last_stream = s;
     ws->last_batched = true;
     if (hi) MESSI_CUDA(cudaMemcpyAsync(ids, did, ibytes, cudaMemcpyDeviceToHost, s));

@@ -161,10 +161,15 @@ k_tc_qprep(const QuerySlot *__restrict__ slots, unsigned B, int len, QueryParams
 }
 
 // Between passes: a query whose candidate list overflowed is screened again
-// with its bound tightened by the rechecked candidates; the others stop.
+// with its bound tightened by the rechecked candidates; the others stop.  The
+// queries screened again are gathered into the first rows of `qtiles2`
+// (their f16 rows copied over, `qmap` giving each one's batch index), so the
+// next pass runs over as many query tiles as they fill, not the batch's.
 __global__ void k_tc_next_pass(const QuerySlot *__restrict__ slots, unsigned B, QueryParams qp, unsigned cap,
                                unsigned *__restrict__ Ubits, unsigned *__restrict__ cand_count,
-                               unsigned *__restrict__ active, unsigned *__restrict__ n_active)
+                               unsigned *__restrict__ active, unsigned *__restrict__ n_active,
+                               const __half *__restrict__ qtiles, __half *__restrict__ qtiles2,
+                               unsigned *__restrict__ qmap, int len)
 {
     const unsigned b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
@@ -172,7 +177,14 @@ __global__ void k_tc_next_pass(const QuerySlot *__restrict__ slots, unsigned B, 
         const float U = prune_threshold(ld_volatile_u64(&slots[b].st->thr), qp.F);
         if (U < __uint_as_float(Ubits[b])) Ubits[b] = __float_as_uint(U);
         cand_count[b] = 0;
-        atomicAdd(n_active, 1u);
+        const unsigned o = atomicAdd(n_active, 1u);
+        qmap[o] = b;
+        const size_t tile_bytes = (size_t)kTcQ * len * 2;
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(qtiles) + (b / kTcQ) * tile_bytes;
+        unsigned char *dst = reinterpret_cast<unsigned char *>(qtiles2) + (o / kTcQ) * tile_bytes;
+        for (unsigned k0 = 0; k0 < (unsigned)len; k0 += 8)
+            *reinterpret_cast<uint4 *>(dst + tc_offset(o % kTcQ, k0, (unsigned)len)) =
+                *reinterpret_cast<const uint4 *>(src + tc_offset(b % kTcQ, k0, (unsigned)len));
     } else {
         active[b] = 0;
     }
@@ -188,6 +200,8 @@ struct ScreenArgs {
     unsigned *cand_count;     // [QT*128]
     unsigned *cand_pos;       // [QT*128][cap]
     const unsigned *active;   // [QT*128]: nonzero when the query collects candidates this pass
+    const unsigned *qmap;     // [B]: batch index of each screened query (nullptr: the identity)
+    unsigned B;               // queries screened (rows of qtiles in use)
     unsigned cap;
     unsigned qpc;             // query tiles per CTA (1 or 2)
     unsigned stages;          // chunk stages of the ring
@@ -331,15 +345,17 @@ struct CandidateSink {
     unsigned *sU;        // shared: U_q bits
     int *lock;           // shared: top-k list locks
     float *topk;         // shared: [QPC * 128][k] top-k lists (1 < k <= kTcTopK)
+    const unsigned *qmap;
     unsigned long long N;
-    unsigned cap;
+    unsigned cap, B;
     int k;
 };
 
-__device__ __noinline__ void screen_candidate(CandidateSink a, unsigned ql, unsigned qj, unsigned long long row,
+__device__ __noinline__ void screen_candidate(CandidateSink a, unsigned ql, unsigned qc, unsigned long long row,
                                               float acc, float xn, float xnrm)
 {
-    if (row >= a.N) return;
+    if (row >= a.N || qc >= a.B) return;
+    const unsigned qj = a.qmap ? a.qmap[qc] : qc;      // the query's batch index
     const float qn = a.qconst[4 * qj + 0], alpha = a.qconst[4 * qj + 1], gamma = a.qconst[4 * qj + 2];
     const float one_m_kappa = 1.f - kKappaP;
     const float lhs = fmaf(xnrm, alpha, fmaf(2.f, acc, -xn * one_m_kappa));
@@ -548,8 +564,9 @@ k_tc_screen(ScreenArgs a)
         const bool cols_live = cbeg < nq * kTcQ;              // one query tile in a QPC = 2 CTA: half idle
         const bool use_topk = a.k > 1 && a.k <= kTcTopK;
         // thread t sets up (and later refreshes) the bounds of query t of the CTA
-        const unsigned own_qj = qt0 * kTcQ + tid;
-        const bool own_have = (unsigned)tid < nq * kTcQ;
+        const unsigned own_qc = qt0 * kTcQ + tid;
+        const bool own_have = (unsigned)tid < nq * kTcQ && own_qc < a.B;
+        const unsigned own_qj = own_have ? (a.qmap ? a.qmap[own_qc] : own_qc) : 0u;
         const float own_qn = own_have ? a.qconst[4 * own_qj + 0] : 0.f;
         const float own_gamma = own_have ? a.qconst[4 * own_qj + 2] : 0.f;
         const bool own_act = own_have && a.active[own_qj] != 0;
@@ -567,7 +584,7 @@ k_tc_screen(ScreenArgs a)
         epi_bar_sync();
         const float amax = __uint_as_float(s_amax);
         const float one_m_kappa = 1.f - kKappaP;
-        const CandidateSink sink{a.qconst, a.cand_count, a.cand_pos, a.Ubits, sE, sU, sLock, topk, a.N, a.cap, a.k};
+        const CandidateSink sink{a.qconst, a.cand_count, a.cand_pos, a.Ubits, sE, sU, sLock, topk, a.qmap, a.N, a.cap, a.B, a.k};
         // series norms of the next tile are fetched one tile ahead
         float nxt_xn = 0.f, nxt_nrm = 0.f;
         auto fetch_norms = [&](unsigned long long j) {
@@ -775,15 +792,17 @@ void launch_tc_qprep(const QuerySlot *slots, unsigned B, int len, const QueryPar
 }
 
 void launch_tc_next_pass(const QuerySlot *slots, unsigned B, const QueryParams &qp, unsigned cap, unsigned *Ubits,
-                         unsigned *cand_count, unsigned *active, unsigned *n_active, cudaStream_t s)
+                         unsigned *cand_count, unsigned *active, unsigned *n_active, const __half *qtiles,
+                         __half *qtiles2, unsigned *qmap, int len, cudaStream_t s)
 {
-    k_tc_next_pass<<<(B + 255) / 256, 256, 0, s>>>(slots, B, qp, cap, Ubits, cand_count, active, n_active);
+    k_tc_next_pass<<<(B + 255) / 256, 256, 0, s>>>(slots, B, qp, cap, Ubits, cand_count, active, n_active, qtiles,
+                                                   qtiles2, qmap, len);
 }
 
 void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm, const __half *qtiles,
                       const float *qconst, unsigned *Ubits, unsigned *cand_count, unsigned *cand_pos,
-                      const unsigned *active, unsigned cap, unsigned long long N, int len, unsigned B, int k,
-                      unsigned *status, cudaStream_t s)
+                      const unsigned *active, const unsigned *qmap, unsigned cap, unsigned long long N, int len,
+                      unsigned B, int k, unsigned *status, cudaStream_t s)
 {
     ScreenArgs a;
     a.rtiles = rtiles;
@@ -795,6 +814,8 @@ void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm,
     a.cand_count = cand_count;
     a.cand_pos = cand_pos;
     a.active = active;
+    a.qmap = qmap;
+    a.B = B;
     a.cap = cap;
     a.N = N;
     a.len = (unsigned)len;

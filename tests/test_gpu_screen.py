@@ -98,3 +98,37 @@ def test_screen_falls_back_outside_f16_range(m):
     ids, d = m.messi_query_batched(ix, q, k=2)
     m.messi_check(ix)
     check(ids, d, *oracle.knn(x.astype(np.float32), q, 2))
+
+
+def test_overflowing_queries_screened_again_in_gathered_tiles(m):
+    """Queries whose candidate lists overflow a pass are screened again on
+    their own, gathered into the first query tile, and still answered exactly.
+
+    For each special query q: 1500 rows q + p with p summing to zero over every
+    pair of points (same PAA, so same iSAX word, at squared distance ~100)
+    fill the seed leaf, so the first pass starts from a loose bound; k = 256
+    lies beyond the top-k tightening, so 6000 rows spread over squared
+    distances 10..90 all pass and overflow the 4096-entry candidate list.  The
+    second pass starts from the exact bound of the rechecked candidates."""
+    rng = np.random.default_rng(90)
+    L, k = 256, 256
+    base = synth.random_walks(30_000, L, seed=91)
+    special = synth.random_walks(2, L, seed=92)
+    rows = [base]
+    for j in range(2):
+        a = rng.normal(0.0, 0.625, size=(1500, L // 2))
+        rows.append(special[j] + np.stack([a, -a], axis=2).reshape(1500, L))
+        u = rng.uniform(10.0, 90.0, size=6000)
+        rows.append(special[j] + rng.normal(size=(6000, L)) * np.sqrt(u / L)[:, None])
+    x = np.concatenate(rows).astype(np.float32)
+    ix = m.messi_build(torch.from_numpy(x).cuda(), 16, 256, leaf_capacity=128)
+    m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN)
+    q = synth.query_mix(base, 300, seed=93)
+    q[5], q[250] = special[0], special[1]        # tile 0 row 5, tile 1 row 122
+    m.messi_set_profiling(ix, True)
+    ids, d = m.messi_query_batched(ix, torch.from_numpy(q).cuda(), k=k, batch=300)
+    m.messi_check(ix)
+    st = m.messi_query_stats(ix)
+    m.messi_set_profiling(ix, False)
+    assert st["scan_launches"] >= 2              # a second pass ran
+    check(ids, d, *oracle.knn(x, q, k))

@@ -272,7 +272,7 @@ void launch_finalize(const IndexView &iv, const QueryParams &qp, QuerySlot slot,
 void launch_lower_bounds(const IndexView &iv, QuerySlot slot, float *lb2_by_id, cudaStream_t s);
 void init_kernel_attributes();
 // screen.cu
-constexpr unsigned kTcCap = 4096;    // candidates per query per screening pass
+constexpr unsigned kTcCap = 16384;   // candidates per query per screening pass
 constexpr unsigned kTcMaxLenHost = 256;
 size_t screen_smem_bytes(int len);
 void init_screen_attributes();

@@ -107,9 +107,9 @@ def test_overflowing_queries_screened_again_in_gathered_tiles(m):
     For each special query q: 1500 rows q + p with p summing to zero over every
     pair of points (same PAA, so same iSAX word, at squared distance ~100)
     fill the seed leaf, so the first pass starts from a loose bound; k = 256
-    lies beyond the top-k tightening, so 6000 rows spread over squared
-    distances 10..90 all pass and overflow the 4096-entry candidate list.  The
-    second pass starts from the exact bound of the rechecked candidates."""
+    lies beyond the top-k tightening, so 18000 rows spread over squared
+    distances 10..90 all pass and overflow the 16384-entry candidate list.
+    The second pass starts from the exact bound of the rechecked candidates."""
     rng = np.random.default_rng(90)
     L, k = 256, 256
     base = synth.random_walks(30_000, L, seed=91)
@@ -118,8 +118,8 @@ def test_overflowing_queries_screened_again_in_gathered_tiles(m):
     for j in range(2):
         a = rng.normal(0.0, 0.625, size=(1500, L // 2))
         rows.append(special[j] + np.stack([a, -a], axis=2).reshape(1500, L))
-        u = rng.uniform(10.0, 90.0, size=6000)
-        rows.append(special[j] + rng.normal(size=(6000, L)) * np.sqrt(u / L)[:, None])
+        u = rng.uniform(10.0, 90.0, size=18000)
+        rows.append(special[j] + rng.normal(size=(18000, L)) * np.sqrt(u / L)[:, None])
     x = np.concatenate(rows).astype(np.float32)
     ix = m.messi_build(torch.from_numpy(x).cuda(), 16, 256, leaf_capacity=128)
     m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN)

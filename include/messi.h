@@ -117,6 +117,32 @@ void messi_free(messi_index *ix);
  * device bytes held, build time).  Host-side only; out must not be NULL. */
 messi_status messi_index_get_info(const messi_index *ix, messi_index_info *out);
 
+/* Sliding-window subsequences of one long series, the collection MESSI
+ * indexes for streaming series and for subsequence matching (Sec. 2: a
+ * streaming series is cut into subsequences of length n by a sliding window
+ * and those are indexed; Sec. 6: subsequence matching slides a window of the
+ * query's length over the long series and indexes every subsequence).
+ * Window i (0 <= i < count, count = (length - n) / stride + 1) is
+ * series[i*stride .. i*stride + n) and becomes row i of out, so a k-NN id
+ * over an index built from out is a window number: start = id * stride.
+ * With znorm != 0 each window is z-normalised (mean 0, standard deviation 1,
+ * Sec. 2) by these steps in FP64, round-to-nearest, no contraction:
+ *   mean = (x_0 + ... + x_{n-1}, summed in order) / n
+ *   var  = ((x_0 - mean)^2 + ... + (x_{n-1} - mean)^2, in order) / n
+ *   inv  = 1 / sqrt(var), or 0 when var == 0 (a constant window -> zeros)
+ *   out_j = (float)((x_j - mean) * inv)
+ * so every other implementation of these steps yields the same bits; with
+ * znorm == 0 the windows are copied unchanged.
+ *
+ * series  device pointer, length float32 values.
+ * n       window length, 1..65536; stride >= 1; length >= n.
+ * out     device pointer, count * n float32 (caller-allocated, row-major).
+ * count   may be NULL; receives the number of windows written.
+ * Asynchronous on `stream` (nothing is allocated).  Returns EINVAL for null
+ * or host pointers and invalid sizes; ECUDA if the launch fails. */
+messi_status messi_windows(const float *series, uint64_t length, uint32_t n, uint32_t stride,
+                           int32_t znorm, float *out, uint64_t *count, messi_stream stream);
+
 /* ---------------------------------------------------------------- query --
  * Exact k-NN (Algorithm 5 for ED, Sec. 3.4 for DTW; k-NN as a sorted array
  * of the k best, Sec. 5.4), one query after another as in the paper's
@@ -146,7 +172,7 @@ messi_status messi_query(const messi_index *ix, const float *queries, uint32_t n
  *     estimated as |x|^2 + |q|^2 - 2 q.x with f16 tensor-core MMAs (FP32
  *     accumulation), widened by a rigorous per-pair error bound; pairs whose
  *     lower end stays within the query's k-th best bound are recomputed
- *     exactly in FP32.  Needs len % 16 == 0, len <= 256 and |values| <= 65000
+ *     exactly in FP32.  Needs len % 16 == 0, len <= 512 and |values| <= 65000
  *     (an f16 copy of the rows, 2*len bytes per series, is built on first
  *     use); otherwise, or for DTW, the call takes the other kernels.
  *   MESSI_BATCH_LB_REFINE: a persistent fused lower-bound-then-refine kernel

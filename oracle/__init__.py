@@ -70,6 +70,7 @@ def _load():
         "orc_lb_improved2": (D, [P, P, P, P, I, I]),
         "orc_knn": (None, [P, I64, I, P, I, I, I, I, I64, I, P, P]),
         "orc_max_threads": (I, []),
+        "orc_windows": (I64, [P, I64, I, I, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -217,6 +218,17 @@ def knn(data, queries, k: int, dist: int = ED, r: int = 0, id_base: int = 0,
     _load().orc_knn(_ptr(data), N, n, _ptr(queries), nq, k, dist, r, id_base, threads,
                     _ptr(ids), _ptr(d2))
     return ids, d2
+
+
+def windows(series, n: int, stride: int = 1, znorm: bool = True) -> np.ndarray:
+    """Every length-n window of a 1-D series at `stride` ([count, n] float32),
+    z-normalised per window by the FP64 steps of ``orc_windows``."""
+    series = _f32(series).reshape(-1)
+    count = (series.shape[0] - n) // stride + 1
+    out = np.empty((count, n), dtype=np.float32)
+    got = _load().orc_windows(_ptr(series), series.shape[0], n, stride, 1 if znorm else 0, _ptr(out))
+    assert got == count
+    return out
 
 
 def merge_topk(parts: Sequence[tuple[np.ndarray, np.ndarray]], k: int):

@@ -325,3 +325,28 @@ void orc_knn(const float *data, int64_t N, int n, const float *queries, int nq,
     free(bi);
     free(bc);
 }
+
+int64_t orc_windows(const float *series, int64_t length, int n, int stride, int znorm, float *out)
+{
+    const int64_t count = (length - n) / stride + 1;
+    for (int64_t i = 0; i < count; ++i) {
+        const float *x = series + i * stride;
+        float *o = out + i * (int64_t)n;
+        if (!znorm) {
+            for (int j = 0; j < n; ++j) o[j] = x[j];
+            continue;
+        }
+        double sum = 0.0;
+        for (int j = 0; j < n; ++j) sum = sum + (double)x[j];
+        const double mean = sum / (double)n;
+        double ss = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const double d = (double)x[j] - mean;
+            ss = ss + d * d;
+        }
+        const double var = ss / (double)n;
+        const double inv = var > 0.0 ? 1.0 / sqrt(var) : 0.0;
+        for (int j = 0; j < n; ++j) o[j] = (float)(((double)x[j] - mean) * inv);
+    }
+    return count;
+}

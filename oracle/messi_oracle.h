@@ -91,6 +91,17 @@ void orc_knn(const float *data, int64_t N, int n, const float *queries, int nq,
 /* Number of OpenMP threads the oracle would use for threads <= 0. */
 int orc_max_threads(void);
 
+/* Sliding-window subsequences (Sec. 2: a streaming series is cut into
+ * subsequences of length n by a sliding window, which are then indexed;
+ * Sec. 6: subsequence matching indexes every window of the query's length).
+ * Window i = series[i*stride .. i*stride + n) for i < count =
+ * (length - n) / stride + 1, written as row i of out.  With znorm each window
+ * is z-normalised (mean 0, standard deviation 1, Sec. 2): mean = sequential
+ * FP64 sum / n, var = sequential FP64 sum of (x - mean)^2 / n, inv =
+ * 1 / sqrt(var) (0 when var is 0), out = (float)((x - mean) * inv).
+ * Returns count. */
+int64_t orc_windows(const float *series, int64_t length, int n, int stride, int znorm, float *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,7 @@ _SIGS = {
     "messi_build": [_P, _U64, _U32, _U32, _U32, _P, _P, ctypes.POINTER(_P)],
     "messi_free": [_P],
     "messi_index_get_info": [_P, ctypes.POINTER(MessiIndexInfo)],
+    "messi_windows": [_P, _U64, _U32, _U32, _I, _P, ctypes.POINTER(_U64), _P],
     "messi_query": [_P, _P, _U32, _U32, _I, _U32, _P, _P, _P],
     "messi_query_batched": [_P, _P, _U32, _U32, _I, _U32, _U32, _P, _P, _P],
     "messi_lower_bounds": [_P, _P, _I, _U32, _P, _P],
@@ -194,6 +195,42 @@ def messi_build(series, segments: int = 16, cardinality: int = 256, leaf_capacit
     _check(_lib.messi_build(p, n, length, segments, cardinality, ctypes.byref(cfg),
                             _stream(stream, series), ctypes.byref(out)), "messi_build")
     return Index(out, n, length, segments, cardinality)
+
+
+def messi_windows(series, n: int, stride: int = 1, znorm: bool = True, out=None, stream=None):
+    """Every length-n window of the 1-D device tensor `series` at `stride`, as
+    a [count, n] float32 device tensor (row i starts at i * stride),
+    z-normalised per window when `znorm`."""
+    import torch
+
+    series = _f32(series)
+    if not _is_torch(series) or not series.is_cuda or series.ndim != 1:
+        raise ValueError("series must be a 1-D CUDA tensor")
+    length = series.shape[0]
+    if n < 1 or stride < 1 or length < n:
+        raise ValueError("need 1 <= n <= len(series) and stride >= 1")
+    count = (length - n) // stride + 1
+    if out is None:
+        out = torch.empty((count, n), dtype=torch.float32, device=series.device)
+    elif tuple(out.shape) != (count, n) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous float32 tensor of shape ({count}, {n})")
+    got = ctypes.c_uint64(0)
+    _check(_lib.messi_windows(ctypes.c_void_p(series.data_ptr()), length, n, stride, 1 if znorm else 0,
+                              ctypes.c_void_p(out.data_ptr()), ctypes.byref(got), _stream(stream, series)),
+           "messi_windows")
+    return out
+
+
+def messi_build_windows(series, n: int, stride: int = 1, znorm: bool = True, segments: int = 16,
+                        cardinality: int = 256, leaf_capacity: int = 0, stream=None) -> Index:
+    """Index every length-n window of one long device series (subsequence
+    matching): ids of the answers are window numbers, start = id * stride.
+    The window matrix is freed once the index holds its own copy."""
+    w = messi_windows(series, n, stride, znorm, stream=stream)
+    try:
+        return messi_build(w, segments, cardinality, leaf_capacity, stream)
+    finally:
+        del w
 
 
 def _outputs(nq, k, on_cuda, device=None):

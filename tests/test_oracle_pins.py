@@ -402,3 +402,37 @@ def test_leaf_partition_properties(N, cap, card):
         if d > w:                                              # its parent had to split
             parent = p >> 1
             assert sum(1 for kk in keys if kk >> (128 - d + 1) == parent) > cap
+
+
+# ------------------------------------------------------ sliding windows
+@pytest.mark.parametrize("length,n,stride", [(1000, 64, 1), (1003, 64, 3), (257, 256, 1), (300, 16, 7)])
+def test_windows_plain_are_slices(length, n, stride):
+    # Sec. 2 / Sec. 6: window i is series[i*stride .. i*stride + n); the
+    # number of windows is the number of starts that leave n points
+    x = np.random.default_rng(length + n).normal(size=length).astype(np.float32)
+    w = oracle.windows(x, n, stride, znorm=False)
+    ref = np.lib.stride_tricks.sliding_window_view(x, n)[::stride]
+    assert w.shape == ref.shape == ((length - n) // stride + 1, n)
+    assert np.array_equal(w, ref)
+
+
+def test_windows_znorm_matches_numpy_population_moments():
+    # z-normalisation (Sec. 2: mean 0, standard deviation 1) against numpy's
+    # mean and population std in float64, a different summation order: equal
+    # to within float32 rounding, and a sample std (n - 1) would be 0.2% off
+    x = np.cumsum(np.random.default_rng(5).normal(size=5000)).astype(np.float32)
+    n = 256
+    w = oracle.windows(x, n, 5, znorm=True)
+    raw = np.lib.stride_tricks.sliding_window_view(x, n)[::5].astype(np.float64)
+    ref = (raw - raw.mean(axis=1, keepdims=True)) / raw.std(axis=1, keepdims=True)
+    assert np.max(np.abs(w - ref)) < 2e-6
+    assert np.max(np.abs(w.astype(np.float64).mean(axis=1))) < 1e-6
+    assert np.max(np.abs(w.astype(np.float64).std(axis=1) - 1.0)) < 1e-6
+
+
+def test_windows_constant_window_becomes_zeros():
+    x = np.random.default_rng(6).normal(size=400).astype(np.float32)
+    x[100:200] = 2.5
+    w = oracle.windows(x, 64, 1, znorm=True)
+    assert np.all(w[100:137] == 0.0)            # windows entirely inside the constant stretch
+    assert np.any(w[99] != 0.0)                  # starts on a random point

@@ -61,6 +61,9 @@ def parse():
                     help="lower-bound batch form: time its shapes on the warm-up queries first")
     ap.add_argument("--mix", default="mixed", choices=["mixed", "fresh", "s0.1", "s0.5", "s1.0"],
                     help="query class (default: the paper-shaped mix)")
+    ap.add_argument("--windows", action="store_true",
+                    help="subsequence collection: the n z-normalised sliding windows (length --len, stride 1) "
+                         "of one random walk of n + len - 1 points")
     return ap.parse_args()
 
 
@@ -316,7 +319,20 @@ def run_messi(args, ws, rank, local):
         pg = dist
     B, K, W = args.batch, args.steps, args.warmup
 
-    data = synth.random_walks_torch(args.n, args.len, seed=synth.DATASET_SEED + rank, device=dev)
+    windows = None
+    if args.windows:
+        walk = synth.random_walks_torch(1, args.n + args.len - 1, seed=synth.DATASET_SEED + rank, device=dev)[0]
+        torch.cuda.synchronize()
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0.record()
+        data = m.messi_windows(walk, args.len, 1, True)
+        w1.record()
+        torch.cuda.synchronize()
+        wms = w0.elapsed_time(w1)
+        del walk
+        windows = {"ms": wms, "written_gbps": args.n * args.len * 4 / (wms * 1e-3) / 1e9}
+    else:
+        data = synth.random_walks_torch(args.n, args.len, seed=synth.DATASET_SEED + rank, device=dev)
     torch.cuda.synchronize()
     ix = m.messi_build(data, 16, 256)
     info = m.messi_index_get_info(ix)
@@ -351,7 +367,10 @@ def run_messi(args, ws, rank, local):
 
     dist_code = 1 if args.dist == "dtw" else 0
     window = (args.window if args.window >= 0 else int(0.10 * args.len)) if dist_code else 0
-    batch_mode = "tc_screen" if args.batch_mode == "tc" else "lb_refine"
+    # the screen takes lengths that are multiples of 16 up to 512 (ED only); other
+    # batches run the lower-bound kernels whatever the requested mode
+    screen_ok = args.len % 16 == 0 and args.len <= 512 and args.dist == "ed"
+    batch_mode = "tc_screen" if args.batch_mode == "tc" and screen_ok else "lb_refine"
     m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN if args.batch_mode == "tc" else m.MESSI_BATCH_LB_REFINE)
     tuning = None
     if args.autotune and args.batch_mode == "lb" and B >= 32:
@@ -434,13 +453,16 @@ def run_messi(args, ws, rank, local):
             "metric": METRIC, "value": head["value"], "unit": "queries/s", "n_gpus": ws, "steps": K, "warmup": W,
             "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": head["value"] / PAPER_QPS, "dtype": "f32", "data": DATA_DESC,
-            "config": {"workload": f"{args.n} x {args.len} fp32 random walks, "
-                                   f"{'ED' if not dist_code else f'DTW window {window}'}, k={args.k}, 16 segments, "
+            "config": {"workload": (f"{args.n} z-normalised sliding windows (length {args.len}, stride 1) of one "
+                                    f"{args.n + args.len - 1}-point random walk" if args.windows else
+                                    f"{args.n} x {args.len} fp32 random walks") +
+                                   f", {'ED' if not dist_code else f'DTW window {window}'}, k={args.k}, 16 segments, "
                                    f"8-bit SAX", "form": head_form, "queries": args.mix,
                        "queries_per_step": B, "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (16 B iSAX word per series streamed per query)"},
             "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
             "build_gbps": build_gbps, "build_ms": info["build_ms"],
+            **({"windows": windows} if windows else {}),
             "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": head["gpu_launches"],
             "clocks": head["clocks"], "parity_sample": parity, "forms": forms,
         }

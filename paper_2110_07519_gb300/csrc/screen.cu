@@ -33,7 +33,6 @@ constexpr int kTcRows = 128;        // M: series per tile
 constexpr int kTcQ = 128;           // N: queries per tile
 constexpr float kKappa = 2.4e-7f;   // 4u: FP32 evaluation of s and rounding of the norms
 constexpr float kKappaP = 7.2e-7f;  // 12u: kappa plus the rounding of the rearranged test
-constexpr int kTcMaxLen = 256;      // query tiles of 128 x len halves stay resident in shared memory
 constexpr int kTcMaxStages = 16;
 constexpr size_t kTcSmemBudget = 216 * 1024;   // dynamic shared memory of one screen CTA
 
@@ -315,6 +314,8 @@ __device__ __forceinline__ bool epi_bar_any(bool v)
 // taken with a bounded spin; a lane that does not get the lock skips its
 // update, which only leaves the bound looser.
 constexpr int kTcTopK = 16;
+static_assert((kTcSmemBudget - (size_t)kTcQ * kTcMaxLenHost * 2 - (size_t)kTcQ * kTcTopK * 4) / (kTcRows * 64 * 2) >= 4,
+              "one query tile of the longest screened length, its top-k lists and 4 ring stages fit");
 
 __device__ __forceinline__ bool topk_lock(int *l)
 {
@@ -822,6 +823,9 @@ void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm,
     a.QT = (B + kTcQ - 1) / kTcQ;
     a.k = k;
     a.status = status;
+    // two query tiles per CTA when they leave room for 4 ring stages (len <= 256),
+    // else one: at the longest screened length (512) a 128 KB query tile and
+    // its 8 KB of top-k lists leave 80 KB, 5 stages of 16 KB
     a.qpc = (a.QT >= 2 && screen_stages(len, 2, k) >= 4) ? 2u : 1u;
     a.stages = screen_stages(len, a.qpc, k);
     const unsigned QG = (a.QT + a.qpc - 1) / a.qpc;

@@ -90,6 +90,22 @@ def test_screened_ties_and_members(m):
     assert ids[0].tolist() == [11, 200, 29_999]
 
 
+def test_screen_length_512_one_query_tile_per_cta(m):
+    # at len 512 a query tile (128 KB of f16) fills most of shared memory, so
+    # each CTA holds one and the MMAs run with N = 128; three query tiles here
+    x = synth.random_walks(40_000, 512, seed=85)
+    ix = m.messi_build(torch.from_numpy(x).cuda(), 16, 256)
+    m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN)
+    q = synth.query_mix(x, 300, seed=86)
+    m.messi_set_profiling(ix, True)
+    for k in (1, 5):
+        ids, d = m.messi_query_batched(ix, torch.from_numpy(q).cuda(), k=k, batch=300)
+        m.messi_check(ix)
+        assert m.messi_query_stats(ix)["screened_queries"] >= 300      # the screen ran
+        check(ids, d, *oracle.knn(x, q, k))
+    m.messi_set_profiling(ix, False)
+
+
 def test_screen_falls_back_outside_f16_range(m):
     x = synth.random_walks(5000, 64, seed=80) * 1e5        # beyond f16: no screen copy
     ix = m.messi_build(torch.from_numpy(x.astype(np.float32)).cuda(), 16, 256)

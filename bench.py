@@ -367,9 +367,9 @@ def run_messi(args, ws, rank, local):
 
     dist_code = 1 if args.dist == "dtw" else 0
     window = (args.window if args.window >= 0 else int(0.10 * args.len)) if dist_code else 0
-    # the screen takes lengths that are multiples of 16 up to 512 (ED only); other
+    # the screen takes lengths that are multiples of 16 up to 2048 (ED only); other
     # batches run the lower-bound kernels whatever the requested mode
-    screen_ok = args.len % 16 == 0 and args.len <= 512 and args.dist == "ed"
+    screen_ok = args.len % 16 == 0 and args.len <= 2048 and args.dist == "ed"
     batch_mode = "tc_screen" if args.batch_mode == "tc" and screen_ok else "lb_refine"
     m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN if args.batch_mode == "tc" else m.MESSI_BATCH_LB_REFINE)
     tuning = None

@@ -172,7 +172,7 @@ messi_status messi_query(const messi_index *ix, const float *queries, uint32_t n
  *     estimated as |x|^2 + |q|^2 - 2 q.x with f16 tensor-core MMAs (FP32
  *     accumulation), widened by a rigorous per-pair error bound; pairs whose
  *     lower end stays within the query's k-th best bound are recomputed
- *     exactly in FP32.  Needs len % 16 == 0, len <= 512 and |values| <= 65000
+ *     exactly in FP32.  Needs len % 16 == 0, len <= 2048 and |values| <= 65000
  *     (an f16 copy of the rows, 2*len bytes per series, is built on first
  *     use); otherwise, or for DTW, the call takes the other kernels.
  *   MESSI_BATCH_LB_REFINE: a persistent fused lower-bound-then-refine kernel

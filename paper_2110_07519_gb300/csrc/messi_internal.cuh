@@ -273,7 +273,7 @@ void launch_lower_bounds(const IndexView &iv, QuerySlot slot, float *lb2_by_id, 
 void init_kernel_attributes();
 // screen.cu
 constexpr unsigned kTcCap = 16384;   // candidates per query per screening pass
-constexpr unsigned kTcMaxLenHost = 512;   // longest series the screen takes (its query tiles stay resident)
+constexpr unsigned kTcMaxLenHost = 2048;  // longest series the screen takes
 size_t screen_smem_bytes(int len);
 void init_screen_attributes();
 void launch_make_screen_copy(const float *raw, unsigned long long N, int len, __half *tiles, float *xn, float *xnorm,

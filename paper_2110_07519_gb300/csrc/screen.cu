@@ -44,6 +44,24 @@ __host__ __device__ __forceinline__ unsigned chunk_k(unsigned len)
     return (len % 64 == 0) ? 64u : (len % 32 == 0) ? 32u : 16u;
 }
 
+// Query tiles stay resident in shared memory up to kTcResidentLen points;
+// longer queries are stored chunk-major like the series tiles and streamed
+// through the ring with each series chunk.
+constexpr unsigned kTcResidentLen = 512;
+
+__host__ __device__ __forceinline__ unsigned query_chunk(unsigned len)
+{
+    return len > kTcResidentLen ? chunk_k(len) : 0u;
+}
+
+// byte offset of element (r, k) in a query tile: full-K core-matrix layout
+// when resident, chunk-major when streamed
+__host__ __device__ __forceinline__ unsigned qtile_offset(unsigned r, unsigned k, unsigned len)
+{
+    const unsigned qc = query_chunk(len);
+    return qc ? (k / qc) * (kTcQ * qc * 2) + tc_offset(r, k % qc, qc) : tc_offset(r, k, len);
+}
+
 __device__ __forceinline__ float tc_coef(int len)
 {
     return 1.002f * (9.765625e-4f + (float)(len + 16) * 1.1920929e-7f);
@@ -120,7 +138,7 @@ k_tc_qprep(const QuerySlot *__restrict__ slots, unsigned B, int len, QueryParams
             h[i] = __float2half_rn(v);
             ss = __dadd_rn(ss, __dmul_rn((double)v, (double)v));
         }
-        *reinterpret_cast<uint4 *>(tbase + tc_offset(r, (unsigned)k0, (unsigned)len)) = *reinterpret_cast<uint4 *>(h);
+        *reinterpret_cast<uint4 *>(tbase + qtile_offset(r, (unsigned)k0, (unsigned)len)) = *reinterpret_cast<uint4 *>(h);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -182,8 +200,8 @@ __global__ void k_tc_next_pass(const QuerySlot *__restrict__ slots, unsigned B, 
         const unsigned char *src = reinterpret_cast<const unsigned char *>(qtiles) + (b / kTcQ) * tile_bytes;
         unsigned char *dst = reinterpret_cast<unsigned char *>(qtiles2) + (o / kTcQ) * tile_bytes;
         for (unsigned k0 = 0; k0 < (unsigned)len; k0 += 8)
-            *reinterpret_cast<uint4 *>(dst + tc_offset(o % kTcQ, k0, (unsigned)len)) =
-                *reinterpret_cast<const uint4 *>(src + tc_offset(b % kTcQ, k0, (unsigned)len));
+            *reinterpret_cast<uint4 *>(dst + qtile_offset(o % kTcQ, k0, (unsigned)len)) =
+                *reinterpret_cast<const uint4 *>(src + qtile_offset(b % kTcQ, k0, (unsigned)len));
     } else {
         active[b] = 0;
     }
@@ -314,8 +332,10 @@ __device__ __forceinline__ bool epi_bar_any(bool v)
 // taken with a bounded spin; a lane that does not get the lock skips its
 // update, which only leaves the bound looser.
 constexpr int kTcTopK = 16;
-static_assert((kTcSmemBudget - (size_t)kTcQ * kTcMaxLenHost * 2 - (size_t)kTcQ * kTcTopK * 4) / (kTcRows * 64 * 2) >= 4,
-              "one query tile of the longest screened length, its top-k lists and 4 ring stages fit");
+static_assert((kTcSmemBudget - (size_t)kTcQ * kTcResidentLen * 2 - (size_t)kTcQ * kTcTopK * 4) / (kTcRows * 64 * 2) >= 4,
+              "one query tile of the longest resident length, its top-k lists and 4 ring stages fit");
+static_assert((kTcSmemBudget - (size_t)2 * kTcQ * kTcTopK * 4) / (3 * kTcRows * 64 * 2) >= 4,
+              "streamed queries: 4 stages of a series chunk and two query chunks fit next to two top-k lists");
 
 __device__ __forceinline__ bool topk_lock(int *l)
 {
@@ -424,9 +444,14 @@ k_tc_screen(ScreenArgs a)
     const unsigned chunk_bytes = kTcRows * ck * 2;
     const unsigned qtile_bytes = kTcQ * len * 2;
     const unsigned QPC = a.qpc, NS = a.stages;
-    unsigned char *qbuf = smem;                               // QPC query tiles
-    unsigned char *ring = smem + QPC * qtile_bytes;           // NS chunk stages
-    float *topk = reinterpret_cast<float *>(ring + NS * chunk_bytes);   // [QPC * 128][k] when 1 < k <= kTcTopK
+    // resident queries: QPC query tiles, then NS stages of one series chunk;
+    // streamed queries (len > kTcResidentLen): NS stages of a series chunk
+    // followed by the same K chunk of each of the QPC query tiles
+    const bool qstream = query_chunk(len) != 0;
+    const unsigned stage_bytes = chunk_bytes * (qstream ? 1 + QPC : 1);
+    unsigned char *qbuf = smem;
+    unsigned char *ring = smem + (qstream ? 0 : QPC * qtile_bytes);
+    float *topk = reinterpret_cast<float *>(ring + NS * stage_bytes);   // [QPC * 128][k] when 1 < k <= kTcTopK
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned QG = (a.QT + QPC - 1) / QPC;               // query-tile groups
     const unsigned groups = gridDim.x / QG;                   // CTAs per query-tile group
@@ -462,7 +487,7 @@ k_tc_screen(ScreenArgs a)
         // ------------------------------------------------ producers
         const unsigned p = (warp == kTcProdWarp0) ? 0u : 1u;
         if (lane == 0 && nt > 0) {
-            if (p == 0) {
+            if (p == 0 && !qstream) {
                 mbar_arrive_expect_tx(&bar_q, nq * qtile_bytes);
                 for (unsigned qi = 0; qi < nq; ++qi)
                     bulk_g2s(qbuf + qi * qtile_bytes,
@@ -482,10 +507,16 @@ k_tc_screen(ScreenArgs a)
                     break;
                 }
                 const unsigned long long rt = g + j * groups;
-                mbar_arrive_expect_tx(&bar_full[st], chunk_bytes);
-                bulk_g2s(ring + st * chunk_bytes,
-                         reinterpret_cast<const unsigned char *>(a.rtiles) + (rt * nch + c) * chunk_bytes, chunk_bytes,
-                         &bar_full[st]);
+                unsigned char *stage = ring + st * stage_bytes;
+                mbar_arrive_expect_tx(&bar_full[st], chunk_bytes * (qstream ? 1 + nq : 1));
+                bulk_g2s(stage, reinterpret_cast<const unsigned char *>(a.rtiles) + (rt * nch + c) * chunk_bytes,
+                         chunk_bytes, &bar_full[st]);
+                if (qstream)
+                    for (unsigned qi = 0; qi < nq; ++qi)
+                        bulk_g2s(stage + (1 + qi) * chunk_bytes,
+                                 reinterpret_cast<const unsigned char *>(a.qtiles) +
+                                     ((unsigned long long)(qt0 + qi) * nch + c) * chunk_bytes,
+                                 chunk_bytes, &bar_full[st]);
                 st += 2;
                 while (st >= NS) {
                     st -= NS;
@@ -506,15 +537,18 @@ k_tc_screen(ScreenArgs a)
         if (nt > 0) {
             const unsigned idesc = tc_idesc_f16(kTcRows, nq * kTcQ);
             const unsigned sq = smem_u32(qbuf), sr = smem_u32(ring);
-            const unsigned sbo_q = (len / 8) * 128, sbo_r = (ck / 8) * 128;
+            const unsigned sbo_r = (ck / 8) * 128, sbo_q = qstream ? sbo_r : (len / 8) * 128;
             // descriptors of k-step 0 of ring stage 0 and of the query
             // operand; the others differ only in the start-address field
             // (address >> 4, bits 0-13), reached by plain adds since every
             // shared-memory address here is below 256 KB.  Query tile 1
             // starts 16 row groups (16 * sbo_q bytes) after tile 0, so one
             // descriptor spans both.
-            const unsigned long long rd0 = tc_desc(sr, 128, sbo_r), qd0 = tc_desc(sq, 128, sbo_q);
-            const unsigned cstride16 = chunk_bytes >> 4;
+            // (streamed queries: the query operand sits chunk_bytes into each
+            // stage and advances with the stage)
+            const unsigned long long rd0 = tc_desc(sr, 128, sbo_r);
+            const unsigned long long qd0 = qstream ? tc_desc(sr + chunk_bytes, 128, sbo_q) : tc_desc(sq, 128, sbo_q);
+            const unsigned sstride16 = stage_bytes >> 4;
             unsigned st = 0;
             const unsigned G = (nch % 2 == 0) ? 2u : 1u;    // chunks per meeting with the relay
             for (unsigned long long j = 0; j < nt; ++j) {
@@ -523,7 +557,8 @@ k_tc_screen(ScreenArgs a)
                     if (c % G == 0) relay_bar_sync();
                     tc_fence_after();
                     if (lane == 0 && !s_fail) {
-                        mma_chunk<KS>(tmem + ab * acc_cols, rd0 + st * cstride16, qd0 + c * (KS * 16u), idesc, c != 0);
+                        const unsigned long long qd = qstream ? qd0 + st * sstride16 : qd0 + c * (KS * 16u);
+                        mma_chunk<KS>(tmem + ab * acc_cols, rd0 + st * sstride16, qd, idesc, c != 0);
                         tc_commit(&bar_empty[st]);
                     }
                     __syncwarp();
@@ -536,7 +571,7 @@ k_tc_screen(ScreenArgs a)
     } else if (warp == kTcRelayWarp) {
         // ------------------------------------------------ relay
         if (nt > 0) {
-            if (lane == 0 && !mbar_wait_bounded(&bar_q, 0)) s_fail = 1;
+            if (lane == 0 && !qstream && !mbar_wait_bounded(&bar_q, 0)) s_fail = 1;
             unsigned st = 0, fpar = 0;          // ring stage and the parity of its current fill
             for (unsigned long long j = 0; j < nt; ++j) {
                 const unsigned ab = (unsigned)(j & 1);
@@ -759,13 +794,16 @@ static size_t screen_topk_bytes(unsigned qpc, int k)
     return (k > 1 && k <= kTcTopK) ? (size_t)qpc * kTcQ * k * sizeof(float) : 0;
 }
 
-// ring stages that fit next to `qpc` resident query tiles and their top-k lists
+// ring stages that fit next to `qpc` resident query tiles (or, streamed, with
+// their chunks inside each stage) and the top-k lists
 unsigned screen_stages(int len, unsigned qpc, int k)
 {
+    const bool qstream = query_chunk((unsigned)len) != 0;
     const size_t chunk = (size_t)kTcRows * chunk_k((unsigned)len) * 2;
-    const size_t q = (size_t)qpc * kTcQ * len * 2 + screen_topk_bytes(qpc, k);
+    const size_t stage = chunk * (qstream ? 1 + qpc : 1);
+    const size_t q = (qstream ? 0 : (size_t)qpc * kTcQ * len * 2) + screen_topk_bytes(qpc, k);
     const size_t left = kTcSmemBudget > q ? kTcSmemBudget - q : 0;
-    return (unsigned)std::min<size_t>(kTcMaxStages, left / chunk);
+    return (unsigned)std::min<size_t>(kTcMaxStages, left / stage);
 }
 
 void init_screen_attributes()
@@ -823,9 +861,10 @@ void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm,
     a.QT = (B + kTcQ - 1) / kTcQ;
     a.k = k;
     a.status = status;
-    // two query tiles per CTA when they leave room for 4 ring stages (len <= 256),
-    // else one: at the longest screened length (512) a 128 KB query tile and
-    // its 8 KB of top-k lists leave 80 KB, 5 stages of 16 KB
+    // two query tiles per CTA when they leave room for 4 ring stages (len <= 256,
+    // and every streamed length: 4 stages of 48 KB next to 16 KB of top-k
+    // lists), else one: at the longest resident length (512) a 128 KB query
+    // tile and its 8 KB of top-k lists leave 80 KB, 5 stages of 16 KB
     a.qpc = (a.QT >= 2 && screen_stages(len, 2, k) >= 4) ? 2u : 1u;
     a.stages = screen_stages(len, a.qpc, k);
     const unsigned QG = (a.QT + a.qpc - 1) / a.qpc;

@@ -124,9 +124,9 @@ def test_set_tuning_rejects_bad_shapes(m, coll):
             m.messi_set_tuning(ix, *bad)
 
 
-@pytest.mark.parametrize("n,w", [(40, 10), (1024, 8)])
+@pytest.mark.parametrize("n,w", [(40, 10), (72, 9)])
 def test_batched_lengths_outside_the_screen(m, n, w):
-    # the tensor-core screen needs len % 16 == 0 and len <= 512; other lengths
+    # the tensor-core screen needs len % 16 == 0 (and len <= 2048); other lengths
     # take the lower-bound form in either batch mode and stay exact
     x = synth.random_walks(8_000, n, seed=60 + n)
     ix = m.messi_build(torch.from_numpy(x).cuda(), w, 256)

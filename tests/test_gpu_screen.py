@@ -106,6 +106,23 @@ def test_screen_length_512_one_query_tile_per_cta(m):
     m.messi_set_profiling(ix, False)
 
 
+@pytest.mark.parametrize("n,N,nq", [(1024, 20_000, 300), (2048, 8_000, 130)])
+def test_screen_streamed_query_chunks(m, n, N, nq):
+    # beyond 512 points the query tiles are streamed chunk by chunk with the
+    # series chunks; 300 queries make query-tile groups of two and of one
+    x = synth.random_walks(N, n, seed=87 + n)
+    ix = m.messi_build(torch.from_numpy(x).cuda(), 16, 256)
+    m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN)
+    q = synth.query_mix(x, nq, seed=88 + n)
+    m.messi_set_profiling(ix, True)
+    for k in (1, 5):
+        ids, d = m.messi_query_batched(ix, torch.from_numpy(q).cuda(), k=k, batch=nq)
+        m.messi_check(ix)
+        assert m.messi_query_stats(ix)["screened_queries"] >= nq      # the screen ran
+        check(ids, d, *oracle.knn(x, q, k))
+    m.messi_set_profiling(ix, False)
+
+
 def test_screen_falls_back_outside_f16_range(m):
     x = synth.random_walks(5000, 64, seed=80) * 1e5        # beyond f16: no screen copy
     ix = m.messi_build(torch.from_numpy(x.astype(np.float32)).cuda(), 16, 256)

@@ -44,10 +44,13 @@ __host__ __device__ __forceinline__ unsigned chunk_k(unsigned len)
     return (len % 64 == 0) ? 64u : (len % 32 == 0) ? 32u : 16u;
 }
 
-// Query tiles stay resident in shared memory up to kTcResidentLen points;
-// longer queries are stored chunk-major like the series tiles and streamed
-// through the ring with each series chunk.
-constexpr unsigned kTcResidentLen = 512;
+// Query tiles stay resident in shared memory up to kTcResidentLen points (two
+// per CTA, so each MMA has N = 256); longer queries are stored chunk-major
+// like the series tiles and streamed through the ring with each series chunk,
+// still two tiles per CTA.  Measured at 512 points: one resident 128 KB tile
+// per CTA (N = 128) ran 0.65 of the tensor peak, streaming two reaches 0.9 at
+// 1024 points.
+constexpr unsigned kTcResidentLen = 256;
 
 __host__ __device__ __forceinline__ unsigned query_chunk(unsigned len)
 {
@@ -332,8 +335,9 @@ __device__ __forceinline__ bool epi_bar_any(bool v)
 // taken with a bounded spin; a lane that does not get the lock skips its
 // update, which only leaves the bound looser.
 constexpr int kTcTopK = 16;
-static_assert((kTcSmemBudget - (size_t)kTcQ * kTcResidentLen * 2 - (size_t)kTcQ * kTcTopK * 4) / (kTcRows * 64 * 2) >= 4,
-              "one query tile of the longest resident length, its top-k lists and 4 ring stages fit");
+static_assert((kTcSmemBudget - (size_t)2 * kTcQ * kTcResidentLen * 2 - (size_t)2 * kTcQ * kTcTopK * 4) /
+                      (kTcRows * 64 * 2) >= 4,
+              "two query tiles of the longest resident length, their top-k lists and 4 ring stages fit");
 static_assert((kTcSmemBudget - (size_t)2 * kTcQ * kTcTopK * 4) / (3 * kTcRows * 64 * 2) >= 4,
               "streamed queries: 4 stages of a series chunk and two query chunks fit next to two top-k lists");
 
@@ -861,10 +865,10 @@ void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm,
     a.QT = (B + kTcQ - 1) / kTcQ;
     a.k = k;
     a.status = status;
-    // two query tiles per CTA when they leave room for 4 ring stages (len <= 256,
-    // and every streamed length: 4 stages of 48 KB next to 16 KB of top-k
-    // lists), else one: at the longest resident length (512) a 128 KB query
-    // tile and its 8 KB of top-k lists leave 80 KB, 5 stages of 16 KB
+    // two query tiles per CTA when they leave room for 4 ring stages: always
+    // for len <= 256 (resident, 128 KB of tiles) and for every streamed length
+    // (4 stages of 48 KB next to 16 KB of top-k lists); one when the batch
+    // has a single query tile
     a.qpc = (a.QT >= 2 && screen_stages(len, 2, k) >= 4) ? 2u : 1u;
     a.stages = screen_stages(len, a.qpc, k);
     const unsigned QG = (a.QT + a.qpc - 1) / a.qpc;

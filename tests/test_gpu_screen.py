@@ -90,9 +90,10 @@ def test_screened_ties_and_members(m):
     assert ids[0].tolist() == [11, 200, 29_999]
 
 
-def test_screen_length_512_one_query_tile_per_cta(m):
-    # at len 512 a query tile (128 KB of f16) fills most of shared memory, so
-    # each CTA holds one and the MMAs run with N = 128; three query tiles here
+def test_screen_length_512_streamed_query_tiles(m):
+    # at len 512 two query tiles (256 KB of f16) no longer fit in shared
+    # memory: they are streamed chunk by chunk with the series chunks, two per
+    # CTA; three query tiles here make groups of two and of one
     x = synth.random_walks(40_000, 512, seed=85)
     ix = m.messi_build(torch.from_numpy(x).cuda(), 16, 256)
     m.messi_set_batch_mode(ix, m.MESSI_BATCH_TC_SCREEN)

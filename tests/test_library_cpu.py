@@ -107,3 +107,47 @@ def test_every_declared_entry_point_is_documented():
         if not before.endswith("*/"):
             undocumented.append(d.group(1))
     assert not undocumented, undocumented
+
+
+def test_windows_arguments_rejected_without_gpu(lib):
+    # messi_windows validates before touching the device: null, empty or
+    # oversize windows, zero stride, a series shorter than one window, and
+    # host pointers are EINVAL
+    P, U32, U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+    f = lib.messi_windows
+    f.argtypes = [P, U64, U32, U32, ctypes.c_int32, P, ctypes.POINTER(U64), P]
+    x = np.zeros(100, np.float32)
+    o = np.zeros(37 * 64, np.float32)
+    cnt = U64(0)
+    xs, os_ = P(x.ctypes.data), P(o.ctypes.data)
+    assert f(None, 100, 64, 1, 1, os_, ctypes.byref(cnt), None) == 1
+    assert f(xs, 100, 64, 1, 1, None, ctypes.byref(cnt), None) == 1
+    assert f(xs, 100, 0, 1, 1, os_, ctypes.byref(cnt), None) == 1
+    assert f(xs, 100, 70_000, 1, 1, os_, ctypes.byref(cnt), None) == 1
+    assert f(xs, 100, 64, 0, 1, os_, ctypes.byref(cnt), None) == 1
+    assert f(xs, 50, 64, 1, 1, os_, ctypes.byref(cnt), None) == 1
+    assert f(xs, 100, 64, 1, 1, os_, ctypes.byref(cnt), None) == 1     # host buffers
+    assert cnt.value == 0
+
+
+def test_bench_traffic_gate_follows_the_kernel_source(tmp_path, monkeypatch):
+    # bench.py reports the ncu DRAM traffic only while the kernel's sources
+    # hash to the value recorded beside it; scaled by the number of series
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_gate", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    csrc = tmp_path / "paper_2110_07519_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for name in ("screen.cu", "tc.cuh", "device_common.cuh"):
+        (csrc / name).write_text(f"// {name}\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    sha = b.scan_source_sha("k_tc_screen")
+    (tmp_path / "profiles" / "k_tc_screen_traffic.txt").write_text(
+        f"# test\nsource_sha: {sha}\ndram_bytes_per_series: 520.5\n")
+    assert b.profiled_traffic(1000, "k_tc_screen") == pytest.approx(520_500.0)
+    (csrc / "screen.cu").write_text("// changed\n")
+    assert b.profiled_traffic(1000, "k_tc_screen") is None
+    assert b.profiled_traffic(1000, "k_lb_scan") is None          # no summary for it here

@@ -12,14 +12,17 @@
 //   FP32 rounding of the norms (computed in FP64).
 // so s - eps <= true d^2 <= s + eps.  A pair is a candidate when
 // s - eps <= U_q, U_q an upper bound of the query's true k-th squared
-// distance; for k = 1 every s + eps also tightens U_q.  Candidates are then
-// recomputed exactly in FP32 and offered to the query's best-so-far, and the
-// usual FP64 near-tie resolution finishes the query.  A query whose candidate
-// list overflows is screened again with its tightened bound.
+// distance; for k <= 16 the k-th smallest s + eps met so far also tightens
+// U_q.  Candidates are then recomputed exactly in FP32 and offered to the
+// query's best-so-far, and the usual FP64 near-tie resolution finishes the
+// query.  A query whose candidate list overflows is screened again with its
+// tightened bound, together with the other such queries only.
 //
 // Operand tiles (see tc.cuh): rows of the collection are copied once to f16 in
-// 128-row tiles already in the tensor-core layout, so one bulk copy loads a
-// tile; queries are laid out the same way, 128 per tile.
+// 128-row tiles already in the tensor-core layout, chunk-major along K, so
+// one bulk copy loads a K chunk of a tile; queries are laid out the same way,
+// 128 per tile (whole-K while they stay resident in shared memory, chunk-major
+// when they are streamed with the series chunks).
 #include <cuda_fp16.h>
 
 #include <algorithm>

@@ -211,8 +211,21 @@ def mixed_order(qpool, rank):
     return qpool.index_select(0, perm).contiguous()
 
 
+def workload_name(args, window=0):
+    """The workload both arms name in `config`: collection, distance, k, index shape."""
+    coll = (f"{args.n} z-normalised sliding windows (length {args.len}, stride 1) of one "
+            f"{args.n + args.len - 1}-point random walk" if args.windows else
+            f"{args.n} x {args.len} fp32 random walks")
+    dist = "ED" if args.dist == "ed" else f"DTW window {window}"
+    return f"{coll}, {dist}, k={args.k}, 16 segments, 8-bit SAX"
+
+
 def run_reference(args, ws, rank, local):
     if rank != 0:
+        return
+    if args.windows or args.dist != "ed":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the ED random-walk "
+                                                             "workload only (no --windows, no --dist dtw)"}))
         return
     import torch
 
@@ -237,8 +250,8 @@ def run_reference(args, ws, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_QPS, "dtype": "f64",
         "data": DATA_DESC,
-        "config": {"workload": f"{args.n} x {args.len} fp32 random walks, ED, k={args.k}",
-                   "queries_per_step": 1, "l2": "inputs larger than L2 (host memory)"},
+        "config": {"workload": workload_name(args), "form": "oracle: FP64 brute force on the host cores",
+                   "queries": "mixed", "queries_per_step": 1, "l2": "inputs larger than L2 (host memory)"},
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle",
                          "sample": f"{args.steps} timed queries (1 per step), FP64 brute force over all "
                                    f"{args.n} series; device-to-host chunk copies excluded"},
@@ -453,11 +466,7 @@ def run_messi(args, ws, rank, local):
             "metric": METRIC, "value": head["value"], "unit": "queries/s", "n_gpus": ws, "steps": K, "warmup": W,
             "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": head["value"] / PAPER_QPS, "dtype": "f32", "data": DATA_DESC,
-            "config": {"workload": (f"{args.n} z-normalised sliding windows (length {args.len}, stride 1) of one "
-                                    f"{args.n + args.len - 1}-point random walk" if args.windows else
-                                    f"{args.n} x {args.len} fp32 random walks") +
-                                   f", {'ED' if not dist_code else f'DTW window {window}'}, k={args.k}, 16 segments, "
-                                   f"8-bit SAX", "form": head_form, "queries": args.mix,
+            "config": {"workload": workload_name(args, window), "form": head_form, "queries": args.mix,
                        "queries_per_step": B, "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (16 B iSAX word per series streamed per query)"},
             "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],

@@ -10,8 +10,9 @@ any order with up to 2 ulp per addition).  Here the f16 rounding is numpy's
 sequential and pairwise round-to-nearest, and sequential round-toward-zero
 (a pessimistic model of an adder that truncates) -- on random walks, on
 all-positive rows (no cancellation: the largest accumulated error), on rows
-near the f16 subnormal range and near its maximum, for every length the
-screen takes (16 .. 2048)."""
+whose f16 rounding errors all share one sign (the worst case of the f16
+term), on rows near the f16 subnormal range and near its maximum, for every
+length the screen takes (16 .. 2048)."""
 import math
 
 import numpy as np

@@ -105,3 +105,70 @@ def test_bound_is_not_vacuous():
     # |q||x| at len 256, so it still separates near from far neighbours
     assert bound(256, 16.0, 16.0) / 256.0 < 1.3e-3
     assert bound(2048, 45.0, 45.0) / 2025.0 < 1.3e-3
+
+
+# ------------------------------------------------ the candidate test itself
+# The epilogue's test, restated with the kernel's constants and rounding
+# directions in float32 (each operation below names the rounding the kernel
+# asks for), to check the claim it rests on: a pair whose true squared
+# distance is at most U is always a candidate -- both under the CTA-wide test
+# and under the rare path's re-test with the query's own slack.
+KP = float(np.float32(7.2e-7))
+
+
+def rn(v):
+    return float(np.float32(v))
+
+
+def ru(v):
+    r = np.float32(v)
+    return float(r) if float(r) >= v else float(np.nextafter(r, np.float32(np.inf)))
+
+
+def rd(v):
+    r = np.float32(v)
+    return float(r) if float(r) <= v else float(np.nextafter(r, np.float32(-np.inf)))
+
+
+def norms(v):
+    ss = 0.0
+    for t in v.astype(np.float64):
+        ss += t * t
+    return rn(ss), ru(math.sqrt(ss * (1.0 + 1e-12)))      # |v|^2 to nearest, |v| rounded up
+
+
+def query_constants(n, qn, qnorm):
+    f = np.float32
+    coef = f(1.002) * (f(9.765625e-4) + f(n + 16) * f(1.1920929e-7))
+    beta = f(5.9604645e-8) * f(math.sqrt(n)) * f(1.002)
+    alpha = (f(qnorm) * (f(2) * coef + f(2) * f(KP)) + beta) * (f(1) + f(1e-6))
+    gamma = (beta * f(qnorm) + f(KP) * f(qn)) * (f(1) + f(1e-6))
+    return float(alpha), float(gamma)
+
+
+@pytest.mark.parametrize("n", [16, 128, 256, 1024, 2048])
+@pytest.mark.parametrize("scale", [1.0, 100.0])
+def test_candidate_test_has_no_false_negatives(n, scale):
+    rng = np.random.default_rng(n + int(scale))
+    q = np.cumsum(rng.normal(size=n))
+    q = ((q - q.mean()) / q.std() * scale).astype(np.float32)
+    qn, qnorm = norms(q)
+    alpha, gamma = query_constants(n, qn, qnorm)
+    omk = rn(1.0 - KP)
+    for sigma in (0.0, 1e-4, 1e-3, 1e-2, 0.1, 1.0, None):
+        if sigma is None:
+            x = np.cumsum(rng.normal(size=n))
+            x = ((x - x.mean()) / x.std() * scale).astype(np.float32)
+        else:
+            x = (q + rng.normal(0.0, sigma * scale, size=n)).astype(np.float32)
+        xn, xnrm = norms(x)
+        d2 = float(np.sum((q.astype(np.float64) - x.astype(np.float64)) ** 2))
+        U = ru(d2)                                       # the tightest float32 bound of d^2
+        p = q.astype(np.float16).astype(np.float32) * x.astype(np.float16).astype(np.float32)
+        for mode in ("seq", "rz"):
+            c = accumulate(p, mode)
+            E = rd(rd(qn - gamma) - U)                               # __fsub_rd twice
+            r = ru(xnrm * alpha + ru(-xn * omk))                     # __fmaf_ru(xnrm, amax, __fmul_ru(..))
+            assert ru(2.0 * c + r) >= E, (n, scale, sigma, mode)     # __fmaf_ru(2, acc, r) >= E
+            lhs = rn(xnrm * alpha + rn(2.0 * c + rn(-xn * omk)))     # fmaf(xnrm, alpha, fmaf(2, acc, -xn omk))
+            assert lhs >= E, (n, scale, sigma, mode)

@@ -172,3 +172,30 @@ def test_candidate_test_has_no_false_negatives(n, scale):
             assert ru(2.0 * c + r) >= E, (n, scale, sigma, mode)     # __fmaf_ru(2, acc, r) >= E
             lhs = rn(xnrm * alpha + rn(2.0 * c + rn(-xn * omk)))     # fmaf(xnrm, alpha, fmaf(2, acc, -xn omk))
             assert lhs >= E, (n, scale, sigma, mode)
+
+
+@pytest.mark.parametrize("n", [16, 128, 256, 1024, 2048])
+@pytest.mark.parametrize("scale", [1.0, 100.0])
+def test_upper_end_bounds_the_true_distance(n, scale):
+    # the rare path lowers U_q with up = (s + eps) rounded up; the k-th
+    # smallest of these bounds the k-th distance only if every up >= d^2
+    rng = np.random.default_rng(10 * n + int(scale))
+    q = np.cumsum(rng.normal(size=n))
+    q = ((q - q.mean()) / q.std() * scale).astype(np.float32)
+    qn, qnorm = norms(q)
+    alpha, gamma = query_constants(n, qn, qnorm)
+    for sigma in (0.0, 1e-4, 1e-3, 1e-2, 0.1, 1.0, None):
+        if sigma is None:
+            x = np.cumsum(rng.normal(size=n))
+            x = ((x - x.mean()) / x.std() * scale).astype(np.float32)
+        else:
+            x = (q + rng.normal(0.0, sigma * scale, size=n)).astype(np.float32)
+        xn, xnrm = norms(x)
+        d2 = float(np.sum((q.astype(np.float64) - x.astype(np.float64)) ** 2))
+        p = q.astype(np.float16).astype(np.float32) * x.astype(np.float16).astype(np.float32)
+        for mode in ("seq", "pairwise", "rz"):
+            c = accumulate(p, mode)
+            shat = rn(-2.0 * c + rn(xn + qn))                        # fmaf(-2, acc, xn + qn)
+            eps = rn(xnrm * alpha + rn(gamma + rn(KP * xn)))         # fmaf(xnrm, alpha, gamma + kappa' xn)
+            up = max(ru(ru(shat + eps) * float(np.float32(1.0000003))), 0.0)
+            assert up >= d2, (n, scale, sigma, mode, up, d2)

@@ -151,3 +151,32 @@ def test_bench_traffic_gate_follows_the_kernel_source(tmp_path, monkeypatch):
     (csrc / "screen.cu").write_text("// changed\n")
     assert b.profiled_traffic(1000, "k_tc_screen") is None
     assert b.profiled_traffic(1000, "k_lb_scan") is None          # no summary for it here
+
+
+def test_autotune_cache_reuses_a_stored_choice(tmp_path, monkeypatch):
+    # the binding's cache: the first call times the shapes and stores the
+    # choice under (collection shape, batch mode, k, device); the next call
+    # applies it without timing; an unreadable cache counts as empty
+    import types
+
+    import paper_2110_07519_gb300 as m
+
+    calls = {"tune": 0, "set": []}
+    choice = {"batch": 128, "chunk_tiles": 16, "ctas_per_sm": 2, "mode": 0, "ms_per_query": 1.5}
+
+    def fake_tune(index, queries, k=1, stream=None):
+        calls["tune"] += 1
+        return dict(choice)
+
+    monkeypatch.setattr(m, "messi_index_get_info", lambda ix: {"n_series": 1000, "len": 256})
+    monkeypatch.setattr(m, "messi_autotune", fake_tune)
+    monkeypatch.setattr(m, "messi_set_tuning", lambda ix, b, c, s: calls["set"].append((b, c, s)))
+    ix = types.SimpleNamespace(_batch_mode=0)
+    cache = tmp_path / "tune.json"
+    cache.write_text("not json")
+    assert m.autotune_cached(ix, None, k=1, cache=str(cache)) == choice
+    assert calls == {"tune": 1, "set": []}
+    assert m.autotune_cached(ix, None, k=1, cache=str(cache)) == choice
+    assert calls["tune"] == 1 and calls["set"] == [(128, 16, 2)]
+    m.autotune_cached(ix, None, k=10, cache=str(cache))            # another k: timed again
+    assert calls["tune"] == 2

@@ -180,3 +180,30 @@ def test_autotune_cache_reuses_a_stored_choice(tmp_path, monkeypatch):
     assert calls["tune"] == 1 and calls["set"] == [(128, 16, 2)]
     m.autotune_cached(ix, None, k=10, cache=str(cache))            # another k: timed again
     assert calls["tune"] == 2
+
+
+def test_bench_clock_sampler_parses_reasons():
+    # the timed region's clock record: median SM clock, the highest max
+    # clock, and every throttle reason seen active in any sample
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_clk", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def communicate(self, timeout=None):
+            return ("1965, 2070, 1100.5, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "1650, 2070, 1398.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                    "garbage line\n"
+                    "1700, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n", "")
+
+    s = b.ClockSampler.__new__(b.ClockSampler)
+    s.proc = FakeProc()
+    rec = s.stop()
+    assert rec == {"sm_mhz": 1700.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    s.proc = None
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]

@@ -28,7 +28,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "messi_oracle.c")
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# MESSI_ORACLE_LIB names a prebuilt library to load instead (the planted-
+# mistake tests compile mutated copies of the source and load them this way)
+_LIB_PATH = os.environ.get("MESSI_ORACLE_LIB") or os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 ED, DTW = 0, 1
@@ -36,6 +38,8 @@ ED, DTW = 0, 1
 
 def build(force: bool = False) -> str:
     """Compile ``messi_oracle.c`` into ``oracle/liboracle.so`` with gcc."""
+    if os.environ.get("MESSI_ORACLE_LIB"):
+        return _LIB_PATH
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "messi_oracle.h"))
     ):

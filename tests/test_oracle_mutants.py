@@ -1,0 +1,96 @@
+"""Planted mistakes in the oracle must fail its pins.
+
+Each case below is a plausible slip in ``oracle/messi_oracle.c`` -- a wrong
+divisor, a flipped comparison, a dropped term, a swapped operand, an
+off-by-one window, a reversed tie-break.  The test compiles a copy of the
+source with that one change (the committed source is never touched), runs
+``tests/test_oracle_pins.py`` against the mutated library in a subprocess,
+and requires at least one pin to fail."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "messi_oracle.c")
+HDR = os.path.join(ROOT, "oracle", "messi_oracle.h")
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+
+MUTANTS = [
+    ("PAA divides by m + 1",
+     "paa[s] = sum / (double)m;", "paa[s] = sum / (double)(m + 1);"),
+    ("a PAA on a breakpoint takes the lower symbol",
+     "if (beta[j - 1] <= paa[s]) ++count;", "if (beta[j - 1] < paa[s]) ++count;"),
+    ("breakpoints at j / (c + 1)",
+     "std_normal_quantile((double)j / (double)card)", "std_normal_quantile((double)j / (double)(card + 1))"),
+    ("iSAX key takes the symbol bits LSB first",
+     "uint32_t bit = (sym[s] >> (b - 1 - j)) & 1u;", "uint32_t bit = (sym[s] >> j) & 1u;"),
+    ("ED adds instead of subtracting",
+     "double d = (double)q[t] - (double)x[t];", "double d = (double)q[t] + (double)x[t];"),
+    ("ED mindist drops the segment length",
+     "        s += d * d;\n    }\n    return (double)m * s;\n}\n\n/* ----------------------------------------------------------------"
+     " Sec. 3.4 */",
+     "        s += d * d;\n    }\n    return s;\n}\n\n/* ----------------------------------------------------------------"
+     " Sec. 3.4 */"),
+    ("DTW mindist tests the lower envelope against the region floor",
+     "if (paaU[k] < lo) d = lo - paaU[k];", "if (paaL[k] < lo) d = lo - paaL[k];"),
+    ("envelope window one point short on the right",
+     "        int b = i + r > n - 1 ? n - 1 : i + r;\n        double hi = (double)q[a], lo = (double)q[a];",
+     "        int b = i + r - 1 > n - 1 ? n - 1 : i + r - 1;\n        double hi = (double)q[a], lo = (double)q[a];"),
+    ("LB_Keogh with the envelope's sides swapped",
+     "        if (c > U[i]) d = c - U[i];\n        else if (c < L[i]) d = c - L[i];",
+     "        if (c > L[i]) d = c - L[i];\n        else if (c < U[i]) d = c - U[i];"),
+    ("LB_Improved drops its second term",
+     "return first + second;", "return first;"),
+    ("LB_Improved does not clamp the candidate",
+     "h[i] = c > U[i] ? U[i] : (c < L[i] ? L[i] : c);", "h[i] = c;"),
+    ("DTW without the diagonal step",
+     "                if (i > 0 && j > 0 && D[(size_t)(i - 1) * n + j - 1] < best)\n"
+     "                    best = D[(size_t)(i - 1) * n + j - 1];\n",
+     ""),
+    ("DTW window one cell narrow",
+     "        int jhi = i + r > n - 1 ? n - 1 : i + r;",
+     "        int jhi = i + r - 1 > n - 1 ? n - 1 : i + r - 1;\n        if (jhi < jlo) jhi = jlo;"),
+    ("ties go to the larger id",
+     "return da < db || (da == db && ia < ib);", "return da < db || (da == db && ia > ib);"),
+    ("window z-normalisation with the sample variance",
+     "const double var = ss / (double)n;", "const double var = ss / (double)(n - 1);"),
+    ("window mean over n + 1 points",
+     "const double mean = sum / (double)n;", "const double mean = sum / (double)(n + 1);"),
+]
+
+
+@pytest.fixture(scope="module")
+def source():
+    return open(SRC).read()
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(tmp_path, source, name, old, new):
+    assert source.count(old) == 1, f"mutation site not found exactly once: {name}"
+    (tmp_path / "messi_oracle.c").write_text(source.replace(old, new))
+    shutil.copy(HDR, tmp_path / "messi_oracle.h")
+    lib = tmp_path / "liboracle.so"
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                    "-o", str(lib), str(tmp_path / "messi_oracle.c"), "-lm"], check=True)
+    env = dict(os.environ, MESSI_ORACLE_LIB=str(lib), OMP_NUM_THREADS="4")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", PINS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"planted mistake survived every pin: {name}\n{r.stdout[-2000:]}"
+
+
+def test_control_unmutated_copy_passes(tmp_path, source):
+    # the same harness on the unchanged source: every pin passes, so a failure
+    # above comes from the planted mistake and not from the harness
+    (tmp_path / "messi_oracle.c").write_text(source)
+    shutil.copy(HDR, tmp_path / "messi_oracle.h")
+    lib = tmp_path / "liboracle.so"
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                    "-o", str(lib), str(tmp_path / "messi_oracle.c"), "-lm"], check=True)
+    env = dict(os.environ, MESSI_ORACLE_LIB=str(lib), OMP_NUM_THREADS="4")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", PINS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-3000:]
+    assert "passed" in r.stdout

@@ -5,7 +5,9 @@ divisor, a flipped comparison, a dropped term, a swapped operand, an
 off-by-one window, a reversed tie-break.  The test compiles a copy of the
 source with that one change (the committed source is never touched), runs
 ``tests/test_oracle_pins.py`` against the mutated library in a subprocess,
-and requires at least one pin to fail."""
+and requires at least one pin to fail.  The Python side of the oracle (leaf
+grouping, streamed k-NN) gets the same treatment through a copy of the
+package with one line changed."""
 import os
 import shutil
 import subprocess
@@ -92,5 +94,53 @@ def test_control_unmutated_copy_passes(tmp_path, source):
     env = dict(os.environ, MESSI_ORACLE_LIB=str(lib), OMP_NUM_THREADS="4")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", PINS],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-3000:]
+    assert "passed" in r.stdout
+
+
+PY_MUTANTS = [
+    ("leaf split on the bit after the next one",
+     "        while mid < hi and bit(sk[mid], d) == 0:", "        while mid < hi and bit(sk[mid], d + 1) == 0:"),
+    ("a node splits only above twice its capacity",
+     "        if hi - lo <= cap or d >= total:", "        if hi - lo <= 2 * cap or d >= total:"),
+    ("root children by the first w - 1 bits",
+     "        if i == N or prefix(sk[i], w) != prefix(sk[start], w):",
+     "        if i == N or prefix(sk[i], w - 1) != prefix(sk[start], w - 1):"),
+    ("streamed k-NN keeps the first block's answer",
+     "        best = part if best is None else merge_topk([best, part], k)",
+     "        best = part if best is None else best"),
+]
+
+
+def run_pins_on_package_copy(tmp_path, init_text):
+    """Pins of a copy of the repository's oracle package whose __init__.py is
+    `init_text` (the copy compiles its own library); returns the pytest run."""
+    root = tmp_path / "root"
+    (root / "oracle").mkdir(parents=True)
+    (root / "tests").mkdir()
+    (root / "oracle" / "__init__.py").write_text(init_text)
+    for f in ("messi_oracle.c", "messi_oracle.h"):
+        shutil.copy(os.path.join(ROOT, "oracle", f), root / "oracle" / f)
+    for f in ("conftest.py", "test_oracle_pins.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), root / "tests" / f)
+    os.symlink(os.path.join(ROOT, "tests", "golden"), root / "tests" / "golden")
+    os.symlink(os.path.join(ROOT, "synth"), root / "synth")
+    env = dict(os.environ, OMP_NUM_THREADS="4")
+    env.pop("MESSI_ORACLE_LIB", None)
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           str(root / "tests" / "test_oracle_pins.py")],
+                          cwd=str(root), env=env, capture_output=True, text=True, timeout=600)
+
+
+@pytest.mark.parametrize("name,old,new", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pins_catch_planted_python_mistake(tmp_path, name, old, new):
+    init = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    assert init.count(old) == 1, f"mutation site not found exactly once: {name}"
+    r = run_pins_on_package_copy(tmp_path, init.replace(old, new))
+    assert r.returncode != 0, f"planted mistake survived every pin: {name}\n{r.stdout[-2000:]}"
+
+
+def test_control_unmutated_package_copy_passes(tmp_path):
+    r = run_pins_on_package_copy(tmp_path, open(os.path.join(ROOT, "oracle", "__init__.py")).read())
     assert r.returncode == 0, r.stdout[-3000:]
     assert "passed" in r.stdout

@@ -61,6 +61,28 @@ MUTANTS = [
      "const double var = ss / (double)n;", "const double var = ss / (double)(n - 1);"),
     ("window mean over n + 1 points",
      "const double mean = sum / (double)n;", "const double mean = sum / (double)(n + 1);"),
+    ("region upper edge one breakpoint too high",
+     "static double region_hi(int v, int card, const double *beta) { return v == card - 1 ? INFINITY : beta[v]; }",
+     "static double region_hi(int v, int card, const double *beta) { return v >= card - 2 ? INFINITY : beta[v + 1]; }"),
+    ("envelope keeps min and max the wrong way round",
+     "            if ((double)q[j] > hi) hi = (double)q[j];\n            if ((double)q[j] < lo) lo = (double)q[j];",
+     "            if ((double)q[j] < hi) hi = (double)q[j];\n            if ((double)q[j] > lo) lo = (double)q[j];"),
+    ("summaries read every row from the first",
+     "        orc_paa(data + i * (int64_t)n, n, w, paa);", "        orc_paa(data, n, w, paa);"),
+    ("k-NN ignores the id base of a block",
+     "topk_insert(bd + base, bi + base, &bc[(size_t)t * nq + qi], k, d, id_base + row);",
+     "topk_insert(bd + base, bi + base, &bc[(size_t)t * nq + qi], k, d, row);"),
+    ("k-NN drops a full array's last slot on a tie",
+     "    if (*cnt == k && !before(d, id, kd[k - 1], ki[k - 1])) return;",
+     "    if (*cnt == k && !before(d, id, kd[k - 1], ki[k - 1])) return;\n    if (*cnt == k - 1 && k > 1) return;"),
+    ("windows ignore the stride",
+     "        const float *x = series + i * stride;\n        float *o = out + i * (int64_t)n;",
+     "        const float *x = series + i;\n        float *o = out + i * (int64_t)n;"),
+    ("DTW mindist BELOW case against the region floor",
+     "else if (paaL[k] > hi) d = paaL[k] - hi;", "else if (paaL[k] > lo) d = paaL[k] - lo;"),
+    ("iSAX key interleaves segment-major",
+     "            int p = j * w + s;                          /* position from the MSB */",
+     "            int p = s * b + j;                          /* position from the MSB */"),
 ]
 
 

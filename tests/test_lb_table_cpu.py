@@ -73,3 +73,35 @@ def test_table_bound_never_exceeds_the_oracle_mindist(card, w, m):
         lb = word_bound(paa_q, word, beta_lib, m)
         exact = oracle.mindist_ed2(paa_q, word.astype(np.uint8), m, card, beta_orc)
         assert lb <= exact, (card, w, m, trial, lb, exact)
+
+
+def entry_dtw(pu: float, pl: float, v: int, beta: np.ndarray, m: int) -> float:
+    lo = -math.inf if v == 0 else float(beta[v - 1])
+    hi = math.inf if v == beta.size else float(beta[v])
+    d = 0.0
+    if pu < lo:
+        d = gap_rd(lo, pu)             # ABOVE: the upper envelope's PAA below the region
+    elif pl > hi:
+        d = gap_rd(pl, hi)             # BELOW
+    return rd32(Fr(rd64(Fr(rd64(Fr(d) * Fr(d))) * m)))
+
+
+@pytest.mark.parametrize("card,w,m", [(4, 4, 16), (256, 16, 16)])
+def test_dtw_table_bound_never_exceeds_the_oracle_mindist(card, w, m):
+    import paper_2110_07519_gb300 as lib
+
+    beta_lib = lib.messi_breakpoints(card)
+    beta_orc = oracle.breakpoints(card)
+    rng = np.random.default_rng(7 * card + w)
+    for trial in range(300):
+        idx = rng.integers(0, beta_lib.size, size=w)
+        near = beta_lib[idx] + rng.integers(-4, 5, size=w) * np.spacing(np.abs(beta_lib[idx]) + 1e-3)
+        centre = near if trial % 2 else rng.normal(size=w)
+        half = np.abs(rng.normal(size=w)) * (0.0 if trial % 3 == 0 else 0.3)
+        pu, pl = centre + half, centre - half            # envelope PAAs, upper >= lower
+        word = rng.integers(0, card, size=w)
+        lb = 0.0
+        for s in range(w):
+            lb = rd32(Fr(lb) + Fr(entry_dtw(float(pu[s]), float(pl[s]), int(word[s]), beta_lib, m)))
+        exact = oracle.mindist_dtw2(pu, pl, word.astype(np.uint8), m, card, beta_orc)
+        assert lb <= exact, (card, w, m, trial, lb, exact)

@@ -1,0 +1,83 @@
+"""The blocked LB_Improved of the DTW filter, modelled on the CPU.
+
+When the window reach equals the kernel's template reach, the second
+LB_Improved term takes each point's envelope of h (the candidate clamped into
+the query's envelope) from blocks of W = 2R + 1 points: a prefix max/min over
+the current block and a suffix max/min over the previous one, read R points
+behind the newest.  This restates that walk step by step (float32 values,
+sums rounded toward -inf) and checks that (a) every envelope it forms equals
+the window max/min of h taken directly, clipped at the ends, and (b) the
+bound never exceeds the oracle's FP64 LB_Improved."""
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+import oracle
+
+
+def rd32(fr: Fr) -> float:
+    f = float(np.float32(float(fr)))
+    if Fr(f) > fr:
+        f = float(np.nextafter(np.float32(f), np.float32(-np.inf)))
+    return f
+
+
+def blocked_model(q, U, L, x, R):
+    n, W = q.size, 2 * R + 1
+    hlast = float(min(max(x[0], L[0]), U[0]))
+    smx, smn = [hlast] * W, [hlast] * W
+    acc1 = acc2 = 0.0
+    env = {}
+    for j0 in range(0, n + R, W):
+        pmx = pmn = 0.0
+        for k in range(W):
+            j = j0 + k
+            h = hlast
+            if j < n:
+                c, u, l = float(x[j]), float(U[j]), float(L[j])
+                d = 0.0
+                if c > u:
+                    d = rd32(Fr(c) - Fr(u))
+                elif c < l:
+                    d = rd32(Fr(l) - Fr(c))
+                acc1 = rd32(Fr(acc1) + Fr(rd32(Fr(d) * Fr(d))))
+                h = min(max(c, l), u)
+                hlast = h
+            pmx = h if k == 0 else max(pmx, h)
+            pmn = h if k == 0 else min(pmn, h)
+            mx = max(smx[k + 1], pmx) if k + 1 < W else pmx
+            mn = min(smn[k + 1], pmn) if k + 1 < W else pmn
+            smx[k] = h
+            smn[k] = h
+            p = j - R
+            if 0 <= p < n:
+                env[p] = (mx, mn)
+                qv = float(q[p])
+                d = 0.0
+                if qv > mx:
+                    d = rd32(Fr(qv) - Fr(mx))
+                elif qv < mn:
+                    d = rd32(Fr(mn) - Fr(qv))
+                acc2 = rd32(Fr(acc2) + Fr(rd32(Fr(d) * Fr(d))))
+        for k in range(W - 2, -1, -1):
+            smx[k] = max(smx[k], smx[k + 1])
+            smn[k] = min(smn[k], smn[k + 1])
+    return rd32(Fr(acc1) + Fr(acc2)), env
+
+
+@pytest.mark.parametrize("n,R", [(16, 1), (16, 4), (33, 2), (100, 6), (128, 12), (256, 25), (40, 13)])
+def test_blocked_envelopes_and_bound(n, R):
+    rng = np.random.default_rng(n * 31 + R)
+    for trial in range(20):
+        q = np.cumsum(rng.normal(size=n)).astype(np.float32)
+        x = (q + rng.normal(0.0, 0.5 + trial % 3, size=n)).astype(np.float32) if trial % 2 else \
+            np.cumsum(rng.normal(size=n)).astype(np.float32)
+        U64, L64 = oracle.envelope(q, R)
+        U, L = U64.astype(np.float32), L64.astype(np.float32)        # max/min of floats: exact
+        lb, env = blocked_model(q, U, L, x, R)
+        h = np.minimum(np.maximum(x, L), U)
+        for p in range(n):
+            lo, hi = max(0, p - R), min(n - 1, p + R)
+            assert env[p] == (float(h[lo:hi + 1].max()), float(h[lo:hi + 1].min())), (n, R, trial, p)
+        assert lb <= oracle.lb_improved2(q, x, R), (n, R, trial)

@@ -1,10 +1,11 @@
-"""The blocked LB_Improved of the DTW filter, modelled on the CPU.
+"""The LB_Improved walks of the DTW filter, modelled on the CPU.
 
 When the window reach equals the kernel's template reach, the second
 LB_Improved term takes each point's envelope of h (the candidate clamped into
 the query's envelope) from blocks of W = 2R + 1 points: a prefix max/min over
 the current block and a suffix max/min over the previous one, read R points
-behind the newest.  This restates that walk step by step (float32 values,
+behind the newest; below it, the register-window walk reads the newest 2r + 1
+of 2R + 1 slots.  This restates both walks step by step (float32 values,
 sums rounded toward -inf) and checks that (a) every envelope it forms equals
 the window max/min of h taken directly, clipped at the ends, and (b) the
 bound never exceeds the oracle's FP64 LB_Improved."""
@@ -81,3 +82,55 @@ def test_blocked_envelopes_and_bound(n, R):
             lo, hi = max(0, p - R), min(n - 1, p + R)
             assert env[p] == (float(h[lo:hi + 1].max()), float(h[lo:hi + 1].min())), (n, R, trial, p)
         assert lb <= oracle.lb_improved2(q, x, R), (n, R, trial)
+
+
+def thread_model(q, U, L, x, R, r):
+    """The register-window variant (template reach R, window r <= R)."""
+    n, W = q.size, 2 * R + 1
+    h0 = float(min(max(x[0], L[0]), U[0]))
+    hw = [h0] * W
+    lo_b = 2 * (R - r)
+    acc1 = acc2 = 0.0
+    env = {}
+    for i in range(n + r):
+        h = hw[W - 1]
+        if i < n:
+            c, u, l = float(x[i]), float(U[i]), float(L[i])
+            d = 0.0
+            if c > u:
+                d = rd32(Fr(c) - Fr(u))
+            elif c < l:
+                d = rd32(Fr(l) - Fr(c))
+            acc1 = rd32(Fr(acc1) + Fr(rd32(Fr(d) * Fr(d))))
+            h = min(max(c, l), u)
+        hw = hw[1:] + [h]
+        p = i - r
+        if p >= 0:
+            vals = [hw[b] if b >= lo_b else h for b in range(W - 1)] + [h]
+            mx, mn = max(vals), min(vals)
+            env[p] = (mx, mn)
+            qv = float(q[p])
+            d = 0.0
+            if qv > mx:
+                d = rd32(Fr(qv) - Fr(mx))
+            elif qv < mn:
+                d = rd32(Fr(mn) - Fr(qv))
+            acc2 = rd32(Fr(acc2) + Fr(rd32(Fr(d) * Fr(d))))
+    return rd32(Fr(acc1) + Fr(acc2)), env
+
+
+@pytest.mark.parametrize("n,R,r", [(16, 4, 1), (33, 4, 3), (100, 8, 6), (128, 16, 12), (256, 32, 25), (40, 6, 6)])
+def test_register_window_envelopes_and_bound(n, R, r):
+    rng = np.random.default_rng(n * 17 + R + r)
+    for trial in range(20):
+        q = np.cumsum(rng.normal(size=n)).astype(np.float32)
+        x = (q + rng.normal(0.0, 0.5 + trial % 3, size=n)).astype(np.float32) if trial % 2 else \
+            np.cumsum(rng.normal(size=n)).astype(np.float32)
+        U64, L64 = oracle.envelope(q, r)
+        U, L = U64.astype(np.float32), L64.astype(np.float32)
+        lb, env = thread_model(q, U, L, x, R, r)
+        h = np.minimum(np.maximum(x, L), U)
+        for p in range(n):
+            lo, hi = max(0, p - r), min(n - 1, p + r)
+            assert env[p] == (float(h[lo:hi + 1].max()), float(h[lo:hi + 1].min())), (n, R, r, trial, p)
+        assert lb <= oracle.lb_improved2(q, x, r), (n, R, r, trial)

@@ -1318,7 +1318,7 @@ __device__ void fin_streamed(const IndexView &iv, const QueryParams &qp, const Q
                              unsigned nlog, unsigned long long *cand, double *d64, unsigned long long *rp, double *rd,
                              long long *ids, float *dists)
 {
-    __shared__ unsigned ncw, rc;
+    __shared__ unsigned ncw, rc, wk;
     __shared__ unsigned long long seen;
     const int tid = threadIdx.x;
     const unsigned k = (unsigned)qp.k;
@@ -1347,8 +1347,21 @@ __device__ void fin_streamed(const IndexView &iv, const QueryParams &qp, const Q
         }
         __syncthreads();
         fin_sort64(cand, d64, npow);
-        // the window's best k, then the running top-k, ranked together
-        const unsigned m = min(k, c), r0 = rc, tot = m + r0;
+        // the window's best k distinct rows (a row logged twice sorts next to
+        // itself: compare with the last one kept), moved to the front in place
+        if (tid == 0) {
+            unsigned out = 0;
+            for (unsigned i = 0; i < c && out < k; ++i) {
+                if (out > 0 && cand[i] == cand[out - 1]) continue;
+                cand[out] = cand[i];
+                d64[out] = d64[i];
+                ++out;
+            }
+            wk = out;
+        }
+        __syncthreads();
+        // then the running top-k, ranked together with them
+        const unsigned m = wk, r0 = rc, tot = m + r0;
         for (unsigned i = tid; i < r0; i += blockDim.x) {
             cand[m + i] = rp[i];
             d64[m + i] = rd[i];

@@ -195,23 +195,28 @@ messi_status messi_query_batched(const messi_index *ix, const float *queries, ui
 messi_status messi_lower_bounds(const messi_index *ix, const float *query, messi_dist dist,
                                 uint32_t window, float *lb2, messi_stream stream);
 
-/* Lower bounds like messi_lower_bounds, for callers that cannot allocate
- * device memory while they run: code inside a CUDA stream capture (where
- * allocation calls are not allowed), a real-time loop that must not block in
- * the allocator, or an embedding that gives the library only a fixed budget.
- * The paper has no counterpart; this is an interface of this library.
+/* Lower bounds like messi_lower_bounds, for callers that may not allocate
+ * device memory while they run: an embedding that owns a fixed device-memory
+ * budget and gives the library only its input and output buffers, or a
+ * latency-critical loop that must not stall in cudaMalloc / cudaFree (which
+ * can synchronise the device).  The paper has no counterpart; this is an
+ * interface of this library.
  *
  * Allocates nothing: query and lb2 must be device pointers (EINVAL for host
- * buffers, which would need staging memory); the scratch -- query state,
- * lower-bound table, query and envelope rows -- lives in one fixed array of
- * 41,216 bytes that every GPU loading the library holds until the process
- * exits.  That array bounds the series length: an index with len > 2048 is
- * rejected with EINVAL (use messi_lower_bounds).  Every call shares the
- * array, so calls whose work overlaps on the GPU (on different streams, or
- * from several threads) race and must be serialised by the caller; each call
- * clears the query state it needs before use.  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress) and should come
- * before any stream capture.  Results equal messi_lower_bounds bit for bit. */
+ * buffers, which would need staging memory) on the device the index was
+ * built on, and that device must be current (EINVAL otherwise).  The scratch
+ * -- query state, lower-bound table, query and envelope rows -- lives in one
+ * fixed array of 41,216 bytes that every GPU loading the library holds until
+ * the process exits.  That array bounds the series length: an index with
+ * len > 2048 is rejected with EINVAL (use messi_lower_bounds).  Every call
+ * shares the array, so calls whose work overlaps on the GPU (on different
+ * streams, or from several threads) race and must be serialised by the
+ * caller; each call clears the query state it needs before use.  The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  A query
+ * holding a non-finite value leaves lb2 unwritten (its previous contents
+ * stay) and messi_check() then reports MESSI_EINVAL.  Results equal
+ * messi_lower_bounds bit for bit. */
 messi_status messi_lower_bounds_noalloc(const messi_index *ix, const float *query, messi_dist dist,
                                         uint32_t window, float *lb2, messi_stream stream);
 
@@ -258,8 +263,24 @@ messi_status messi_set_tuning(messi_index *ix, const messi_tuning *t);
 messi_status messi_debug_tc_gemm(const uint16_t *a_tile, const uint16_t *b_tile, uint32_t k, uint32_t n,
                                  uint32_t lbo, uint32_t sbo, float *d);
 
-/* Profiling mode: record CUDA events around every scan launch and every
- * query, reported by messi_query_stats.  Off by default. */
+/* Test hook for the failure path of the k > 1 result array (no counterpart
+ * in the paper).  The array of the k best is updated under a lock taken with
+ * a bounded spin; a thread that gives up after spin_limit tries drops its
+ * candidate and sets the timeout bit of the index's status word, which the
+ * next messi_check() reports as MESSI_ETIMEOUT (the answer of that call is
+ * then not exact).  With hold_lock != 0 every query of messi_query starts
+ * with that lock held, so its first k > 1 insertion gives up.  Defaults:
+ * spin_limit 4,194,304, hold_lock 0 (restore them with those values).  No
+ * wait of the kernels on memory copies is affected. */
+messi_status messi_debug_set_lock_fault(messi_index *ix, uint32_t spin_limit, int hold_lock);
+
+/* Profiling level, reported by messi_query_stats.  0 (default): off.
+ * 1: CUDA events around every lower-bound scan group (per-query path), every
+ * screen launch (screened batch) and every fused launch (lower-bound batch
+ * form) -- scan_ms / scan_launches.  2: also around every query (per-query
+ * path) or batch (batched forms) -- query_ms_p50 / p99.  Events are recorded
+ * on the call's stream.  Any level above 0 turns off the graph replay of the
+ * lower-bound batch form.  EINVAL for other levels. */
 messi_status messi_set_profiling(messi_index *ix, int enable);
 
 /* Synchronise `stream` and report (then clear) the device status word. */
@@ -289,7 +310,8 @@ messi_status messi_breakpoints(uint32_t cardinality, double *out);
  * another and has no counterpart).  Requests enter an arrival queue; worker
  * threads, one per CUDA stream, admit them into device batches in arrival
  * order while the device memory charged to unfinished requests stays within
- * mem_budget, run each batch (ED: messi_query_batched kernels; DTW: the
+ * mem_budget (a request is admitted beyond it only when nothing else is in
+ * flight), run each batch (ED: messi_query_batched kernels; DTW: the
  * per-query kernels) with k = the largest k of the batch, and give every
  * request the first k of its row.  Batches on different streams overlap on
  * the device.  A request's result does not depend on what else is in flight:
@@ -309,7 +331,9 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, rejected, batches, inflight_peak;
     double p50_ms, p99_ms, mean_ms;   /* submit-to-result latency of completed requests */
-    uint64_t reserved[4];
+    uint64_t budget_waits;            /* times a worker found queued requests but had to
+                                         wait for admitted ones to free their memory */
+    uint64_t reserved[3];
 } messi_server_stats;
 
 /* Start a server on `ix` (which must outlive it); cfg may be NULL.  Builds
@@ -333,6 +357,12 @@ messi_status messi_server_poll(messi_server *srv, uint64_t ticket, int64_t *ids,
  * rejected, batches run, the largest number in flight, and submit-to-result
  * latency percentiles (ms) over completed requests. */
 messi_status messi_server_get_stats(messi_server *srv, messi_server_stats *out);
+
+/* Hold (paused != 0) or resume admission.  While held, workers finish the
+ * batches they have but admit nothing new; submit keeps queueing (up to
+ * max_queued).  For draining a server before the index changes, and for
+ * bringing the queue to a known state. */
+messi_status messi_server_pause(messi_server *srv, int paused);
 
 /* Stop the workers after the queued requests and release everything. */
 void messi_server_destroy(messi_server *srv);

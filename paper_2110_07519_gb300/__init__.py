@@ -76,7 +76,7 @@ class MessiServerConfig(ctypes.Structure):
 class MessiServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "rejected", "batches", "inflight_peak")] + [
         ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
-        ("reserved", ctypes.c_uint64 * 4)]
+        ("budget_waits", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 3)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
@@ -105,7 +105,9 @@ _SIGS = {
     "messi_server_submit": [_P, _P, _U32, _I, _U32, ctypes.POINTER(_U64)],
     "messi_server_poll": [_P, _U64, _P, _P, ctypes.POINTER(ctypes.c_double), _U64],
     "messi_server_get_stats": [_P, ctypes.POINTER(MessiServerStats)],
+    "messi_server_pause": [_P, _I],
     "messi_server_destroy": [_P],
+    "messi_debug_set_lock_fault": [_P, _U32, _I],
     "messi_last_error": [],
 }
 for _name, _args in _SIGS.items():
@@ -343,8 +345,11 @@ def messi_query_stats(index: Index) -> dict:
     return st.as_dict()
 
 
-def messi_set_profiling(index: Index, enable: bool = True):
-    _check(_lib.messi_set_profiling(index.handle, 1 if enable else 0), "messi_set_profiling")
+def messi_set_profiling(index: Index, level=2):
+    """0 off; 1 events around the dominant kernel launches; 2 also per query
+    (True means 2, False 0)."""
+    level = 2 if level is True else 0 if level is False else int(level)
+    _check(_lib.messi_set_profiling(index.handle, level), "messi_set_profiling")
 
 
 def messi_set_batch_mode(index: Index, mode: int):
@@ -413,6 +418,13 @@ def messi_debug_tc_gemm(a_tile: np.ndarray, b_tile: np.ndarray, k: int, n: int, 
     return d
 
 
+def messi_debug_set_lock_fault(index: Index, spin_limit: int = 1 << 22, hold_lock: bool = False):
+    """Test hook: tries of the k-array lock before a timeout, and whether every
+    per-query call starts with that lock held (defaults restore normal use)."""
+    _check(_lib.messi_debug_set_lock_fault(index.handle, spin_limit, 1 if hold_lock else 0),
+           "messi_debug_set_lock_fault")
+
+
 def messi_check(index: Index, stream=None):
     _check(_lib.messi_check(index.handle, _stream(stream)), "messi_check")
 
@@ -475,6 +487,10 @@ def messi_server_get_stats(server: Server) -> dict:
     out = MessiServerStats()
     _check(_lib.messi_server_get_stats(server.handle, ctypes.byref(out)), "messi_server_get_stats")
     return out.as_dict()
+
+
+def messi_server_pause(server: Server, paused: bool = True):
+    _check(_lib.messi_server_pause(server.handle, 1 if paused else 0), "messi_server_pause")
 
 
 def messi_server_destroy(server: Server):

@@ -17,16 +17,6 @@ thread_local std::string g_last_error;
 
 bool is_pow2(unsigned v) { return v && !(v & (v - 1)); }
 
-bool is_device_ptr(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 std::mutex g_attr_mu;
 std::vector<int> g_attr_done;
 
@@ -272,28 +262,6 @@ messi_status ensure_tc_workspace(messi_index *ix, Workspace *ws, unsigned B)
     return MESSI_OK;
 }
 
-IndexView view_of(const messi_index *ix)
-{
-    IndexView v;
-    v.raw = ix->raw;
-    v.sax = ix->sax;
-    v.ids = ix->ids;
-    v.pos_of_id = ix->pos_of_id;
-    v.leaf_off = ix->leaf_off;
-    v.leaf_key = ix->leaf_key;
-    v.leaf_box = ix->leaf_box;
-    v.beta64 = ix->beta64;
-    v.N = ix->N;
-    v.L = ix->L;
-    v.len = ix->len;
-    v.w = ix->w;
-    v.card = ix->card;
-    v.bits = ix->bits;
-    v.m = ix->m;
-    v.status = ix->status;
-    return v;
-}
-
 cudaEvent_t pool_event(Workspace *ws, size_t i)
 {
     while (ws->ev_pool.size() <= i) {
@@ -319,6 +287,70 @@ messi_status check_sizes(uint64_t n, uint32_t len, uint32_t segments, uint32_t c
 }
 
 }  // namespace
+
+IndexView view_of(const messi_index *ix)
+{
+    IndexView v;
+    v.raw = ix->raw;
+    v.sax = ix->sax;
+    v.ids = ix->ids;
+    v.pos_of_id = ix->pos_of_id;
+    v.leaf_off = ix->leaf_off;
+    v.leaf_key = ix->leaf_key;
+    v.leaf_box = ix->leaf_box;
+    v.beta64 = ix->beta64;
+    v.N = ix->N;
+    v.L = ix->L;
+    v.len = ix->len;
+    v.w = ix->w;
+    v.card = ix->card;
+    v.bits = ix->bits;
+    v.m = ix->m;
+    v.status = ix->status;
+    return v;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+messi_status check_device(const messi_index *ix, const void *const *ptrs, int n, const char *where)
+{
+    int dev = 0;
+    if (!cuda_ok(cudaGetDevice(&dev), where)) return MESSI_ECUDA;
+    if (dev != ix->device)
+        return fail(MESSI_EINVAL, std::string(where) + ": the index lives on device " + std::to_string(ix->device) +
+                                      " but device " + std::to_string(dev) + " is current");
+    for (int i = 0; i < n; ++i) {
+        if (!ptrs[i]) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, ptrs[i]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;   // not CUDA memory: a host pointer
+        }
+        if (a.type == cudaMemoryTypeDevice && a.device != dev)
+            return fail(MESSI_EINVAL, std::string(where) + ": a buffer lives on device " + std::to_string(a.device) +
+                                          ", not on the index's device " + std::to_string(dev));
+    }
+    return MESSI_OK;
+}
+
+QueryParams make_params(const messi_index *ix, uint32_t k, int dist, uint32_t window)
+{
+    QueryParams qp;
+    qp.k = (int)k;
+    qp.dist = dist;
+    qp.r = dist == MESSI_DTW ? (int)window : 0;
+    qp.F = band_factor(dist, ix->len);
+    qp.lock_spin = ix->lock_spin;
+    return qp;
+}
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -465,6 +497,18 @@ messi_status messi_build(const float *series, uint64_t n, uint32_t len, uint32_t
     const unsigned cap = (cfg && cfg->leaf_capacity) ? cfg->leaf_capacity : 2000u;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ensure_attributes();
+    {
+        // what the finished index holds at least (rows in leaf order, words,
+        // ids both ways), plus the staging copy of host series: more than the
+        // device has free is refused before anything is allocated or read
+        const bool host_series = !is_device_ptr(series);
+        const double need = (double)n * len * 4.0 * (host_series ? 2.0 : 1.0) + (double)n * 24.0;
+        size_t free_b = 0, total_b = 0;
+        if (!cuda_ok(cudaMemGetInfo(&free_b, &total_b), "messi_build: cudaMemGetInfo")) return MESSI_ECUDA;
+        if (need > (double)free_b)
+            return fail(MESSI_ENOMEM, "messi_build: the index needs at least " + std::to_string((long long)(need / 1e6)) +
+                                          " MB of device memory, " + std::to_string(free_b / 1000000) + " MB are free");
+    }
 
     messi_index *ix = new messi_index();
     cudaGetDevice(&ix->device);
@@ -581,7 +625,8 @@ static messi_status query_args(const messi_index *ix, const float *queries, uint
     if (k == 0 || k > (uint32_t)kMaxK || k > ix->N) return fail(MESSI_EINVAL, "messi_query: k must be in [1, min(n, 1024)]");
     if (dist != MESSI_ED && dist != MESSI_DTW) return fail(MESSI_EINVAL, "messi_query: unknown distance");
     if (dist == MESSI_DTW && window >= (uint32_t)ix->len) return fail(MESSI_EINVAL, "messi_query: window must be < len");
-    return MESSI_OK;
+    const void *ptrs[3] = {queries, ids, dists};
+    return check_device(ix, ptrs, 3, "messi_query");
 }
 
 messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uint32_t nq, uint32_t k,
@@ -611,11 +656,7 @@ messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uin
     if (hd) { ddist = reinterpret_cast<float *>(stage + so); so += align256(dbytes); }
 
     const IndexView iv = view_of(ix);
-    QueryParams qp;
-    qp.k = (int)k;
-    qp.dist = (int)dist;
-    qp.r = dist == MESSI_DTW ? (int)window : 0;
-    qp.F = band_factor(qp.dist, ix->len);
+    const QueryParams qp = make_params(ix, k, (int)dist, window);
     const QuerySlot slot = ws->slot;
     MESSI_CUDA(cudaMemsetAsync(slot.acc, 0, sizeof(QueryCounters), s));
     const unsigned long long launches0 = ws->launches;
@@ -624,11 +665,13 @@ messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uin
     size_t evn = 0;
     for (uint32_t qi = 0; qi < nq; ++qi) {
         int eq0 = -1, es0 = -1;
-        if (ix->profiling) {
+        if (ix->profiling >= 2) {
             eq0 = (int)evn;
             cudaEventRecord(pool_event(ws, evn++), s);
         }
         launch_prep(iv, qp, slot, dq + (size_t)qi * ix->len, s);
+        if (ix->hold_lock)   // test hook: the k-array lock starts out held
+            MESSI_CUDA(cudaMemsetAsync(&slot.st->lock, 0xff, sizeof(unsigned), s));
         launch_seed(iv, qp, slot, s, &ws->launches);
         if (ix->profiling) {
             es0 = (int)evn;
@@ -642,7 +685,7 @@ messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uin
         launch_refine(iv, qp, slot, s, &ws->launches);
         launch_finalize(iv, qp, slot, did + (size_t)qi * k, ddist + (size_t)qi * k, s);
         ws->launches += 3;
-        if (ix->profiling) {
+        if (ix->profiling >= 2) {
             cudaEventRecord(pool_event(ws, evn++), s);
             ws->query_ev.push_back({eq0, (int)evn - 1});
         }
@@ -790,11 +833,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
     if (hd) { ddist = reinterpret_cast<float *>(stage + so); so += align256(dbytes); }
 
     const IndexView iv = view_of(ix);
-    QueryParams qp;
-    qp.k = (int)k;
-    qp.dist = 0;
-    qp.r = 0;
-    qp.F = band_factor(0, ix->len);
+    const QueryParams qp = make_params(ix, k, MESSI_ED, 0);
     MESSI_CUDA(cudaMemsetAsync(ws->bacc, 0, sizeof(QueryCounters), s));
     const unsigned long long launches0 = ws->launches;
     ws->scan_ev.clear();
@@ -809,7 +848,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
     for (uint32_t g = 0; g < nq && use_tc; g += B) {
         const unsigned nb = std::min<unsigned>(B, nq - g);
         int eq0 = -1, es0 = -1;
-        if (ix->profiling) {
+        if (ix->profiling >= 2) {
             eq0 = (int)evn;
             cudaEventRecord(pool_event(ws, evn++), s);
         }
@@ -864,7 +903,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
                 if ((chk = answer_one(ix, ws, iv, qp, dq + (size_t)(g + b) * ix->len, did + (size_t)(g + b) * k,
                                       ddist + (size_t)(g + b) * k, s)) != MESSI_OK)
                     return chk;
-        if (ix->profiling) {
+        if (ix->profiling >= 2) {
             cudaEventRecord(pool_event(ws, evn++), s);
             for (unsigned r = 0; r < nb; ++r) ws->query_ev.push_back({eq0, (int)evn - 1});
         }
@@ -881,8 +920,10 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
         int eq0 = -1, es0 = -1;
         cudaEvent_t f0 = nullptr, f1 = nullptr;
         if (ix->profiling) {
-            eq0 = (int)evn;
-            cudaEventRecord(pool_event(ws, evn++), s);
+            if (ix->profiling >= 2) {
+                eq0 = (int)evn;
+                cudaEventRecord(pool_event(ws, evn++), s);
+            }
             es0 = (int)evn;
             f0 = pool_event(ws, evn++);
             f1 = pool_event(ws, evn++);
@@ -890,8 +931,8 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
         launch_batch(iv, qp, ws->bslots_dev, nb, dq + (size_t)g * ix->len, did + (size_t)g * k, ddist + (size_t)g * k,
                      ws->redo_dev + g, ix->tune_chunk_tiles, ix->tune_ctas_per_sm, ws->bcounter, s, &ws->launches,
                      f0, f1);
-        if (ix->profiling) {
-            ws->scan_ev.push_back({es0, es0 + 1});
+        if (ix->profiling) ws->scan_ev.push_back({es0, es0 + 1});
+        if (ix->profiling >= 2) {
             cudaEventRecord(pool_event(ws, evn++), s);
             for (unsigned r = 0; r < nb; ++r) ws->query_ev.push_back({eq0, (int)evn - 1});
         }
@@ -1042,8 +1083,8 @@ messi_status messi_autotune(messi_index *ix, const float *queries, uint32_t nq, 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const bool prof = ix->profiling;
-    ix->profiling = false;
+    const int prof = ix->profiling;
+    ix->profiling = 0;
     double best = 1e300;
     Shape pick = cand.front();
     messi_status st = MESSI_OK;
@@ -1090,10 +1131,19 @@ messi_status messi_autotune(messi_index *ix, const float *queries, uint32_t nq, 
     return MESSI_OK;
 }
 
+messi_status messi_debug_set_lock_fault(messi_index *ix, uint32_t spin_limit, int hold_lock)
+{
+    if (!ix) return fail(MESSI_EINVAL, "messi_debug_set_lock_fault: null index");
+    ix->lock_spin = spin_limit;
+    ix->hold_lock = hold_lock != 0;
+    return MESSI_OK;
+}
+
 messi_status messi_set_profiling(messi_index *ix, int enable)
 {
     if (!ix) return fail(MESSI_EINVAL, "messi_set_profiling: null index");
-    ix->profiling = enable != 0;
+    if (enable < 0 || enable > 2) return fail(MESSI_EINVAL, "messi_set_profiling: level 0, 1 or 2");
+    ix->profiling = enable;
     return MESSI_OK;
 }
 
@@ -1117,10 +1167,13 @@ messi_status messi_lower_bounds(const messi_index *cix, const float *query, mess
     if (dist != MESSI_ED && dist != MESSI_DTW) return fail(MESSI_EINVAL, "messi_lower_bounds: unknown distance");
     if (dist == MESSI_DTW && window >= (uint32_t)cix->len) return fail(MESSI_EINVAL, "messi_lower_bounds: window must be < len");
     messi_index *ix = const_cast<messi_index *>(cix);
+    const void *ptrs[2] = {query, lb2};
+    messi_status chk = check_device(ix, ptrs, 2, "messi_lower_bounds");
+    if (chk != MESSI_OK) return chk;
     Workspace *ws = &ix->ws;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ensure_attributes();
-    messi_status chk = ensure_workspace(ix, ws);
+    chk = ensure_workspace(ix, ws);
     if (chk != MESSI_OK) return chk;
     const bool hq = !is_device_ptr(query), ho = !is_device_ptr(lb2);
     const size_t qbytes = (size_t)ix->len * 4, obytes = (size_t)ix->N * 4;
@@ -1135,7 +1188,7 @@ messi_status messi_lower_bounds(const messi_index *cix, const float *query, mess
     }
     if (ho) dout = reinterpret_cast<float *>(stage + align256(qbytes));
     const IndexView iv = view_of(ix);
-    QueryParams qp{1, (int)dist, dist == MESSI_DTW ? (int)window : 0, band_factor((int)dist, ix->len)};
+    const QueryParams qp = make_params(ix, 1, (int)dist, window);
     launch_prep(iv, qp, ws->slot, dq, s);
     launch_lower_bounds(iv, ws->slot, dout, s);
     ix->launches += 2;

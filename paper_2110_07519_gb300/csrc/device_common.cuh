@@ -381,7 +381,9 @@ __device__ __forceinline__ float order_floor(unsigned b) { return __uint_as_floa
 // query's best-so-far.  Candidates within the near-tie band of the current
 // k-th best are logged for the final FP64 resolution.  k = 1 keeps the best
 // as a packed 64-bit atomicMin; k > 1 inserts into a sorted k-array under a
-// lock with a bounded spin.  Offering the same row twice changes nothing
+// lock with a bounded spin (qp.lock_spin tries; a waiter that runs out sets
+// the timeout bit of the status word and drops the candidate, so the query
+// reports MESSI_ETIMEOUT).  Offering the same row twice changes nothing
 // (its packed value is already in the array or no longer qualifies); the
 // log may then hold it twice, which the final step removes.
 static __device__ __noinline__ void offer(const QueryParams &qp, const QuerySlot &slot, unsigned *status, float d2,
@@ -406,7 +408,7 @@ static __device__ __noinline__ void offer(const QueryParams &qp, const QuerySlot
     unsigned spins = 0, nap = 32;
     while (atomicCAS(&st->lock, 0u, 1u) != 0u) {
         if (P >= ld_volatile_u64(&st->thr)) return;
-        if (++spins > kSpinLimit) {
+        if (++spins > qp.lock_spin) {
             atomicOr(status, kStTimeout);
             return;
         }

@@ -114,6 +114,7 @@ struct QueryParams {
     int dist;                   // 0 ED, 1 DTW
     int r;                      // DTW window
     float F;                    // near-tie band factor (>= (1+gamma)^2)
+    unsigned lock_spin;         // tries of the k-array lock before a timeout (kSpinLimit)
 };
 
 }  // namespace messi
@@ -215,11 +216,15 @@ struct messi_index {
     // bookkeeping
     std::atomic<size_t> device_bytes{0};   // workspaces of server workers grow it concurrently
     double build_ms = 0.0;
-    bool profiling = false;
+    int profiling = 0;                  // 1: events around the scan / screen launches; 2: and every query
     unsigned long long launches = 0;
     // tuned shapes of the batched path
     unsigned tune_batch = 64, tune_chunk_tiles = 32, tune_ctas_per_sm = 2;
     int batch_mode = 1;                 // 0: lower bound + FP32 refine, 1: tensor-core screen
+    // test hook (messi_debug_set_lock_fault): tries of the k-array lock, and
+    // whether the per-query path starts every query with that lock held
+    unsigned lock_spin = messi::kSpinLimit;
+    bool hold_lock = false;
     // tensor-core screen: f16 tile copy of the rows and their norms
     __half *screen16 = nullptr;
     float *xn = nullptr, *xnorm = nullptr;
@@ -239,6 +244,16 @@ bool cuda_ok(cudaError_t e, const char *what);
 
 int num_sms();
 void compute_breakpoints(int card, double *beta);
+// device or managed memory (false for host memory and unknown pointers)
+bool is_device_ptr(const void *p);
+// EINVAL unless the current device is the one the index lives on, and every
+// non-null device pointer in ptrs (host pointers are skipped) is memory of
+// that device (managed memory is accepted on any device)
+messi_status check_device(const messi_index *ix, const void *const *ptrs, int n, const char *where);
+IndexView view_of(const messi_index *ix);
+// query parameters of one call: k, distance, window, near-tie band and the
+// index's k-array lock spin limit
+QueryParams make_params(const messi_index *ix, uint32_t k, int dist, uint32_t window);
 
 // ------------------------------------------------------------- launchers
 // summarize.cu

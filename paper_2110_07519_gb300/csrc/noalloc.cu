@@ -1,15 +1,15 @@
 // noalloc.cu -- messi_lower_bounds_noalloc: the per-series lower bounds of
 // one query against an existing index, computed without allocating memory.
 //
-// Who needs it: code that must not call cudaMalloc while it runs -- a
-// stream-capture region (allocation calls are illegal during capture), a
-// real-time loop that may not block on the allocator, or an embedding that
-// owns a fixed device-memory budget and hands the library only its input and
-// output buffers.  messi_lower_bounds() keeps its scratch (query state, the
-// lower-bound table, the query and its envelope) in a workspace it allocates
-// on first use; this entry point keeps the same scratch in the fixed-size
-// file-scope array below instead, which every GPU that loads the library
-// holds until the process exits.
+// Who needs it: callers that may not call cudaMalloc while they run -- an
+// embedding that owns a fixed device-memory budget and hands the library
+// only its input and output buffers, or a latency-critical loop that must
+// not stall in the allocator (cudaMalloc and cudaFree can synchronise the
+// device and wait for other streams' work).  messi_lower_bounds() keeps its
+// scratch (query state, the lower-bound table, the query and its envelope)
+// in a workspace it allocates on first use; this entry point keeps the same
+// scratch in the fixed-size file-scope array below instead, which every GPU
+// that loads the library holds until the process exits.
 #include <mutex>
 #include <vector>
 
@@ -34,10 +34,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 std::mutex g_mu;
 std::vector<void *> g_addr;   // indexed by device ordinal
 
-messi_status scratch_address(void **out)
+messi_status scratch_address(int dev, void **out)
 {
-    int dev = 0;
-    if (!cuda_ok(cudaGetDevice(&dev), "messi_lower_bounds_noalloc: cudaGetDevice")) return MESSI_ECUDA;
     std::lock_guard<std::mutex> lk(g_mu);
     if ((int)g_addr.size() <= dev) g_addr.resize(dev + 1, nullptr);
     if (!g_addr[dev]) {
@@ -48,16 +46,6 @@ messi_status scratch_address(void **out)
     }
     *out = g_addr[dev];
     return MESSI_OK;
-}
-
-bool on_device(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -76,12 +64,16 @@ extern "C" messi_status messi_lower_bounds_noalloc(const messi_index *ix, const 
     if (ix->len > kNoAllocMaxLen)
         return fail(MESSI_EINVAL, "messi_lower_bounds_noalloc: series length exceeds the 2048-point maximum "
                                   "of its fixed scratch; use messi_lower_bounds");
-    if (!on_device(query) || !on_device(lb2))
+    if (!is_device_ptr(query) || !is_device_ptr(lb2))
         return fail(MESSI_EINVAL, "messi_lower_bounds_noalloc: query and lb2 must be device pointers "
                                   "(host buffers would need staging memory)");
-    void *base = nullptr;
-    messi_status st = scratch_address(&base);
+    // the index, both buffers and the scratch used below must all be the
+    // current device's memory
+    const void *ptrs[2] = {query, lb2};
+    messi_status st = check_device(ix, ptrs, 2, "messi_lower_bounds_noalloc");
     if (st != MESSI_OK) return st;
+    void *base = nullptr;
+    if ((st = scratch_address(ix->device, &base)) != MESSI_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *b = static_cast<char *>(base);
 
@@ -96,23 +88,8 @@ extern "C" messi_status messi_lower_bounds_noalloc(const messi_index *ix, const 
     if (!cuda_ok(cudaMemsetAsync(slot.st, 0, kStateBytes, s), "messi_lower_bounds_noalloc: clear state"))
         return MESSI_ECUDA;
 
-    IndexView iv;
-    iv.raw = ix->raw;
-    iv.sax = ix->sax;
-    iv.ids = ix->ids;
-    iv.pos_of_id = ix->pos_of_id;
-    iv.leaf_off = ix->leaf_off;
-    iv.leaf_key = ix->leaf_key;
-    iv.beta64 = ix->beta64;
-    iv.N = ix->N;
-    iv.L = ix->L;
-    iv.len = ix->len;
-    iv.w = ix->w;
-    iv.card = ix->card;
-    iv.bits = ix->bits;
-    iv.m = ix->m;
-    iv.status = ix->status;
-    QueryParams qp{1, (int)dist, dist == MESSI_DTW ? (int)window : 0, band_factor((int)dist, ix->len)};
+    const IndexView iv = view_of(ix);
+    const QueryParams qp = make_params(ix, 1, (int)dist, window);
     launch_prep(iv, qp, slot, query, s);
     launch_lower_bounds(iv, slot, lb2, s);
     if (!cuda_ok(cudaGetLastError(), "messi_lower_bounds_noalloc: launch")) return MESSI_ECUDA;

@@ -70,9 +70,11 @@ struct messi_server {
     size_t admitted_cost = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
+    bool paused = false;
     std::vector<Worker *> workers;
     // statistics
-    uint64_t submitted = 0, completed = 0, rejected = 0, batches = 0, inflight = 0, inflight_peak = 0;
+    uint64_t submitted = 0, completed = 0, rejected = 0, batches = 0, inflight = 0, inflight_peak = 0,
+             budget_waits = 0;
     std::vector<double> latencies;
 };
 
@@ -86,6 +88,28 @@ size_t request_cost(const messi_index *ix, uint32_t k)
            kSeedMax * 8 + 3 * (size_t)ix->len * 4 + 256;
 }
 
+// The queued request a worker would open its batch with: the oldest of the
+// worker's preferred distance (worker 0 prefers ED, the others DTW, so ED
+// batches never queue behind DTW batches), else the oldest.  Caller holds mu.
+std::deque<Request>::iterator first_request(messi_server *srv, Worker *w)
+{
+    const messi_dist pref = (w == srv->workers[0] || srv->workers.size() == 1) ? MESSI_ED : MESSI_DTW;
+    for (auto it = srv->arrivals.begin(); it != srv->arrivals.end(); ++it)
+        if (it->dist == pref) return it;
+    return srv->arrivals.begin();
+}
+
+// Whether a worker may open a batch now: requests are queued, admission is not
+// held, and the first request fits the memory budget next to the requests in
+// flight (a request larger than the budget is admitted when nothing else is
+// in flight, so it cannot wait forever).  Caller holds mu.
+bool can_admit(messi_server *srv, Worker *w)
+{
+    if (srv->arrivals.empty() || srv->paused) return false;
+    const size_t c = first_request(srv, w)->cost;
+    return srv->admitted_cost == 0 || srv->admitted_cost + c <= srv->cfg.mem_budget;
+}
+
 void worker_loop(messi_server *srv, Worker *w)
 {
     messi_index *ix = srv->ix;
@@ -97,21 +121,26 @@ void worker_loop(messi_server *srv, Worker *w)
         batch.clear();
         {
             std::unique_lock<std::mutex> lk(srv->mu);
-            srv->cv_work.wait(lk, [&] { return srv->stop || !srv->arrivals.empty(); });
-            if (srv->stop && srv->arrivals.empty()) return;
-            // admit in arrival order: same (distance, window) as the oldest
-            // request of this worker's preferred distance (worker 0 prefers ED,
-            // the others DTW, so ED batches never queue behind DTW batches),
-            // while the memory budget allows
-            const messi_dist pref = (w == srv->workers[0] || srv->workers.size() == 1) ? MESSI_ED : MESSI_DTW;
-            auto first = srv->arrivals.begin();
-            for (auto it = srv->arrivals.begin(); it != srv->arrivals.end(); ++it)
-                if (it->dist == pref) { first = it; break; }
+            bool counted = false;
+            srv->cv_work.wait(lk, [&] {
+                if (srv->stop && (srv->arrivals.empty() || srv->paused)) return true;
+                if (can_admit(srv, w)) return true;
+                // requests wait for memory held by batches in flight
+                if (!counted && !srv->arrivals.empty() && !srv->paused) {
+                    ++srv->budget_waits;
+                    counted = true;
+                }
+                return false;
+            });
+            if (srv->stop && (srv->arrivals.empty() || srv->paused)) return;
+            // admit in arrival order: same (distance, window) as the first
+            // request, while the memory budget allows
+            auto first = first_request(srv, w);
             const messi_dist d0 = first->dist;
             const uint32_t w0 = first->window;
             for (auto it = srv->arrivals.begin(); it != srv->arrivals.end() && batch.size() < maxB;) {
                 if (it->dist == d0 && (d0 == MESSI_ED || it->window == w0)) {
-                    if (!batch.empty() && srv->admitted_cost + it->cost > srv->cfg.mem_budget) break;
+                    if (srv->admitted_cost > 0 && srv->admitted_cost + it->cost > srv->cfg.mem_budget) break;
                     srv->admitted_cost += it->cost;
                     batch.push_back(std::move(*it));
                     it = srv->arrivals.erase(it);
@@ -259,7 +288,9 @@ messi_status messi_server_submit(messi_server *srv, const float *query, uint32_t
         srv->arrivals.push_back(std::move(r));
         ++srv->submitted;
     }
-    srv->cv_work.notify_one();
+    // every worker re-checks: which one may admit depends on its preferred
+    // distance and on the memory budget
+    srv->cv_work.notify_all();
     return MESSI_OK;
 }
 
@@ -295,6 +326,7 @@ messi_status messi_server_get_stats(messi_server *srv, messi_server_stats *out)
     out->rejected = srv->rejected;
     out->batches = srv->batches;
     out->inflight_peak = srv->inflight_peak;
+    out->budget_waits = srv->budget_waits;
     std::vector<double> lat = srv->latencies;
     if (!lat.empty()) {
         std::sort(lat.begin(), lat.end());
@@ -308,12 +340,24 @@ messi_status messi_server_get_stats(messi_server *srv, messi_server_stats *out)
     return MESSI_OK;
 }
 
+messi_status messi_server_pause(messi_server *srv, int paused)
+{
+    if (!srv) return fail(MESSI_EINVAL, "messi_server_pause: null server");
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->paused = paused != 0;
+    }
+    srv->cv_work.notify_all();
+    return MESSI_OK;
+}
+
 void messi_server_destroy(messi_server *srv)
 {
     if (!srv) return;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->stop = true;
+        srv->paused = false;   // the queued requests are answered before the workers stop
     }
     srv->cv_work.notify_all();
     for (Worker *w : srv->workers)

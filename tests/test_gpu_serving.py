@@ -1,6 +1,8 @@
-"""Serving loop: requests submitted one at a time and the same requests
-arriving as a Poisson stream (continuous batching, mixed ED / DTW and k)
-give identical results, which also match the FP64 oracle."""
+"""Serving loop: requests submitted one at a time, the same requests
+arriving as a Poisson stream, and the same requests as one burst released
+at once (continuous batching, mixed ED / DTW and k) give identical results,
+which also match the FP64 oracle; the burst shares batches and keeps several
+requests in flight."""
 import threading
 import time
 
@@ -81,13 +83,34 @@ def test_alone_equals_in_the_mix_and_oracle(m):
     assert st["completed"] == st["submitted"] == 2 * len(reqs)
     assert st["p99_ms"] >= st["p50_ms"] > 0
 
-    # exactness against the oracle on a sample of both distances
-    for i in [j for j in range(len(reqs)) if reqs[j][2] == 0][:10] + [j for j in range(len(reqs)) if reqs[j][2] == 1][:4]:
-        q, k, dist, r = reqs[i]
-        ref_ids, ref_d2 = oracle.knn(x, q, k, dist, r)
-        assert np.array_equal(mixed[i][0], ref_ids[0]), i
-        rel = np.abs(mixed[i][1] - np.sqrt(ref_d2[0])) / np.maximum(np.sqrt(ref_d2[0]), 1e-30)
-        assert rel.max() <= 1e-5
+    # the same requests as one burst that arrives while admission is held:
+    # on release the workers take them as shared batches, several requests in
+    # flight at once, and every answer is unchanged
+    m.messi_server_pause(srv)
+    burst = {i: m.messi_server_submit(srv, *reqs[i]) for i in order}
+    m.messi_server_pause(srv, False)
+    together = [None] * len(reqs)
+    for i in order:
+        while together[i] is None:
+            together[i] = m.messi_server_poll(srv, burst[i], reqs[i][1], wait_us=200_000)
+    st2 = m.messi_server_get_stats(srv)
+    assert st2["completed"] - st["completed"] == len(reqs)
+    assert st2["batches"] - st["batches"] < len(reqs)     # requests shared batches
+    assert st2["inflight_peak"] > 1
+    for i in range(len(reqs)):
+        assert np.array_equal(together[i][0], alone[i][0]) and np.array_equal(together[i][1], alone[i][1]), i
+
+    # exactness of every answer against the oracle: one brute-force pass per
+    # distance at the largest k (a k-NN answer is the prefix of the 10-NN)
+    for dist, r in ((0, 0), (1, 12)):
+        sel = [j for j in range(len(reqs)) if reqs[j][2] == dist]
+        ref_ids, ref_d2 = oracle.knn(x, np.stack([reqs[j][0] for j in sel]), 10, dist, r)
+        for row, i in enumerate(sel):
+            k = reqs[i][1]
+            assert np.array_equal(mixed[i][0], ref_ids[row, :k]), i
+            ref = np.sqrt(ref_d2[row, :k])
+            rel = np.abs(mixed[i][1] - ref) / np.maximum(ref, 1e-30)
+            assert rel.max() <= 1e-5, i
     m.messi_server_destroy(srv)
     m.messi_check(ix)
 

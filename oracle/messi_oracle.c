@@ -16,33 +16,113 @@
 
 /* ---------------------------------------------------------------- Sec. 2.2 */
 
-/* Phi(x) - p, evaluated where it keeps full relative accuracy: through
- * erfc in the lower tail, through erf (as (Phi(x) - 1/2) - (p - 1/2), both
- * parts exact or accurately rounded) near the centre. */
-static double cdf_minus(double x, double p)
+/* The breakpoints are the doubles nearest the N(0,1) quantiles PhiInv(j/c):
+ * the real quantile is irrational, so its nearest double is unique and any
+ * correct evaluation of the definition gives the same table.  To decide
+ * which double is nearest, Phi is evaluated in double-double arithmetic (a
+ * value is an unevaluated sum hi + lo, ~104-bit significand) from its
+ * Maclaurin series
+ *     Phi(x) = 1/2 + (1/sqrt(2 pi)) * sum_n (-1)^n x^(2n+1) / (2^n n! (2n+1)),
+ * which converges for every x; for |x| <= 3 its terms stay below 2^7, so the
+ * sum keeps about 90 correct bits. */
+typedef struct { double hi, lo; } dd_t;
+
+static dd_t dd_from_sum(double a, double b)             /* exact a + b (two-sum) */
 {
-    if (x < -0.6) return 0.5 * erfc(-x / sqrt(2.0)) - p;
-    return 0.5 * erf(x / sqrt(2.0)) - (p - 0.5);
+    dd_t r;
+    double s = a + b, v = s - a;
+    r.hi = s;
+    r.lo = (a - (s - v)) + (b - v);
+    return r;
+}
+static dd_t dd_renorm(double a, double b)               /* |a| >= |b| */
+{
+    dd_t r;
+    double s = a + b;
+    r.hi = s;
+    r.lo = b - (s - a);
+    return r;
+}
+static dd_t dd_add(dd_t a, dd_t b)
+{
+    dd_t s = dd_from_sum(a.hi, b.hi), t = dd_from_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = dd_renorm(s.hi, s.lo);
+    s.lo += t.lo;
+    return dd_renorm(s.hi, s.lo);
+}
+static dd_t dd_mul(dd_t a, dd_t b)
+{
+    double p = a.hi * b.hi;
+    double e = fma(a.hi, b.hi, -p);                      /* exact error of the product */
+    e += a.hi * b.lo + a.lo * b.hi;
+    return dd_renorm(p, e);
+}
+static dd_t dd_div_d(dd_t a, double b)                   /* a / b, b a double */
+{
+    double q1 = a.hi / b;
+    double p = q1 * b, pe = fma(q1, b, -p);              /* q1 * b exactly: p + pe */
+    dd_t r = dd_add(a, dd_renorm(-p, -pe));
+    double q2 = r.hi / b;
+    return dd_renorm(q1, q2);
 }
 
-/* PhiInv(p) by bisection: shrink [lo, hi] until the two ends are adjacent
- * doubles, then keep the end whose CDF is nearer p. */
+/* 1/sqrt(2 pi) as a double-double: pi = 3.141592653589793116 +
+ * 1.2246467991473532e-16 (the double nearest pi, then the double nearest
+ * the rest); sqrt by one Newton step from the double root, and the
+ * reciprocal by one more. */
+static dd_t inv_sqrt_two_pi(void)
+{
+    dd_t two_pi = {2.0 * 3.141592653589793116, 2.0 * 1.2246467991473532e-16};
+    double s = sqrt(two_pi.hi);
+    dd_t s2 = {s * s, fma(s, s, -(s * s))};
+    dd_t rem = dd_add(two_pi, (dd_t){-s2.hi, -s2.lo});
+    dd_t root = dd_renorm(s, rem.hi / (2.0 * s));         /* sqrt(2 pi) */
+    double r0 = 1.0 / root.hi;
+    dd_t prod = dd_mul(root, (dd_t){r0, 0.0});            /* root * r0 = 1 - e */
+    dd_t e = dd_add((dd_t){1.0, 0.0}, (dd_t){-prod.hi, -prod.lo});
+    return dd_renorm(r0, r0 * e.hi);                      /* r0 (1 + e) */
+}
+
+/* Phi(x) - p for a double-double x with |x| <= 3 (p exact in double). */
+static dd_t cdf_minus_dd(dd_t x, double p)
+{
+    dd_t half_x2 = dd_mul(dd_mul(x, x), (dd_t){0.5, 0.0});
+    dd_t power = x;                                       /* (-1)^n x^(2n+1) / (2^n n!) */
+    dd_t sum = x;
+    for (int n = 1; n < 200; ++n) {
+        power = dd_div_d(dd_mul(power, (dd_t){-half_x2.hi, -half_x2.lo}), (double)n);
+        dd_t term = dd_div_d(power, (double)(2 * n + 1));
+        sum = dd_add(sum, term);
+        if (fabs(term.hi) < 1e-40) break;
+    }
+    dd_t phi = dd_add((dd_t){0.5, 0.0}, dd_mul(inv_sqrt_two_pi(), sum));
+    return dd_add(phi, (dd_t){-p, 0.0});
+}
+
+/* The double nearest PhiInv(p), 0 < p < 1/2: bisection on doubles in
+ * [-3, 0] (the CDF's sign decides each step) down to two adjacent doubles
+ * lo < hi around the quantile, then the one nearer it -- hi if the CDF at
+ * their midpoint (lo + hi)/2, held exactly as a double-double, is below p. */
 static double std_normal_quantile(double p)
 {
-    double lo = -40.0, hi = 40.0;
-    for (int it = 0; it < 2000; ++it) {
-        double mid = 0.5 * (lo + hi);
+    double lo = -3.0, hi = 0.0;
+    for (int it = 0; it < 4000; ++it) {
+        double mid = lo + 0.5 * (hi - lo);
         if (mid <= lo || mid >= hi) break;
-        if (cdf_minus(mid, p) < 0.0) lo = mid; else hi = mid;
+        dd_t g = cdf_minus_dd((dd_t){mid, 0.0}, p);
+        if (g.hi < 0.0) lo = mid; else hi = mid;
     }
-    return (fabs(cdf_minus(lo, p)) < fabs(cdf_minus(hi, p))) ? lo : hi;
+    dd_t m = dd_renorm(lo, 0.5 * (hi - lo));
+    return cdf_minus_dd(m, p).hi < 0.0 ? hi : lo;
 }
 
 void orc_breakpoints(int card, double *beta)
 {
-    /* Lower half by bisection (where erfc is evaluated at positive arguments
-     * and keeps full relative accuracy); the upper half by the symmetry of
-     * N(0,1), PhiInv(1 - p) = -PhiInv(p); the median is 0. */
+    /* Lower half by bisection (p < 1/2, where the CDF minus p keeps its
+     * relative accuracy); the upper half by the symmetry of N(0,1),
+     * PhiInv(1 - p) = -PhiInv(p), which maps nearest doubles to nearest
+     * doubles; the median is 0. */
     for (int j = 1; 2 * j < card; ++j)
         beta[j - 1] = std_normal_quantile((double)j / (double)card);
     for (int j = 1; j < card; ++j) {

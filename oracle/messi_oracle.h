@@ -25,8 +25,9 @@ extern "C" {
 #endif
 
 /* iSAX breakpoints (Sec. 2.2, "iSAX Representation": the y-axis is split
- * into c equiprobable regions of N(0,1)).  beta[j-1] = PhiInv(j / c) for
- * j = 1..c-1, found by bisection on Phi(x) = erfc(-x / sqrt 2) / 2. */
+ * into c equiprobable regions of N(0,1)).  beta[j-1] = the double nearest
+ * PhiInv(j / c) for j = 1..c-1, found by bisection on doubles with Phi
+ * evaluated in double-double arithmetic from its Maclaurin series. */
 void orc_breakpoints(int card, double *beta);
 
 /* PAA (Sec. 2.2): paa[s] = mean of x[s*m .. s*m+m-1], FP64 sequential sum,

@@ -396,53 +396,6 @@ int num_sms()
     return cached[dev];
 }
 
-// N(0,1) quantiles j/c by safeguarded Newton iteration on Phi(x) - p, with
-// Phi evaluated through erfc in the lower tail and erf near the centre; the
-// upper half follows from symmetry.  Each root is polished to the double
-// whose CDF lies nearest p among its neighbours.
-namespace {
-double phi_minus(double x, double p)
-{
-    const double rt2 = 1.4142135623730951;
-    if (x < -0.6) return 0.5 * std::erfc(-x / rt2) - p;
-    return 0.5 * std::erf(x / rt2) - (p - 0.5);
-}
-
-double quantile_newton(double p)
-{
-    const double inv_sqrt_2pi = 0.3989422804014327;
-    double lo = -40.0, hi = 40.0, x = 0.0;
-    for (int it = 0; it < 200; ++it) {
-        const double f = phi_minus(x, p);
-        if (f < 0) lo = x; else hi = x;
-        const double dens = inv_sqrt_2pi * std::exp(-0.5 * x * x);
-        double nx = x - f / dens;
-        if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
-        if (nx == x) break;
-        x = nx;
-    }
-    for (int pass = 0; pass < 4; ++pass) {   // local polish over neighbours
-        const double a = std::nextafter(x, -INFINITY), b = std::nextafter(x, INFINITY);
-        double best = x, eb = std::fabs(phi_minus(x, p));
-        const double ea = std::fabs(phi_minus(a, p)), ebb = std::fabs(phi_minus(b, p));
-        if (ea < eb) { best = a; eb = ea; }
-        if (ebb < eb) { best = b; }
-        if (best == x) break;
-        x = best;
-    }
-    return x;
-}
-}  // namespace
-
-void compute_breakpoints(int card, double *beta)
-{
-    for (int j = 1; 2 * j < card; ++j) beta[j - 1] = quantile_newton((double)j / card);
-    for (int j = 1; j < card; ++j) {
-        if (2 * j == card) beta[j - 1] = 0.0;
-        else if (2 * j > card) beta[j - 1] = -beta[card - j - 1];
-    }
-}
-
 }  // namespace messi
 
 using namespace messi;

@@ -55,15 +55,34 @@ def test_python_binding_names_match_header():
         assert callable(getattr(m, n)), n
 
 
-@pytest.mark.parametrize("card", [2, 4, 16, 64, 256])
+@pytest.mark.parametrize("card", [2, 4, 8, 16, 32, 64, 128, 256])
 def test_breakpoints_match_oracle(card):
+    # both sides compute the double nearest each quantile (each by its own
+    # method): the tables agree bit for bit, so a PAA value gets the same
+    # symbol from either
     import paper_2110_07519_gb300 as m
 
     lib_b = m.messi_breakpoints(card)
     orc_b = oracle.breakpoints(card)
-    ulps = np.abs(lib_b - orc_b) / np.spacing(np.maximum(np.abs(orc_b), 1e-300))
-    assert ulps.max() <= 2, ulps.max()
+    assert np.array_equal(lib_b.view(np.uint64), orc_b.view(np.uint64))
     assert np.all(np.diff(lib_b) > 0)
+
+
+@pytest.mark.parametrize("card", [4, 16, 64, 256])
+def test_library_breakpoints_correctly_rounded(card):
+    # against a 300-bit evaluation of the quantile (mpmath), independently
+    # of the oracle
+    mpmath = pytest.importorskip("mpmath")
+    import paper_2110_07519_gb300 as m
+
+    mpmath.mp.prec = 300
+    lib_b = m.messi_breakpoints(card)
+    for j in range(1, card):
+        exact = mpmath.sqrt(2) * mpmath.erfinv(2 * mpmath.mpf(j) / card - 1)
+        got = lib_b[j - 1]
+        gap = abs(mpmath.mpf(got) - exact)
+        for nb in (np.nextafter(got, -np.inf), np.nextafter(got, np.inf)):
+            assert gap < abs(mpmath.mpf(nb) - exact), (card, j)
 
 
 def test_invalid_arguments_rejected_without_gpu(lib):

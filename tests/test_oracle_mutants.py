@@ -27,6 +27,12 @@ MUTANTS = [
      "if (beta[j - 1] <= paa[s]) ++count;", "if (beta[j - 1] < paa[s]) ++count;"),
     ("breakpoints at j / (c + 1)",
      "std_normal_quantile((double)j / (double)card)", "std_normal_quantile((double)j / (double)(card + 1))"),
+    ("CDF series loses its alternating sign",
+     "dd_mul(power, (dd_t){-half_x2.hi, -half_x2.lo})", "dd_mul(power, half_x2)"),
+    ("quantile rounded to the farther of its two neighbours",
+     "return cdf_minus_dd(m, p).hi < 0.0 ? hi : lo;", "return cdf_minus_dd(m, p).hi < 0.0 ? lo : hi;"),
+    ("CDF series term divided by 2n - 1",
+     "dd_t term = dd_div_d(power, (double)(2 * n + 1));", "dd_t term = dd_div_d(power, (double)(2 * n - 1));"),
     ("iSAX key takes the symbol bits LSB first",
      "uint32_t bit = (sym[s] >> (b - 1 - j)) & 1u;", "uint32_t bit = (sym[s] >> j) & 1u;"),
     ("ED adds instead of subtracting",

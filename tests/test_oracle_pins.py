@@ -48,6 +48,28 @@ def test_breakpoints_vs_scipy_symmetry_monotone(card):
     assert np.allclose(sp.ndtr(b), np.arange(1, card) / card, rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("card", [2, 4, 8, 16, 32, 64, 128, 256])
+def test_breakpoints_are_the_nearest_doubles(card):
+    # beta_j is the double nearest the real quantile PhiInv(j/c): checked
+    # against a 300-bit evaluation (mpmath's erfinv), 0 ulps
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 300
+    b = oracle.breakpoints(card)
+    for j in range(1, card):
+        exact = mpmath.sqrt(2) * mpmath.erfinv(2 * mpmath.mpf(j) / card - 1)
+        gap = abs(mpmath.mpf(b[j - 1]) - exact)
+        for nb in (np.nextafter(b[j - 1], -np.inf), np.nextafter(b[j - 1], np.inf)):
+            assert gap < abs(mpmath.mpf(nb) - exact), (card, j)
+
+
+def test_breakpoint_examples_to_the_last_bit():
+    # the nearest doubles of three textbook quantiles (their decimal forms
+    # pin the value to the bit): PhiInv(1/4), PhiInv(7/8), PhiInv(1/256)
+    assert oracle.breakpoints(4)[0] == -0.6744897501960817
+    assert oracle.breakpoints(8)[6] == 1.150349380376008
+    assert oracle.breakpoints(256)[0] == -2.6600674686174597
+
+
 # ------------------------------------------------------------------- PAA
 def test_paa_constant_and_ramp():
     n, w = 256, 16

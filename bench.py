@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--dist", default="ed", choices=["ed", "dtw"])
     ap.add_argument("--window", type=int, default=-1, help="DTW reach in points (default 10%% of len)")
     ap.add_argument("--cpu-sample", type=int, default=4, help="queries in the CPU-oracle sample")
+    ap.add_argument("--class-queries", type=int, default=64,
+                    help="queries per class in the plain form's per-class breakdown (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--form", default="both", choices=["both", "plain", "batched"])
@@ -287,7 +289,7 @@ def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists, dist=
     clocks = ClockSampler(dev.index or 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     agg = {"kern_ms": 0.0, "kern_launches": 0, "launches": 0, "survivors": 0, "rows": 0, "words": 0, "lat": [],
-           "screened": 0}
+           "screened": 0, "row_bytes": 0, "bsf_updates": 0}
     torch.cuda.synchronize()
     e0.record(stream)
     for s in range(W, W + K):
@@ -300,7 +302,8 @@ def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists, dist=
         agg["survivors"] += st["lb_survivors"]
         agg["rows"] += st["refined"] + st["abandoned"]
         agg["words"] += st["lb_evaluated"]
-        agg["lat"] += [st["query_ms_p50"], st["query_ms_p99"]]
+        agg["row_bytes"] += st["row_bytes"]
+        agg["bsf_updates"] += st["bsf_updates"]
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -377,6 +380,15 @@ def run_messi(args, ws, rank, local):
         cpu = {"value": args.cpu_sample / cpu_s, "unit": "queries/s", "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_sample} queries of the timed mix, FP64 brute force over all {args.n} "
                          f"series (1M-row chunks copied to the host; copy time excluded)"}
+    # per-class queries for the plain form's breakdown (fresh walks; members
+    # with sigma 0.1 / 0.5 / 1.0 noise), drawn while the collection exists
+    class_pools = {}
+    if not args.windows and args.form in ("both", "plain") and args.class_queries > 0:
+        cq = args.class_queries
+        class_pools["fresh"] = synth.random_walks_torch(cq, args.len, seed=synth.QUERY_SEED + 100 + rank, device=dev)
+        for i, sg in enumerate((0.1, 0.5, 1.0)):
+            class_pools[f"sigma{sg}"] = synth.noisy_members_torch(data, cq, sg,
+                                                                  seed=synth.NOISE_SEED + 100 + i + rank)[0]
     qpool = qpool.clone()
     del data
     torch.cuda.empty_cache()
@@ -421,19 +433,54 @@ def run_messi(args, ws, rank, local):
             algo = 16.0 * args.n + 4.0 * args.len * r["rows"] / max(r["kern_launches"], 1)
             roof = {"bound": "hbm", "achieved": algo / kern_avg_s / 1e9, "peak": peak, "unit": "GB/s",
                     "frac": algo / kern_avg_s / 1e9 / peak, "peak_kind": peak_kind}
-        words_q = r["words"] / nqt if form == "plain" else float(args.n)
-        q_bytes = (40.0 * n_leaves + 4.0 * ntiles + 16.0 * words_q + 8.0 * r["survivors"] / nqt
-                   + 4.0 * args.len * r["rows"] / nqt)
+        if form == "plain":
+            # bytes one query moves: leaf boxes and offsets, tile stamps, the
+            # words of its live tiles, its survivor list (written once, read by
+            # the refinement) and the raw-row bytes its refinement read
+            q_bytes = (40.0 * n_leaves + 4.0 * ntiles + 16.0 * r["words"] / nqt + 16.0 * r["survivors"] / nqt
+                       + r["row_bytes"] / nqt)
+        elif batch_mode == "tc_screen":
+            # per query: its share of the f16 rows and norms each screen launch
+            # streams, plus the rows its exact recheck read
+            q_bytes = ((2.0 * args.len + 8.0) * args.n * r["kern_launches"] + r["row_bytes"]) / nqt
+        else:
+            q_bytes = (16.0 * args.n * r["kern_launches"] + r["row_bytes"]) / nqt
         forms[form] = {
             "value": replica_throughput(ws, nqt, r["elapsed_ms"]), "ms_per_step": r["elapsed_ms"] / K,
             "p50_ms": r["p50"], "p99_ms": r["p99"], "gpu_launches": r["launches"], "clocks": r["clocks"],
             "roofline": dict(roof, kernel=kernel, algorithmic_per_launch=algo, avg_launch_ms=kern_avg_s * 1e3,
                              launches=r["kern_launches"]),
             "counters": {"lb_survivors_per_query": r["survivors"] / nqt, "rows_read_per_query": r["rows"] / nqt,
-                         "words_scanned_per_query": r["words"] / nqt},
+                         "row_bytes_per_query": r["row_bytes"] / nqt,
+                         "words_scanned_per_query": r["words"] / nqt,
+                         "bsf_updates_per_query": r["bsf_updates"] / nqt},
             "query_roofline_frac": q_bytes / (r["elapsed_ms"] * 1e-3 / nqt) / 1e9 / peak,
             **({"tuning": tuning} if tuning and form == "batched" else {}),
         }
+    # plain form, query class by class (untimed against the bench clock; CUDA
+    # events around each class's call): throughput and the work counters
+    if class_pools and "plain" in forms:
+        per_class = {}
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for name, cq in class_pools.items():
+            m.messi_query(ix, cq[:8], k=args.k, dist=dist_code, window=window)   # warm-up
+            torch.cuda.synchronize()
+            c0.record(stream)
+            m.messi_query(ix, cq, k=args.k, dist=dist_code, window=window)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            st = m.messi_query_stats(ix)
+            nq_c = cq.shape[0]
+            per_class[name] = {
+                "queries": nq_c, "queries_per_s": nq_c / (c0.elapsed_time(c1) * 1e-3),
+                "words_scanned_per_query": st["lb_evaluated"] / nq_c,
+                "lb_survivors_per_query": st["lb_survivors"] / nq_c,
+                "rows_read_per_query": (st["refined"] + st["abandoned"]) / nq_c,
+                "row_bytes_per_query": st["row_bytes"] / nq_c,
+                "seeded_per_query": st["seeded"] / nq_c,
+                "bsf_updates_per_query": st["bsf_updates"] / nq_c,
+                "leaves_live_per_query": st["leaves_live"] / nq_c}
+        forms["plain"]["per_class"] = per_class
     head_form = max(forms, key=lambda f: forms[f]["value"])
     head = forms[head_form]
     traffic = profiled_traffic(args.n, head["roofline"]["kernel"])

@@ -81,7 +81,9 @@ typedef struct {
     uint64_t leaves_live;     /* leaves whose symbol box did not prune them   */
     uint64_t screened_queries; /* batched screen: queries over all its passes
                                   (a query screened again counts again)      */
-    uint64_t reserved[4];
+    uint64_t row_bytes;       /* ED refinement: bytes of raw rows read (whole
+                                  256-point chunks up to an early abandon)   */
+    uint64_t reserved[3];
 } messi_stats;
 
 typedef struct {

@@ -955,6 +955,7 @@ messi_status messi_query_stats(const messi_index *cix, messi_stats *out)
     out->bsf_updates = c.bsf_updates;
     out->tie_rechecks = c.tie_rechecks;
     out->leaves_live = c.leaves_live;
+    out->row_bytes = c.row_bytes;
     if (ix->profiling) {
         double sum = 0.0;
         for (auto &pr : ws->scan_ev) {

@@ -184,10 +184,14 @@ __device__ __forceinline__ float warp_ed2(const float *__restrict__ q, const flo
 // Two rows at once (more loads in flight); same arithmetic as warp_ed2 for
 // each row.  A row whose running sum exceeds thr after a 256-point chunk
 // stops accumulating; its returned value is then that partial sum (> thr).
+// na / nb receive the points of each row read (whole 256-point chunks
+// loaded while the row was still live; len when it ran to the end).
 __device__ __forceinline__ void warp_ed2_pair(const float *__restrict__ q, const float *__restrict__ xa,
                                               const float *__restrict__ xb, int len, float thr, float &da,
-                                              float &db)
+                                              float &db, int &na, int &nb)
 {
+    na = 0;
+    nb = 0;
     const int lane = threadIdx.x & 31;
     const int n4 = len >> 2;
     const float4 *q4 = reinterpret_cast<const float4 *>(q);
@@ -196,6 +200,9 @@ __device__ __forceinline__ void warp_ed2_pair(const float *__restrict__ q, const
     float aa = 0.f, ab = 0.f;
     bool live_a = true, live_b = true;
     for (int base = 0; base < n4; base += 64) {
+        const int pts = min(256, 4 * (n4 - base));
+        if (live_a) na += pts;
+        if (live_b) nb += pts;
         float4 xv[4];
 #pragma unroll
         for (int t = 0; t < 2; ++t) {

@@ -49,7 +49,7 @@ constexpr unsigned kSpinLimit = 1u << 22;
 // ------------------------------------------------------- per-query state
 struct QueryCounters {
     unsigned long long lb_evaluated, lb_survivors, lbk_survivors, seeded, refined, abandoned,
-        bsf_updates, tie_rechecks, leaves_live;
+        bsf_updates, tie_rechecks, leaves_live, row_bytes;
 };
 
 struct QueryState {

@@ -44,8 +44,8 @@ constexpr int kScanWpt = 2;
 constexpr int kScanTileWords = kScanThreads * kScanWpt;   // 1024 words, 16 KB
 static_assert(kScanTileWords == kScanTileWordsHost, "scan tile size shared with the workspace layout");
 constexpr int kScanStages = 4;
-constexpr int kScanCtasPerSm = 2;
-constexpr int kScanSmem = kMaxSegments * kMaxCard * 4 + kScanStages * kScanTileWords * 16;
+constexpr int kScanCtasPerSm = 3;
+constexpr int kScanSmem = kScanStages * kScanTileWords * 16 + kMaxSegments * kMaxCard * 2;   // 72 KB
 constexpr int kFinThreads = 1024;
 
 // ------------------------------------------------------------------ prep
@@ -399,20 +399,89 @@ k_live_tiles(QuerySlot slot, unsigned long long ntiles, unsigned epoch)
     }
 }
 
+// The scan's table: every entry of the query's FP32 table (already rounded
+// down) as a 16-bit multiple of a power of two D, rounded down and capped at
+// 65535 -- code * D <= entry exactly, since dividing by a power of two is
+// exact.  A word's bound is then (sum of its 16 codes) * D: an integer sum,
+// at most 16 D below the sum of its FP32 entries, still never above the
+// exact bound.  D is the smallest power of two >= R / 4096, R the pruning
+// threshold (or, while no threshold exists, 16 x the largest entry, which
+// bounds every word), so the looser bound costs at most R / 128 and a capped
+// code alone already exceeds R.  Half the bytes of the FP32 table: a row of
+// 256 entries spans 4 bank rows instead of 8, and the table lookups of a warp
+// (the scan's bottleneck) meet fewer bank conflicts.
+struct ScanCodes {
+    float D;          // the power of two
+    unsigned limit;   // largest code sum that survives: floor(threshold / D)
+};
+
+__device__ __forceinline__ ScanCodes scan_codes(const float *__restrict__ lut, float thrp, unsigned short *codes,
+                                                 float *red)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float R = thrp;
+    if (!(thrp < f_inf())) {   // no finite threshold: bound by the largest entry
+        float mx = 0.f;
+        for (int i = tid; i < kMaxSegments * kMaxCard; i += blockDim.x) mx = fmaxf(mx, lut[i]);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (lane == 0) red[warp] = mx;
+        __syncthreads();
+        mx = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+        R = 16.f * mx;
+    }
+    int e = 0;
+    const float f = frexpf(R * (1.f / 4096.f), &e);       // R / 4096 = f 2^e, f in [0.5, 1)
+    ScanCodes sc;
+    sc.D = (R > 0.f && f > 0.f) ? fmaxf(ldexpf(1.f, e), 1.17549435e-38f) : 1.17549435e-38f;   // >= R / 4096
+    for (int i = tid; i < kMaxSegments * kMaxCard; i += blockDim.x) {
+        const float c = lut[i] / sc.D;                    // exact (or overflow to inf)
+        codes[i] = c >= 65535.f ? (unsigned short)65535 : (unsigned short)c;   // truncation = floor
+    }
+    if (thrp < f_inf()) {
+        const float q = thrp / sc.D;                      // exact
+        sc.limit = q >= 4294967040.f ? 0xffffffffu : (unsigned)q;
+    } else {
+        sc.limit = 0xffffffffu;
+    }
+    return sc;
+}
+
+// code sum of the 8 segments held in two 32-bit words starting at segment s0
+__device__ __forceinline__ unsigned code_half(unsigned w0, unsigned w1, const unsigned short *codes, int s0)
+{
+    unsigned v[8];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) v[b] = codes[(s0 + b) * kMaxCard + ((w0 >> (8 * b)) & 0xffu)];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) v[4 + b] = codes[(s0 + 4 + b) * kMaxCard + ((w1 >> (8 * b)) & 0xffu)];
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+}
+
+// Persistent CTAs; CTA c owns the contiguous run [c*tpc, (c+1)*tpc) of the
+// live-tile list and writes its survivors into its own region of the
+// survivor arrays, so compaction needs only a shared-memory counter.  Tiles
+// arrive by 1-D bulk copies into a ring of kScanStages stages; no block-wide
+// barrier per tile: each warp counts itself done with a stage, and the last
+// warp to finish it refills it with the tile kScanStages further on, so warps
+// drift apart by up to a few tiles instead of waiting for the slowest.
 __global__ void __launch_bounds__(kScanThreads, kScanCtasPerSm)
 k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bars[kScanStages];
+    __shared__ unsigned done[kScanStages];
+    __shared__ int issued_it[kScanStages];     // iteration of the last copy issued into each stage
     __shared__ int timed_out;
     __shared__ unsigned s_count;
-    __shared__ unsigned long long s_words;
-    float *lut = reinterpret_cast<float *>(smem);
-    uint4 *stage = reinterpret_cast<uint4 *>(smem + kMaxSegments * kMaxCard * 4);
+    __shared__ float red[32];
+    uint4 *stage = reinterpret_cast<uint4 *>(smem);
+    unsigned short *codes = reinterpret_cast<unsigned short *>(smem + kScanStages * kScanTileWords * 16);
     QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
     const int tid = threadIdx.x, lane = tid & 31;
-    for (int i = tid; i < kMaxSegments * kMaxCard; i += blockDim.x) lut[i] = slot.lut[i];
+    constexpr unsigned kWarps = kScanThreads / 32;
     const float thrp = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
     const unsigned long long seed_lo = st->seed_lo, seed_hi = st->seed_hi;
     const unsigned long long N = iv.N;
@@ -421,51 +490,56 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
     const unsigned tpc = (nlive + gridDim.x - 1) / gridDim.x;
     const unsigned i0 = min(nlive, blockIdx.x * tpc), i1 = min(nlive, i0 + tpc);
     const unsigned long long region = (unsigned long long)blockIdx.x * tpc * kScanTileWords;
+    auto issue = [&](unsigned idx, int s) {
+        const unsigned long long first = (unsigned long long)slot.live_list[idx] * kScanTileWords;
+        const unsigned long long cnt = min((unsigned long long)kScanTileWords, N - first);
+        const unsigned bytes = (unsigned)(cnt * 16);
+        issued_it[s] = (int)(idx - i0);
+        mbar_arrive_expect_tx(&bars[s], bytes);
+        bulk_g2s(stage + s * kScanTileWords, iv.sax + first, bytes, &bars[s]);
+    };
     if (tid == 0) {
         timed_out = 0;
         s_count = 0;
-        s_words = 0;
-        for (int s = 0; s < kScanStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < kScanStages; ++s) {
+            mbar_init(&bars[s], 1);
+            done[s] = 0;
+            issued_it[s] = -1;
+        }
         fence_barrier_init();
         fence_proxy_async();
         if (blockIdx.x == 0) {
             st->scan_grid = gridDim.x;
             st->region_words = tpc * kScanTileWords;
         }
-    }
-    __syncthreads();
-    auto issue = [&](unsigned idx, int s) {
-        const unsigned long long first = (unsigned long long)slot.live_list[idx] * kScanTileWords;
-        const unsigned long long cnt = min((unsigned long long)kScanTileWords, N - first);
-        const unsigned bytes = (unsigned)(cnt * 16);
-        mbar_arrive_expect_tx(&bars[s], bytes);
-        bulk_g2s(stage + s * kScanTileWords, iv.sax + first, bytes, &bars[s]);
-    };
-    if (tid == 0)
         for (int s = 0; s < kScanStages && i0 + s < i1; ++s) issue(i0 + s, s);
+    }
+    const ScanCodes sc = scan_codes(slot.lut, thrp, codes, red);
+    __syncthreads();
     unsigned iter = 0;
     for (unsigned idx = i0; idx < i1; ++idx, ++iter) {
+        if (__shfl_sync(0xffffffffu, *reinterpret_cast<volatile int *>(&timed_out), 0)) break;
         const int s = iter % kScanStages;
         const unsigned parity = (iter / kScanStages) & 1u;
-        const bool ok = mbar_wait_bounded(&bars[s], parity);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(iv.status, kStTimeout);
-            timed_out = 1;
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[s], parity))) {
+            if (lane == 0) {
+                atomicOr(iv.status, kStTimeout);
+                timed_out = 1;
+            }
             break;
         }
         const unsigned long long first = (unsigned long long)slot.live_list[idx] * kScanTileWords;
         const unsigned cnt = (unsigned)min((unsigned long long)kScanTileWords, N - first);
-        if (tid == 0) s_words += cnt;
 #pragma unroll
         for (int r = 0; r < kScanWpt; ++r) {
             const unsigned j = tid + r * kScanThreads;
             const bool valid = j < cnt;
             const uint4 wv = valid ? stage[s * kScanTileWords + j] : make_uint4(0, 0, 0, 0);
             // first half of the segments; the rest only if some lane can still survive
-            float lb = lb2_half(wv.x, wv.y, lut, 0, 0.f);
-            if (__any_sync(0xffffffffu, valid && lb <= thrp)) lb = lb2_half(wv.z, wv.w, lut, 8, lb);
+            unsigned sum = code_half(wv.x, wv.y, codes, 0);
+            if (__any_sync(0xffffffffu, valid && sum <= sc.limit)) sum += code_half(wv.z, wv.w, codes, 8);
             const unsigned long long pos = first + j;
-            const bool surv = valid && lb <= thrp && (pos < seed_lo || pos >= seed_hi);
+            const bool surv = valid && sum <= sc.limit && (pos < seed_lo || pos >= seed_hi);
             const unsigned ballot = __ballot_sync(0xffffffffu, surv);
             if (ballot) {   // warp-uniform
                 unsigned base = 0;
@@ -474,83 +548,125 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
                 if (surv) {
                     const unsigned long long o = region + base + __popc(ballot & ((1u << lane) - 1u));
                     slot.surv_pos[o] = (unsigned)pos;
-                    slot.surv_lb[o] = lb;
+                    slot.surv_lb[o] = (float)sum * sc.D;   // exact: sum < 2^24, D a power of two
                 }
             }
         }
-        __syncthreads();
-        if (tid == 0 && idx + kScanStages < i1) issue(idx + kScanStages, s);
+        // this warp is done with stage s; the last warp to finish it refills it
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            if (atomicAdd(&done[s], 1u) == kWarps - 1) {
+                done[s] = 0;
+                if (idx + kScanStages < i1 && !*reinterpret_cast<volatile int *>(&timed_out)) {
+                    fence_proxy_async();
+                    issue(idx + kScanStages, s);
+                }
+            }
+        }
     }
+    __syncthreads();
     if (timed_out) {
-        // let the copies still in flight (iterations iter .. iter+S-1) land
-        // before the block's shared memory is released
+        // each stage holds at most one copy in flight, the last one issued into
+        // it (a stage is refilled only after every warp waited for and used
+        // its previous copy); let those land before shared memory is released
         if (tid == 0)
-            for (unsigned it = iter; it < iter + kScanStages && i0 + it < i1; ++it)
-                mbar_wait_bounded(&bars[it % kScanStages], (it / kScanStages) & 1u);
+            for (int s = 0; s < kScanStages; ++s)
+                if (issued_it[s] >= 0) mbar_wait_bounded(&bars[s], ((unsigned)issued_it[s] / kScanStages) & 1u);
         if (tid == 0) slot.region_count[blockIdx.x] = 0;
         return;
     }
-    __syncthreads();
     if (tid == 0) {
         slot.region_count[blockIdx.x] = s_count;
         if (s_count) atomicAdd(&st->c.lb_survivors, (unsigned long long)s_count);
-        if (s_words) atomicAdd(&st->c.lb_evaluated, s_words);
+        if (i1 > i0) {
+            unsigned long long wsum = 0;
+            for (unsigned idx = i0; idx < i1; ++idx) {
+                const unsigned long long first = (unsigned long long)slot.live_list[idx] * kScanTileWords;
+                wsum += min((unsigned long long)kScanTileWords, N - first);
+            }
+            atomicAdd(&st->c.lb_evaluated, wsum);
+        }
     }
 }
 
 
 // ------------------------------------------------------------ ED refine
-// A warp takes 32 survivors at a time: one coalesced read of their positions
-// and bounds, one read of the live best-so-far, a ballot of those whose bound
-// is still within it; then real distances for those, two rows in flight.
+// Refinement in bound order (the priority-queue order of Sec. 3, Algorithm
+// 8), without sorting: the survivors stay in the scan's regions and the
+// kernel sweeps them in kRefineBands passes over bands of the lower bound,
+// band b holding bounds in [t (b / B)^2, t ((b + 1) / B)^2) of the scan's
+// threshold t (uniform in distance, finer where most survivors sit).  Every
+// warp finishes its share of band b before it starts band b + 1, and stops at
+// the first band whose floor lies above the live best-so-far.  A warp takes
+// 32 survivors at a time (one coalesced read of their positions and bounds;
+// the lists stay in L2 across bands), ballots those inside the band and
+// within the live threshold, then computes real distances two rows at a
+// time.  Exactness does not depend on the order, only the number of rows
+// read does.
+constexpr int kRefineBands = 8;
+
 __global__ void __launch_bounds__(256)
 k_refine_ed(IndexView iv, QueryParams qp, QuerySlot slot)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ unsigned prefix[kMaxScanGrid + 1], counts[kMaxScanGrid];
     QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
     float *qs = reinterpret_cast<float *>(dsm);
     for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
-    __syncthreads();
-    // survivors in increasing lower-bound bucket: a warp takes chunks of 32
-    // and stops once a chunk's first (smallest) bucket lies above the threshold
-    const unsigned n = ld_volatile_u32(&st->ord_count);
-    const unsigned nchunks = (n + 31) >> 5;
+    const unsigned G = st->scan_grid;
+    const unsigned long long RW = st->region_words;
+    const unsigned nchunks = chunk_prefix(slot, G, prefix, counts);   // ends with a block barrier
     const int lane = threadIdx.x & 31;
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
-    unsigned long long done = 0, aband = 0;
-    for (unsigned ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += nw) {
-        const unsigned i = ch * 32 + lane;
-        const bool valid = i < n;
-        const unsigned pos = valid ? slot.surv2[i] : 0u;
-        const float lb = valid ? slot.surv2_lb[i] : f_inf();
-        float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
-        if (order_floor(order_bucket(__shfl_sync(0xffffffffu, lb, 0))) > thr) break;
-        unsigned mask = __ballot_sync(0xffffffffu, valid && lb <= thr);
-        while (mask) {
-            const int a = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const int b = mask ? __ffs(mask) - 1 : -1;
-            if (b >= 0) mask &= mask - 1;
-            const unsigned pa = __shfl_sync(0xffffffffu, pos, a);
-            const unsigned pb = __shfl_sync(0xffffffffu, pos, b >= 0 ? b : a);
-            float da, db;
-            warp_ed2_pair(qs, iv.raw + (unsigned long long)pa * iv.len, iv.raw + (unsigned long long)pb * iv.len,
-                          iv.len, thr, da, db);
-            if (da <= thr) { ++done; if (lane == 0) offer(qp, slot, iv.status, da, iv.ids[pa]); }
-            else ++aband;
-            if (b >= 0) {
-                if (db <= thr) { ++done; if (lane == 0) offer(qp, slot, iv.status, db, iv.ids[pb]); }
+    const float t0 = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+    const int bands = t0 < f_inf() ? kRefineBands : 1;
+    unsigned long long done = 0, aband = 0, bytes = 0;
+    for (int band = 0; band < bands; ++band) {
+        const float flo = bands == 1 ? 0.f : t0 * ((float)(band * band) / (float)(kRefineBands * kRefineBands));
+        const float fhi = band == bands - 1 ? f_inf()
+                                            : t0 * ((float)((band + 1) * (band + 1)) / (float)(kRefineBands * kRefineBands));
+        if (flo > prune_threshold(ld_volatile_u64(&st->thr), qp.F)) break;   // every later band too
+        for (unsigned ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += nw) {
+            const unsigned rg = region_of(ch, prefix, G);
+            const unsigned within = (ch - prefix[rg]) * 32 + lane;
+            const bool valid = within < counts[rg];
+            const unsigned long long i = rg * RW + within;
+            const unsigned pos = valid ? slot.surv_pos[i] : 0u;
+            const float lb = valid ? slot.surv_lb[i] : f_inf();
+            const bool in_band = lb >= flo && lb < fhi;
+            float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+            unsigned mask = __ballot_sync(0xffffffffu, valid && in_band && lb <= thr);
+            while (mask) {
+                const int a = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int b = mask ? __ffs(mask) - 1 : -1;
+                if (b >= 0) mask &= mask - 1;
+                const unsigned pa = __shfl_sync(0xffffffffu, pos, a);
+                const unsigned pb = __shfl_sync(0xffffffffu, pos, b >= 0 ? b : a);
+                float da, db;
+                int na, nb;
+                warp_ed2_pair(qs, iv.raw + (unsigned long long)pa * iv.len, iv.raw + (unsigned long long)pb * iv.len,
+                              iv.len, thr, da, db, na, nb);
+                bytes += 4ull * na;
+                if (da <= thr) { ++done; if (lane == 0) offer(qp, slot, iv.status, da, iv.ids[pa]); }
                 else ++aband;
+                if (b >= 0) {
+                    bytes += 4ull * nb;
+                    if (db <= thr) { ++done; if (lane == 0) offer(qp, slot, iv.status, db, iv.ids[pb]); }
+                    else ++aband;
+                }
+                __syncwarp();
+                thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
+                mask &= __ballot_sync(0xffffffffu, lb <= thr);
             }
-            __syncwarp();
-            thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
-            mask &= __ballot_sync(0xffffffffu, lb <= thr);
         }
     }
     if (lane == 0) {
         if (done) atomicAdd(&st->c.refined, done);
         if (aband) atomicAdd(&st->c.abandoned, aband);
+        if (bytes) atomicAdd(&st->c.row_bytes, bytes);
     }
 }
 
@@ -827,7 +943,7 @@ k_fused_ed(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, un
         if (tid == 0)
             for (unsigned t = 0; t < nt && t < (unsigned)kFuStages; ++t) issue(t0 + t, (int)t);
         __syncthreads();
-        unsigned long long evals = 0, nsurv = 0, done = 0, aband = 0;
+        unsigned long long evals = 0, nsurv = 0, done = 0, aband = 0, bytes = 0;
         for (unsigned t = 0; t < nt; ++t) {
             const int sidx = t % kFuStages;
             const bool ok = mbar_wait_bounded(&bars[sidx], uses[sidx] & 1u);
@@ -885,13 +1001,16 @@ k_fused_ed(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, un
                 if (!ua && !ub) continue;
                 const unsigned pa = list_pos[e], pb = (e + 1 < n) ? list_pos[e + 1] : pa;
                 float da, db;
+                int na, nb;
                 warp_ed2_pair(qs, iv.raw + (unsigned long long)(ua ? pa : pb) * iv.len,
-                              iv.raw + (unsigned long long)pb * iv.len, iv.len, live, da, db);
+                              iv.raw + (unsigned long long)pb * iv.len, iv.len, live, da, db, na, nb);
                 if (ua) {
+                    bytes += 4ull * na;
                     if (da <= live) { ++done; if (lane == 0) offer(qp, slot, iv.status, da, iv.ids[pa]); }
                     else ++aband;
                 }
                 if (ub) {
+                    bytes += 4ull * nb;
                     if (db <= live) { ++done; if (lane == 0) offer(qp, slot, iv.status, db, iv.ids[pb]); }
                     else ++aband;
                 }
@@ -906,6 +1025,7 @@ k_fused_ed(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, un
         if (lane == 0) {
             if (done) atomicAdd(&st->c.refined, done);
             if (aband) atomicAdd(&st->c.abandoned, aband);
+            if (bytes) atomicAdd(&st->c.row_bytes, bytes);
         }
         __syncthreads();
     }
@@ -1455,6 +1575,7 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
             atomicAdd(&acc->bsf_updates, st->c.bsf_updates);
             atomicAdd(&acc->tie_rechecks, st->c.tie_rechecks);
             atomicAdd(&acc->leaves_live, st->c.leaves_live);
+            atomicAdd(&acc->row_bytes, st->c.row_bytes);
         }
         return;
     }
@@ -1535,6 +1656,7 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
         atomicAdd(&acc->bsf_updates, st->c.bsf_updates);
         atomicAdd(&acc->tie_rechecks, st->c.tie_rechecks);
         atomicAdd(&acc->leaves_live, st->c.leaves_live);
+        atomicAdd(&acc->row_bytes, st->c.row_bytes);
     }
 }
 
@@ -1597,6 +1719,8 @@ float band_factor(int dist, int len)
 void init_kernel_attributes()
 {
     cudaFuncSetAttribute(k_lb_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
+    // three CTAs of 72 KB each per SM: ask for the largest shared-memory carveout
+    cudaFuncSetAttribute(k_lb_scan, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinSmem);
     cudaFuncSetAttribute(k_finalize_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinSmem);
     cudaFuncSetAttribute(k_finalize_batch_args, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinSmem);
@@ -1647,9 +1771,8 @@ void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, c
                    unsigned long long *launches)
 {
     if (qp.dist == 0) {
-        launch_order(qp, slot, 0, slot.surv2, slot.surv2_lb, s);
         k_refine_ed<<<num_sms() * 8, 256, iv.len * 4, s>>>(iv, qp, slot);
-        if (launches) *launches += 4;
+        if (launches) *launches += 1;
     } else {
         if (!launch_lbk_thread(iv, qp, slot, s)) {
             // windows wider than the register forms: warp per candidate, per

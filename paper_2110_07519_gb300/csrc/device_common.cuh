@@ -241,6 +241,67 @@ __device__ __forceinline__ void warp_ed2_pair(const float *__restrict__ q, const
     db = warp_sum(ab);
 }
 
+// R rows at once (R row loads in flight per lane); same arithmetic as
+// warp_ed2 for each row.  A row with live[r] false on entry is not read (its
+// d[r] and n[r] are 0 and mean nothing).  A row whose running sum exceeds
+// thr after a 256-point chunk stops; d[r] is then that partial sum (> thr).
+// n[r] receives the points of row r read (whole 256-point chunks loaded
+// while it was live).
+template <int R>
+__device__ __forceinline__ void warp_ed2_rows(const float *__restrict__ q, const float *const (&x)[R], bool (&live)[R],
+                                              int len, float thr, float (&d)[R], int (&n)[R])
+{
+    const int lane = threadIdx.x & 31;
+    const int n4 = len >> 2;
+    const float4 *q4 = reinterpret_cast<const float4 *>(q);
+    float acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        acc[r] = 0.f;
+        n[r] = 0;
+    }
+    for (int base = 0; base < n4; base += 64) {
+        const int pts = min(256, 4 * (n4 - base));
+        float4 xv[R][2];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (live[r]) n[r] += pts;
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int i = base + lane + 32 * t;
+                xv[r][t] = (live[r] && i < n4) ? __ldg(reinterpret_cast<const float4 *>(x[r]) + i)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int i = base + lane + 32 * t;
+            if (i < n4) {
+                const float4 qv = q4[i];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float e;
+                    e = qv.x - xv[r][t].x; acc[r] = fmaf(e, e, acc[r]);
+                    e = qv.y - xv[r][t].y; acc[r] = fmaf(e, e, acc[r]);
+                    e = qv.z - xv[r][t].z; acc[r] = fmaf(e, e, acc[r]);
+                    e = qv.w - xv[r][t].w; acc[r] = fmaf(e, e, acc[r]);
+                }
+            }
+        }
+        if (base + 64 < n4 && thr < f_inf()) {
+            bool any = false;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (live[r] && warp_sum(acc[r]) > thr) live[r] = false;
+                any = any || live[r];
+            }
+            if (!any) break;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[r] = warp_sum(acc[r]);
+}
+
 // ------------------------------------------------------------------ DTW
 // Banded DTW of q and x (length n, reach r) by one warp, anti-diagonal
 // wavefront: cells (i, j) with i + j = a are independent; lane handles
@@ -322,9 +383,10 @@ __device__ T warp_dtw(const float *__restrict__ q, const float *__restrict__ x, 
 }
 
 // Survivors are stored in per-scan-CTA regions; a refine block turns the
-// region counts into a prefix over 32-entry chunks so warps can take chunks
-// by index.  Returns the number of chunks.
-__device__ __forceinline__ unsigned chunk_prefix(const QuerySlot &slot, unsigned G, unsigned *prefix, unsigned *counts)
+// region counts into a prefix over chunks of 2^shift entries (default 32) so
+// warps can take chunks by index.  Returns the number of chunks.
+__device__ __forceinline__ unsigned chunk_prefix(const QuerySlot &slot, unsigned G, unsigned *prefix, unsigned *counts,
+                                                 int shift = 5)
 {
     __shared__ unsigned part[32];
     const unsigned per = (G + blockDim.x - 1) / blockDim.x;
@@ -333,7 +395,7 @@ __device__ __forceinline__ unsigned chunk_prefix(const QuerySlot &slot, unsigned
     for (unsigned c = lo; c < hi; ++c) {
         const unsigned n = slot.region_count[c];
         counts[c] = n;
-        sum += (n + 31) >> 5;
+        sum += (n + (1u << shift) - 1u) >> shift;
     }
     // block-wide exclusive scan of the per-thread sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -359,7 +421,7 @@ __device__ __forceinline__ unsigned chunk_prefix(const QuerySlot &slot, unsigned
     unsigned run = (warp ? part[warp - 1] : 0u) + inc - sum;
     for (unsigned c = lo; c < hi; ++c) {
         prefix[c] = run;
-        run += (counts[c] + 31) >> 5;
+        run += (counts[c] + (1u << shift) - 1u) >> shift;
     }
     if (threadIdx.x == blockDim.x - 1) prefix[G] = run;
     __syncthreads();

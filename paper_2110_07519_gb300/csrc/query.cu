@@ -517,8 +517,11 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
     const ScanCodes sc = scan_codes(slot.lut, thrp, codes, red);
     __syncthreads();
     unsigned iter = 0;
+    unsigned tile_next = i0 < i1 ? slot.live_list[i0] : 0u;   // the next tile's number, loaded a tile ahead
     for (unsigned idx = i0; idx < i1; ++idx, ++iter) {
         if (__shfl_sync(0xffffffffu, *reinterpret_cast<volatile int *>(&timed_out), 0)) break;
+        const unsigned tile = tile_next;
+        if (idx + 1 < i1) tile_next = slot.live_list[idx + 1];
         const int s = iter % kScanStages;
         const unsigned parity = (iter / kScanStages) & 1u;
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[s], parity))) {
@@ -528,7 +531,7 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
             }
             break;
         }
-        const unsigned long long first = (unsigned long long)slot.live_list[idx] * kScanTileWords;
+        const unsigned long long first = (unsigned long long)tile * kScanTileWords;
         const unsigned cnt = (unsigned)min((unsigned long long)kScanTileWords, N - first);
 #pragma unroll
         for (int r = 0; r < kScanWpt; ++r) {
@@ -596,72 +599,153 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
 // 8), without sorting: the survivors stay in the scan's regions and the
 // kernel sweeps them in kRefineBands passes over bands of the lower bound,
 // band b holding bounds in [t (b / B)^2, t ((b + 1) / B)^2) of the scan's
-// threshold t (uniform in distance, finer where most survivors sit).  Every
-// warp finishes its share of band b before it starts band b + 1, and stops at
-// the first band whose floor lies above the live best-so-far.  A warp takes
-// 32 survivors at a time (one coalesced read of their positions and bounds;
-// the lists stay in L2 across bands), ballots those inside the band and
-// within the live threshold, then computes real distances two rows at a
-// time.  Exactness does not depend on the order, only the number of rows
-// read does.
-constexpr int kRefineBands = 8;
+// threshold t (uniform in distance).  Every warp finishes its share of band b
+// before it starts band b + 1, and stops at the first band whose floor lies
+// above the live best-so-far.  A warp owns a contiguous run of 128-entry
+// survivor chunks and reads it chunk by chunk (each lane four consecutive
+// positions and bounds by two 16-byte loads, the next chunk loaded while the
+// current one is used); it gathers the entries inside the band and within
+// the live threshold into a shared-memory buffer and, every 32 gathered,
+// computes their real distances four rows at a time, re-checking each bound
+// against the live threshold first.  Exactness does not depend on the order,
+// only the number of rows read does.
+constexpr int kRefineBands = 4;
+constexpr int kRefineThreads = 256;
+constexpr int kRefineRows = 4;
+constexpr int kRefineChunkShift = 7;   // 128-entry chunks
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kRefineThreads, 3)
 k_refine_ed(IndexView iv, QueryParams qp, QuerySlot slot)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ unsigned prefix[kMaxScanGrid + 1], counts[kMaxScanGrid];
+    __shared__ unsigned gpos[kRefineThreads / 32][160];
+    __shared__ float glb[kRefineThreads / 32][160];
     QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
     float *qs = reinterpret_cast<float *>(dsm);
     for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
     const unsigned G = st->scan_grid;
     const unsigned long long RW = st->region_words;
-    const unsigned nchunks = chunk_prefix(slot, G, prefix, counts);   // ends with a block barrier
-    const int lane = threadIdx.x & 31;
+    const unsigned nchunks = chunk_prefix(slot, G, prefix, counts, kRefineChunkShift);   // ends with a block barrier
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned *bpos = gpos[wib];
+    float *blb = glb[wib];
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    const unsigned wglob = blockIdx.x * (blockDim.x >> 5) + wib;
     const float t0 = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
     const int bands = t0 < f_inf() ? kRefineBands : 1;
     unsigned long long done = 0, aband = 0, bytes = 0;
+    // the live threshold, re-read after every group of rows (a stale value is
+    // only looser: it skips fewer rows, and offer() re-checks what it accepts)
+    float thr = t0;
+    // refine the first `cnt` gathered entries (cnt <= 32), four rows at a time
+    auto refine_buffered = [&](unsigned cnt) {
+        for (unsigned e0 = 0; e0 < cnt; e0 += kRefineRows) {
+            const float *x[kRefineRows];
+            bool live[kRefineRows], take[kRefineRows];
+            unsigned pos[kRefineRows];
+#pragma unroll
+            for (int r = 0; r < kRefineRows; ++r) {
+                const unsigned e = e0 + r;
+                take[r] = e < cnt && blb[e < cnt ? e : 0] <= thr;
+                pos[r] = take[r] ? bpos[e] : bpos[0];
+                x[r] = iv.raw + (unsigned long long)pos[r] * iv.len;
+                live[r] = take[r];
+            }
+            // issued behind the row loads, so its latency overlaps theirs
+            const unsigned long long T = ld_volatile_u64(&st->thr);
+            float d[kRefineRows];
+            int n[kRefineRows];
+            warp_ed2_rows<kRefineRows>(qs, x, live, iv.len, thr, d, n);
+#pragma unroll
+            for (int r = 0; r < kRefineRows; ++r) {
+                if (!take[r]) continue;
+                bytes += 4ull * n[r];
+                if (d[r] <= thr) {
+                    ++done;
+                    if (lane == 0) offer(qp, slot, iv.status, d[r], iv.ids[pos[r]]);
+                } else {
+                    ++aband;
+                }
+            }
+            __syncwarp();
+            thr = fminf(thr, prune_threshold(T, qp.F));
+        }
+    };
+    // the warp's chunks: one contiguous run [c_lo, c_hi)
+    const unsigned per = (nchunks + nw - 1) / nw;
+    const unsigned c_lo = min(nchunks, wglob * per), c_hi = min(nchunks, c_lo + per);
     for (int band = 0; band < bands; ++band) {
         const float flo = bands == 1 ? 0.f : t0 * ((float)(band * band) / (float)(kRefineBands * kRefineBands));
         const float fhi = band == bands - 1 ? f_inf()
                                             : t0 * ((float)((band + 1) * (band + 1)) / (float)(kRefineBands * kRefineBands));
-        if (flo > prune_threshold(ld_volatile_u64(&st->thr), qp.F)) break;   // every later band too
-        for (unsigned ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += nw) {
-            const unsigned rg = region_of(ch, prefix, G);
-            const unsigned within = (ch - prefix[rg]) * 32 + lane;
-            const bool valid = within < counts[rg];
-            const unsigned long long i = rg * RW + within;
-            const unsigned pos = valid ? slot.surv_pos[i] : 0u;
-            const float lb = valid ? slot.surv_lb[i] : f_inf();
-            const bool in_band = lb >= flo && lb < fhi;
-            float thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
-            unsigned mask = __ballot_sync(0xffffffffu, valid && in_band && lb <= thr);
-            while (mask) {
-                const int a = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const int b = mask ? __ffs(mask) - 1 : -1;
-                if (b >= 0) mask &= mask - 1;
-                const unsigned pa = __shfl_sync(0xffffffffu, pos, a);
-                const unsigned pb = __shfl_sync(0xffffffffu, pos, b >= 0 ? b : a);
-                float da, db;
-                int na, nb;
-                warp_ed2_pair(qs, iv.raw + (unsigned long long)pa * iv.len, iv.raw + (unsigned long long)pb * iv.len,
-                              iv.len, thr, da, db, na, nb);
-                bytes += 4ull * na;
-                if (da <= thr) { ++done; if (lane == 0) offer(qp, slot, iv.status, da, iv.ids[pa]); }
-                else ++aband;
-                if (b >= 0) {
-                    bytes += 4ull * nb;
-                    if (db <= thr) { ++done; if (lane == 0) offer(qp, slot, iv.status, db, iv.ids[pb]); }
-                    else ++aband;
+        thr = fminf(thr, prune_threshold(ld_volatile_u64(&st->thr), qp.F));
+        if (flo > thr) break;   // every later band too
+        unsigned nbuf = 0;      // warp-uniform
+        // a chunk's region advances by at most a step or two from the
+        // previous chunk's; lane l holds entries 4l .. 4l+3 of the chunk
+        unsigned rg = c_lo < c_hi ? region_of(c_lo, prefix, G) : 0u;
+        auto load = [&](unsigned ch, uint4 &pos, float4 &lb, unsigned &nvalid) {
+            while (rg + 1 < G && prefix[rg + 1] <= ch) ++rg;
+            const unsigned first = (ch - prefix[rg]) << kRefineChunkShift;
+            nvalid = min(counts[rg] - first, 128u);
+            const unsigned long long i = rg * RW + first + 4 * lane;   // 16-byte aligned
+            if (4u * lane < nvalid) {
+                pos = *reinterpret_cast<const uint4 *>(slot.surv_pos + i);
+                lb = *reinterpret_cast<const float4 *>(slot.surv_lb + i);
+            } else {
+                pos = make_uint4(0, 0, 0, 0);
+                lb = make_float4(f_inf(), f_inf(), f_inf(), f_inf());
+            }
+        };
+        uint4 npos = make_uint4(0, 0, 0, 0);
+        float4 nlb = make_float4(f_inf(), f_inf(), f_inf(), f_inf());
+        unsigned nv = 0;
+        if (c_lo < c_hi) load(c_lo, npos, nlb, nv);
+        for (unsigned ch = c_lo; ch < c_hi; ++ch) {
+            const uint4 cpos = npos;
+            const float4 clb = nlb;
+            const unsigned cnv = nv;
+            if (ch + 1 < c_hi) load(ch + 1, npos, nlb, nv);
+            const unsigned pp[4] = {cpos.x, cpos.y, cpos.z, cpos.w};
+            const float ll[4] = {clb.x, clb.y, clb.z, clb.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float lb = ll[k];
+                const bool keep = 4u * lane + k < cnv && lb >= flo && lb < fhi && lb <= thr;
+                const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const unsigned o = nbuf + __popc(ballot & ((1u << lane) - 1u));
+                    bpos[o] = pp[k];
+                    blb[o] = lb;
                 }
-                __syncwarp();
-                thr = prune_threshold(ld_volatile_u64(&st->thr), qp.F);
-                mask &= __ballot_sync(0xffffffffu, lb <= thr);
+                nbuf += __popc(ballot);
+            }
+            __syncwarp();
+            while (nbuf >= 32) {
+                refine_buffered(32);
+                // move the rest (at most 127) to the front
+                const unsigned rest = nbuf - 32;
+                for (unsigned j = 0; j < rest; j += 32) {
+                    unsigned p2 = 0;
+                    float l2 = 0.f;
+                    if (j + lane < rest) {
+                        p2 = bpos[32 + j + lane];
+                        l2 = blb[32 + j + lane];
+                    }
+                    __syncwarp();
+                    if (j + lane < rest) {
+                        bpos[j + lane] = p2;
+                        blb[j + lane] = l2;
+                    }
+                    __syncwarp();
+                }
+                nbuf = rest;
             }
         }
+        if (nbuf) refine_buffered(nbuf);
+        __syncwarp();
     }
     if (lane == 0) {
         if (done) atomicAdd(&st->c.refined, done);
@@ -1771,7 +1855,7 @@ void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, c
                    unsigned long long *launches)
 {
     if (qp.dist == 0) {
-        k_refine_ed<<<num_sms() * 8, 256, iv.len * 4, s>>>(iv, qp, slot);
+        k_refine_ed<<<num_sms() * 3, kRefineThreads, iv.len * 4, s>>>(iv, qp, slot);   // one wave: 3 blocks per SM
         if (launches) *launches += 1;
     } else {
         if (!launch_lbk_thread(iv, qp, slot, s)) {

@@ -45,7 +45,7 @@ constexpr int kScanTileWords = kScanThreads * kScanWpt;   // 1024 words, 16 KB
 static_assert(kScanTileWords == kScanTileWordsHost, "scan tile size shared with the workspace layout");
 constexpr int kScanStages = 4;
 constexpr int kScanCtasPerSm = 3;
-constexpr int kScanSmem = kScanStages * kScanTileWords * 16 + kMaxSegments * kMaxCard * 2;   // 72 KB
+constexpr int kScanSmem = kScanStages * kScanTileWords * 16;   // 64 KB ring (+ 8 KB static code table)
 constexpr int kFinThreads = 1024;
 
 // ------------------------------------------------------------------ prep
@@ -67,8 +67,28 @@ __device__ __forceinline__ double gap_rd(double edge, double p)   // edge - p, e
     return d > 0.0 ? d : 0.0;
 }
 
+// Table entry (s, v): m * d^2, d the distance from the query's segment-s
+// value (ED: PAA; DTW: PAA of U below the region, of L above it) to region v,
+// every step rounded toward -inf; 0 beyond the index's segments and symbols.
+__device__ __forceinline__ float table_entry(int s, int v, int w, int card, int m, int dist, double p, double pu,
+                                             double pl, const double *sbeta)
+{
+    if (s >= w || v >= card) return 0.f;
+    const double lo = region_lo(v, sbeta), hi = region_hi(v, card, sbeta);
+    double d = 0.0;
+    if (dist == 0) {
+        if (p < lo) d = gap_rd(lo, p);
+        else if (p > hi) d = gap_rd(p, hi);
+    } else {
+        if (pu < lo) d = gap_rd(lo, pu);            // ABOVE
+        else if (pl > hi) d = gap_rd(pl, hi);       // BELOW
+    }
+    return __double2float_rd(__dmul_rd(__dmul_rd(d, d), (double)m));
+}
+
+// with_table = false leaves the table to k_prep's other blocks (one row each)
 __device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot,
-                                          const float *__restrict__ query)
+                                          const float *__restrict__ query, bool with_table = true)
 {
     __shared__ double paa[kMaxSegments], paaU[kMaxSegments], paaL[kMaxSegments];
     __shared__ int sym[kMaxSegments];
@@ -140,23 +160,11 @@ __device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams
     }
     __syncthreads();
     // table: T[s][v] = m * d^2, every step rounded toward -inf
-    for (int e = tid; e < kMaxSegments * kMaxCard; e += blockDim.x) {
-        const int s = e / kMaxCard, v = e % kMaxCard;
-        float out = 0.f;
-        if (s < w && v < card) {
-            const double lo = region_lo(v, sbeta), hi = region_hi(v, card, sbeta);
-            double d = 0.0;
-            if (qp.dist == 0) {
-                if (paa[s] < lo) d = gap_rd(lo, paa[s]);
-                else if (paa[s] > hi) d = gap_rd(paa[s], hi);
-            } else {
-                if (paaU[s] < lo) d = gap_rd(lo, paaU[s]);            // ABOVE
-                else if (paaL[s] > hi) d = gap_rd(paaL[s], hi);       // BELOW
-            }
-            out = __double2float_rd(__dmul_rd(__dmul_rd(d, d), (double)m));
+    if (with_table)
+        for (int e = tid; e < kMaxSegments * kMaxCard; e += blockDim.x) {
+            const int s = e / kMaxCard, v = e % kMaxCard;
+            slot.lut[e] = s < w ? table_entry(s, v, w, card, m, qp.dist, paa[s], paaU[s], paaL[s], sbeta) : 0.f;
         }
-        slot.lut[e] = out;
-    }
     if (tid == 0) {
         // interleaved key of the query word
         unsigned long long khi = 0ull, klo = 0ull;
@@ -202,10 +210,60 @@ __device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams
     }
 }
 
+// One row of the table (segment s, 256 symbols, one per thread): the row's
+// FP64 work spread over its own block, since FP64 throughput per SM is low.
+// The segment's PAA (ED) or PAAs of the envelope (DTW) are recomputed here in
+// the same order as prep_body's.
+__device__ __forceinline__ void prep_table_row(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot,
+                                               const float *__restrict__ query, int s)
+{
+    __shared__ double sbeta[kMaxCard];
+    __shared__ double ps, psu, psl;
+    const int tid = threadIdx.x;
+    const int len = iv.len, w = iv.w, m = iv.m, card = iv.card;
+    if (s >= w) {
+        for (int v = tid; v < kMaxCard; v += blockDim.x) slot.lut[s * kMaxCard + v] = 0.f;
+        return;
+    }
+    __shared__ float up_pts[kMaxLen], dn_pts[kMaxLen];
+    for (int i = tid; i < kMaxCard; i += blockDim.x) sbeta[i] = i < card - 1 ? iv.beta64[i] : 0.0;
+    if (qp.dist == 1)   // the LB_Keogh envelope on the segment, window clipped at the ends
+        for (int i = tid; i < m; i += blockDim.x) {
+            const int t = s * m + i, lo = max(0, t - qp.r), hi = min(len - 1, t + qp.r);
+            float up = query[lo], dn = query[lo];
+            for (int j = lo + 1; j <= hi; ++j) {
+                up = fmaxf(up, query[j]);
+                dn = fminf(dn, query[j]);
+            }
+            up_pts[i] = up;
+            dn_pts[i] = dn;
+        }
+    __syncthreads();
+    if (tid == 0) {   // sequential FP64 sums, in prep_body's order
+        double a = 0.0, au = 0.0, al = 0.0;
+        for (int i = 0; i < m; ++i) {
+            a = __dadd_rn(a, (double)query[s * m + i]);
+            if (qp.dist == 1) {
+                au = __dadd_rn(au, (double)up_pts[i]);
+                al = __dadd_rn(al, (double)dn_pts[i]);
+            }
+        }
+        ps = __ddiv_rn(a, (double)m);
+        psu = __ddiv_rn(au, (double)m);
+        psl = __ddiv_rn(al, (double)m);
+    }
+    __syncthreads();
+    for (int v = tid; v < kMaxCard; v += blockDim.x)
+        slot.lut[s * kMaxCard + v] = table_entry(s, v, w, card, m, qp.dist, ps, psu, psl, sbeta);
+}
+
+// Block 0: query state, PAA, symbols, key and seed range; blocks 1..16: one
+// row of the table each.
 __global__ void __launch_bounds__(kPrepThreads)
 k_prep(IndexView iv, QueryParams qp, QuerySlot slot, const float *__restrict__ query)
 {
-    prep_body(iv, qp, slot, query);
+    if (blockIdx.x == 0) prep_body(iv, qp, slot, query, false);
+    else prep_table_row(iv, qp, slot, query, (int)blockIdx.x - 1);
 }
 
 // one block per query of a batch
@@ -449,13 +507,15 @@ __device__ __forceinline__ ScanCodes scan_codes(const float *__restrict__ lut, f
 }
 
 // code sum of the 8 segments held in two 32-bit words starting at segment s0
+// (symbol b of a word taken by one byte permute; the table sits in static
+// shared memory, so its base folds into the loads' address offsets)
 __device__ __forceinline__ unsigned code_half(unsigned w0, unsigned w1, const unsigned short *codes, int s0)
 {
     unsigned v[8];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) v[b] = codes[(s0 + b) * kMaxCard + ((w0 >> (8 * b)) & 0xffu)];
+    for (int b = 0; b < 4; ++b) v[b] = codes[(s0 + b) * kMaxCard + __byte_perm(w0, 0u, 0x4440u + b)];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) v[4 + b] = codes[(s0 + 4 + b) * kMaxCard + ((w1 >> (8 * b)) & 0xffu)];
+    for (int b = 0; b < 4; ++b) v[4 + b] = codes[(s0 + 4 + b) * kMaxCard + __byte_perm(w1, 0u, 0x4440u + b)];
     return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
 }
 
@@ -476,8 +536,8 @@ k_lb_scan(IndexView iv, QueryParams qp, QuerySlot slot)
     __shared__ int timed_out;
     __shared__ unsigned s_count;
     __shared__ float red[32];
+    __shared__ __align__(16) unsigned short codes[kMaxSegments * kMaxCard];
     uint4 *stage = reinterpret_cast<uint4 *>(smem);
-    unsigned short *codes = reinterpret_cast<unsigned short *>(smem + kScanStages * kScanTileWords * 16);
     QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -1551,12 +1611,13 @@ __device__ void fin_streamed(const IndexView &iv, const QueryParams &qp, const Q
         }
         __syncthreads();
         fin_sort64(cand, d64, npow);
-        // the window's best k distinct rows (a row logged twice sorts next to
-        // itself: compare with the last one kept), moved to the front in place
+        // the window's best k distinct rows (a row logged twice has one FP64
+        // distance, so it sorts next to itself whatever its FP32 keys: compare
+        // ids with the last one kept), moved to the front in place
         if (tid == 0) {
             unsigned out = 0;
             for (unsigned i = 0; i < c && out < k; ++i) {
-                if (out > 0 && cand[i] == cand[out - 1]) continue;
+                if (out > 0 && cand_id(cand[i]) == cand_id(cand[out - 1])) continue;
                 cand[out] = cand[i];
                 d64[out] = d64[i];
                 ++out;
@@ -1581,7 +1642,7 @@ __device__ void fin_streamed(const IndexView &iv, const QueryParams &qp, const Q
         if (tid == 0) {
             unsigned out = 0;
             for (unsigned i = 0; i < tot && out < k; ++i) {
-                if (i > 0 && cand[i] == cand[i - 1]) continue;   // the same row logged twice
+                if (i > 0 && cand_id(cand[i]) == cand_id(cand[i - 1])) continue;   // the same row logged twice
                 rp[out] = cand[i];
                 rd[out] = d64[i];
                 ++out;
@@ -1667,42 +1728,31 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
     unsigned npow = 1;
     while (npow < c) npow <<= 1;
     for (unsigned i = c + tid; i < npow; i += blockDim.x) cand[i] = kEmpty;
-    __syncthreads();
-    block_bitonic(
-        npow, [&](unsigned i, unsigned j) { return cand[i] < cand[j]; },
-        [&](unsigned i, unsigned j) {
-            const unsigned long long t = cand[i];
-            cand[i] = cand[j];
-            cand[j] = t;
-        });
     // the same row may have been offered more than once (screened batches
-    // re-offer rows); equal packed entries are the same row: keep one
-    __shared__ int dup;
-    if (tid == 0) dup = 0;
+    // re-offer rows), possibly under two FP32 keys: ordered by (id, distance)
+    // the entries of one row sit together, the smallest first; keep that one,
+    // then order the rest by (distance, id)
+    __shared__ unsigned nuniq;
+    if (tid == 0) nuniq = 0;
     __syncthreads();
+    auto by_id = [](unsigned long long P) { return (P << 32) | (P >> 32); };
+    auto swap_cand = [&](unsigned i, unsigned j) {
+        const unsigned long long t = cand[i];
+        cand[i] = cand[j];
+        cand[j] = t;
+    };
+    block_bitonic(npow, [&](unsigned i, unsigned j) { return by_id(cand[i]) < by_id(cand[j]); }, swap_cand);
     unsigned long long *mark = reinterpret_cast<unsigned long long *>(d64);
-    for (unsigned i = tid; i < npow; i += blockDim.x) mark[i] = (i > 0 && i < c && cand[i] == cand[i - 1]) ? 1ull : 0ull;
-    __syncthreads();
     for (unsigned i = tid; i < npow; i += blockDim.x)
-        if (mark[i]) { cand[i] = kEmpty; dup = 1; }
+        mark[i] = (i > 0 && i < c && cand_id(cand[i]) == cand_id(cand[i - 1])) ? 1ull : 0ull;
     __syncthreads();
-    unsigned c_eff = c;
-    if (dup) {
-        block_bitonic(
-            npow, [&](unsigned i, unsigned j) { return cand[i] < cand[j]; },
-            [&](unsigned i, unsigned j) {
-                const unsigned long long t = cand[i];
-                cand[i] = cand[j];
-                cand[j] = t;
-            });
-        __shared__ unsigned nuniq;
-        if (tid == 0) nuniq = 0;
-        __syncthreads();
-        for (unsigned i = tid; i < c; i += blockDim.x)
-            if (cand[i] != kEmpty) atomicAdd(&nuniq, 1u);
-        __syncthreads();
-        c_eff = nuniq;
+    for (unsigned i = tid; i < npow; i += blockDim.x) {
+        if (mark[i]) cand[i] = kEmpty;
+        else if (i < c) atomicAdd(&nuniq, 1u);
     }
+    __syncthreads();
+    block_bitonic(npow, [&](unsigned i, unsigned j) { return cand[i] < cand[j]; }, swap_cand);
+    const unsigned c_eff = nuniq;
     const unsigned cu = c_eff;
     // ambiguity: a candidate beyond the k-th inside the band, or two of the
     // first k within the band of each other (their order is not certain)
@@ -1818,7 +1868,7 @@ void init_kernel_attributes()
 void launch_prep(const IndexView &iv, const QueryParams &qp, QuerySlot slot, const float *query,
                  cudaStream_t s)
 {
-    k_prep<<<1, kPrepThreads, 0, s>>>(iv, qp, slot, query);
+    k_prep<<<1 + kMaxSegments, kPrepThreads, 0, s>>>(iv, qp, slot, query);
 }
 
 void launch_seed(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s,

@@ -4,8 +4,9 @@ CPU.
 When more candidates lie in the near-tie band than one pass holds, the log is
 taken window by window: a window's in-band entries are ranked by (FP64
 distance, id), its best k distinct rows are kept (the log may hold a row
-twice: screened batches re-offer rows), and they are merged with the running
-top-k, again keeping distinct rows.  Restated here with small windows, that
+twice, even under two FP32 keys: screened batches re-offer rows, and rows
+are told apart by id), and they are merged with the running top-k, again
+keeping distinct rows.  Restated here with small windows, that
 must equal ranking every distinct in-band row at once -- with duplicates
 placed anywhere, mass ties in the FP64 distance, and k from 1 to beyond a
 window."""
@@ -22,7 +23,7 @@ def windowed(log, band, d64, k, W):
         for P in win:
             if len(best) == k:
                 break
-            if best and P == best[-1]:
+            if best and P[1] == best[-1][1]:      # the same row (its id), whatever its FP32 key
                 continue
             best.append(P)
         merged = sorted(best + running, key=lambda P: (d64[P[1]], P[1]))
@@ -30,15 +31,15 @@ def windowed(log, band, d64, k, W):
         for i, P in enumerate(merged):
             if len(running) == k:
                 break
-            if i > 0 and P == merged[i - 1]:
+            if i > 0 and P[1] == merged[i - 1][1]:
                 continue
             running.append(P)
     return [P[1] for P in running]
 
 
 def reference(log, band, d64, k):
-    rows = sorted({P for P in log if P[0] <= band}, key=lambda P: (d64[P[1]], P[1]))
-    return [P[1] for P in rows[:k]]
+    ids = sorted({P[1] for P in log if P[0] <= band}, key=lambda i: (d64[i], i))
+    return ids[:k]
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 5, 8, 20])
@@ -52,6 +53,11 @@ def test_windowed_ranking_equals_global_ranking(k, W):
         d64 = {int(i): float(rng.integers(0, 6)) + (0.0 if trial % 2 else float(rng.random())) for i in ids}
         rows = [(np.float32(d64[int(i)]).item(), int(i)) for i in ids]
         log = rows + [rows[j] for j in rng.integers(0, n, size=int(rng.integers(0, 2 * n)))]   # duplicates
+        # the same row logged again under a different FP32 key (one ulp off),
+        # as a differently ordered FP32 evaluation could give
+        for j in rng.integers(0, n, size=int(rng.integers(0, n // 2 + 1))):
+            key, rid = rows[j]
+            log.append((float(np.nextafter(np.float32(key), np.float32(np.inf))), rid))
         order = rng.permutation(len(log))
         log = [log[j] for j in order]
         band = float(rng.uniform(0, 6))

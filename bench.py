@@ -123,6 +123,17 @@ def measured_peak_tensor():
         return 1700.0, "fallback"
 
 
+def derived_peak_fp32():
+    """Plain FP32 arithmetic rate (no measured figure exists): 152 SMs x 128
+    FP32 lanes x 2 operations per fused multiply-add x the maximum SM clock."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        mhz = 2070.0
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12, f"derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x {mhz:.0f} MHz"
+
+
 def measured_peak_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -289,7 +300,8 @@ def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists, dist=
     clocks = ClockSampler(dev.index or 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     agg = {"kern_ms": 0.0, "kern_launches": 0, "launches": 0, "survivors": 0, "rows": 0, "words": 0, "lat": [],
-           "screened": 0, "row_bytes": 0, "bsf_updates": 0}
+           "screened": 0, "row_bytes": 0, "bsf_updates": 0, "refine_ms": 0.0, "refine_launches": 0,
+           "dtw_cells": 0}
     torch.cuda.synchronize()
     e0.record(stream)
     for s in range(W, W + K):
@@ -304,6 +316,9 @@ def time_form(m, ix, qpool, form, B, K, W, k, stream, pg, dev, ids, dists, dist=
         agg["words"] += st["lb_evaluated"]
         agg["row_bytes"] += st["row_bytes"]
         agg["bsf_updates"] += st["bsf_updates"]
+        agg["refine_ms"] += st["refine_ms"]
+        agg["refine_launches"] += st["refine_launches"]
+        agg["dtw_cells"] += st["dtw_cells"]
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -411,7 +426,30 @@ def run_messi(args, ws, rank, local):
         kern_avg_s = r["kern_ms"] * 1e-3 / max(r["kern_launches"], 1)
         n_leaves = m.messi_index_get_info(ix)["n_leaves"]
         ntiles = (args.n + 1023) // 1024
-        if form == "plain":
+        refine = None
+        if r["refine_launches"]:
+            rs = r["refine_ms"] * 1e-3
+            if dist_code == 1:
+                # banded DTW: 5 FP32 operations per band cell (difference, square,
+                # add, two minima) over the cells the recurrence evaluated
+                fpk, fkind = derived_peak_fp32()
+                refine = {"kernel": "k_dtw_thread", "bound": "alu", "cells": r["dtw_cells"],
+                          "achieved": 5.0 * r["dtw_cells"] / rs / 1e12, "peak": fpk, "unit": "TFLOP/s",
+                          "frac": 5.0 * r["dtw_cells"] / rs / 1e12 / fpk, "peak_kind": fkind,
+                          "avg_launch_ms": r["refine_ms"] / r["refine_launches"], "launches": r["refine_launches"]}
+            else:
+                # ED refinement: raw-row bytes read plus the survivor lists (8 B each)
+                rb = r["row_bytes"] + 8.0 * r["survivors"]
+                refine = {"kernel": "k_refine_ed", "bound": "hbm", "achieved": rb / rs / 1e9, "peak": peak,
+                          "unit": "GB/s", "frac": rb / rs / 1e9 / peak, "peak_kind": peak_kind,
+                          "avg_launch_ms": r["refine_ms"] / r["refine_launches"], "launches": r["refine_launches"]}
+        if form == "plain" and dist_code == 1 and refine:
+            # DTW per query: the banded DTW kernel (FP32 arithmetic bound)
+            kernel = "k_dtw_thread"
+            algo = 5.0 * r["dtw_cells"] / r["refine_launches"]
+            kern_avg_s = r["refine_ms"] * 1e-3 / r["refine_launches"]
+            roof = {k_: v for k_, v in refine.items() if k_ not in ("kernel", "cells", "avg_launch_ms", "launches")}
+        elif form == "plain":
             # the timed scan group: leaf boxes + leaf offsets (40 B per leaf), the
             # tile stamps (4 B per tile), and 16 B per word of the live tiles
             kernel = "k_lb_scan"
@@ -419,6 +457,12 @@ def run_messi(args, ws, rank, local):
             roof = {"bound": "hbm", "achieved": algo / kern_avg_s / 1e9, "peak": peak, "unit": "GB/s",
                     "frac": algo / kern_avg_s / 1e9 / peak, "peak_kind": peak_kind,
                     "timed": "k_leaf_prune + k_live_tiles + k_lb_scan per query"}
+        elif dist_code == 1 and refine:
+            # batched DTW: the banded DTW kernel of the overlapped per-query sequences
+            kernel = "k_dtw_thread"
+            algo = 5.0 * r["dtw_cells"] / r["refine_launches"]
+            kern_avg_s = r["refine_ms"] * 1e-3 / r["refine_launches"]
+            roof = {k_: v for k_, v in refine.items() if k_ not in ("kernel", "cells", "avg_launch_ms", "launches")}
         elif batch_mode == "tc_screen":
             # the screen's dense work: 2 * len flops per (series, query) pair, for every
             # query of every launch (a first pass screens the batch, a later one only
@@ -433,7 +477,7 @@ def run_messi(args, ws, rank, local):
             algo = 16.0 * args.n + 4.0 * args.len * r["rows"] / max(r["kern_launches"], 1)
             roof = {"bound": "hbm", "achieved": algo / kern_avg_s / 1e9, "peak": peak, "unit": "GB/s",
                     "frac": algo / kern_avg_s / 1e9 / peak, "peak_kind": peak_kind}
-        if form == "plain":
+        if form == "plain" or dist_code == 1:
             # bytes one query moves: leaf boxes and offsets, tile stamps, the
             # words of its live tiles, its survivor list (written once, read by
             # the refinement) and the raw-row bytes its refinement read
@@ -450,10 +494,12 @@ def run_messi(args, ws, rank, local):
             "p50_ms": r["p50"], "p99_ms": r["p99"], "gpu_launches": r["launches"], "clocks": r["clocks"],
             "roofline": dict(roof, kernel=kernel, algorithmic_per_launch=algo, avg_launch_ms=kern_avg_s * 1e3,
                              launches=r["kern_launches"]),
+            **({"refine": refine} if refine else {}),
             "counters": {"lb_survivors_per_query": r["survivors"] / nqt, "rows_read_per_query": r["rows"] / nqt,
                          "row_bytes_per_query": r["row_bytes"] / nqt,
                          "words_scanned_per_query": r["words"] / nqt,
-                         "bsf_updates_per_query": r["bsf_updates"] / nqt},
+                         "bsf_updates_per_query": r["bsf_updates"] / nqt,
+                         **({"dtw_cells_per_query": r["dtw_cells"] / nqt} if dist_code == 1 else {})},
             "query_roofline_frac": q_bytes / (r["elapsed_ms"] * 1e-3 / nqt) / 1e9 / peak,
             **({"tuning": tuning} if tuning and form == "batched" else {}),
         }

@@ -83,7 +83,12 @@ typedef struct {
                                   (a query screened again counts again)      */
     uint64_t row_bytes;       /* ED refinement: bytes of raw rows read (whole
                                   256-point chunks up to an early abandon)   */
-    uint64_t reserved[3];
+    uint64_t dtw_cells;       /* DTW: band cells computed, (2r + 1) per row of
+                                  the recurrence evaluated (up to an abandon) */
+    double refine_ms;         /* summed durations of the final refinement
+                                  kernel (ED refine / banded DTW), CUDA events
+                                  (profiling level >= 1, per-query path)      */
+    uint64_t refine_launches;
 } messi_stats;
 
 typedef struct {
@@ -184,7 +189,10 @@ messi_status messi_query(const messi_index *ix, const float *queries, uint32_t n
  * more accepted near-ties than a batch slot logs) is answered again by the
  * per-query kernels, so results equal messi_query's.  Both modes synchronise
  * `stream` (they read per-batch outcomes on the host).
- * DTW queries are answered by the per-query kernels. */
+ * DTW (either mode): the queries' per-query kernel sequences run side by side
+ * on up to 4 streams of the library, each with its own workspace (24 bytes
+ * per series each), so the small grids of one query share the GPU with the
+ * others'; the call waits for them on `stream` and synchronises it. */
 messi_status messi_query_batched(const messi_index *ix, const float *queries, uint32_t nq,
                                  uint32_t k, messi_dist dist, uint32_t window, uint32_t batch,
                                  int64_t *ids, float *dists, messi_stream stream);
@@ -279,7 +287,9 @@ messi_status messi_debug_set_lock_fault(messi_index *ix, uint32_t spin_limit, in
 /* Profiling level, reported by messi_query_stats.  0 (default): off.
  * 1: CUDA events around every lower-bound scan group (per-query path), every
  * screen launch (screened batch) and every fused launch (lower-bound batch
- * form) -- scan_ms / scan_launches.  2: also around every query (per-query
+ * form) -- scan_ms / scan_launches -- and around every final refinement
+ * kernel of the per-query path (also for batched DTW) -- refine_ms /
+ * refine_launches.  2: also around every query (per-query
  * path) or batch (batched forms) -- query_ms_p50 / p99.  Events are recorded
  * on the call's stream.  Any level above 0 turns off the graph replay of the
  * lower-bound batch form.  EINVAL for other levels. */
@@ -313,8 +323,8 @@ messi_status messi_breakpoints(uint32_t cardinality, double *out);
  * threads, one per CUDA stream, admit them into device batches in arrival
  * order while the device memory charged to unfinished requests stays within
  * mem_budget (a request is admitted beyond it only when nothing else is in
- * flight), run each batch (ED: messi_query_batched kernels; DTW: the
- * per-query kernels) with k = the largest k of the batch, and give every
+ * flight), run each batch through messi_query_batched's forms with k = the
+ * largest k of the batch, and give every
  * request the first k of its row.  Batches on different streams overlap on
  * the device.  A request's result does not depend on what else is in flight:
  * the answer is exact and a k-NN answer is a prefix of any larger k.

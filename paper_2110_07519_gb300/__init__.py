@@ -44,7 +44,7 @@ class MessiStats(ctypes.Structure):
         "bsf_updates", "tie_rechecks", "kernel_launches", "scan_launches")] + [
         ("scan_ms", ctypes.c_double), ("query_ms_p50", ctypes.c_double), ("query_ms_p99", ctypes.c_double),
         ("leaves_live", ctypes.c_uint64), ("screened_queries", ctypes.c_uint64), ("row_bytes", ctypes.c_uint64),
-        ("reserved", ctypes.c_uint64 * 3)]
+        ("dtw_cells", ctypes.c_uint64), ("refine_ms", ctypes.c_double), ("refine_launches", ctypes.c_uint64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}

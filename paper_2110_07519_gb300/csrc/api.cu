@@ -379,6 +379,14 @@ void free_workspace(Workspace &w)
     if (w.gargs_done) cudaEventDestroy(w.gargs_done);
     if (w.capture_stream) cudaStreamDestroy(w.capture_stream);
     for (cudaEvent_t e : w.ev_pool) cudaEventDestroy(e);
+    for (Workspace *sw : w.sub) {
+        if (!sw) continue;
+        free_workspace(*sw);
+        delete sw;
+    }
+    for (cudaStream_t t : w.sub_streams) cudaStreamDestroy(t);
+    for (cudaEvent_t e : w.sub_done) cudaEventDestroy(e);
+    if (w.fork) cudaEventDestroy(w.fork);
     w = Workspace{};
 }
 
@@ -582,6 +590,50 @@ static messi_status query_args(const messi_index *ix, const float *queries, uint
     return check_device(ix, ptrs, 3, "messi_query");
 }
 
+// The per-query kernel sequence of one query on stream s and slot workspace
+// qws; profiling events (ix->profiling) are recorded on s and registered in
+// ews, the workspace whose statistics the call reports.
+static cudaError_t enqueue_query(messi_index *ix, Workspace *qws, Workspace *ews, const IndexView &iv,
+                                 const QueryParams &qp, const float *q, long long *ids, float *dists, cudaStream_t s,
+                                 size_t &evn)
+{
+    const QuerySlot slot = qws->slot;
+    int eq0 = -1, es0 = -1;
+    if (ix->profiling >= 2) {
+        eq0 = (int)evn;
+        cudaEventRecord(pool_event(ews, evn++), s);
+    }
+    launch_prep(iv, qp, slot, q, s);
+    if (ix->hold_lock) {   // test hook: the k-array lock starts out held
+        const cudaError_t e = cudaMemsetAsync(&slot.st->lock, 0xff, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
+    launch_seed(iv, qp, slot, s, &ews->launches);
+    if (ix->profiling) {
+        es0 = (int)evn;
+        cudaEventRecord(pool_event(ews, evn++), s);
+    }
+    launch_scan(iv, qp, slot, next_epoch(qws, s), s);
+    if (ix->profiling) {
+        cudaEventRecord(pool_event(ews, evn++), s);
+        ews->scan_ev.push_back({es0, es0 + 1});
+    }
+    cudaEvent_t r0 = nullptr, r1 = nullptr;
+    if (ix->profiling) {
+        ews->refine_ev.push_back({(int)evn, (int)evn + 1});
+        r0 = pool_event(ews, evn++);
+        r1 = pool_event(ews, evn++);
+    }
+    launch_refine(iv, qp, slot, s, &ews->launches, r0, r1);
+    launch_finalize(iv, qp, slot, ids, dists, s);
+    ews->launches += 3;
+    if (ix->profiling >= 2) {
+        cudaEventRecord(pool_event(ews, evn++), s);
+        ews->query_ev.push_back({eq0, (int)evn - 1});
+    }
+    return cudaGetLastError();
+}
+
 messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uint32_t nq, uint32_t k,
                        messi_dist dist, uint32_t window, int64_t *ids, float *dists, messi_stream stream)
 {
@@ -615,34 +667,11 @@ messi_status run_plain(messi_index *ix, Workspace *ws, const float *queries, uin
     const unsigned long long launches0 = ws->launches;
     ws->scan_ev.clear();
     ws->query_ev.clear();
+    ws->refine_ev.clear();
     size_t evn = 0;
-    for (uint32_t qi = 0; qi < nq; ++qi) {
-        int eq0 = -1, es0 = -1;
-        if (ix->profiling >= 2) {
-            eq0 = (int)evn;
-            cudaEventRecord(pool_event(ws, evn++), s);
-        }
-        launch_prep(iv, qp, slot, dq + (size_t)qi * ix->len, s);
-        if (ix->hold_lock)   // test hook: the k-array lock starts out held
-            MESSI_CUDA(cudaMemsetAsync(&slot.st->lock, 0xff, sizeof(unsigned), s));
-        launch_seed(iv, qp, slot, s, &ws->launches);
-        if (ix->profiling) {
-            es0 = (int)evn;
-            cudaEventRecord(pool_event(ws, evn++), s);
-        }
-        launch_scan(iv, qp, slot, next_epoch(ws, s), s);
-        if (ix->profiling) {
-            cudaEventRecord(pool_event(ws, evn++), s);
-            ws->scan_ev.push_back({es0, es0 + 1});
-        }
-        launch_refine(iv, qp, slot, s, &ws->launches);
-        launch_finalize(iv, qp, slot, did + (size_t)qi * k, ddist + (size_t)qi * k, s);
-        ws->launches += 3;
-        if (ix->profiling >= 2) {
-            cudaEventRecord(pool_event(ws, evn++), s);
-            ws->query_ev.push_back({eq0, (int)evn - 1});
-        }
-    }
+    for (uint32_t qi = 0; qi < nq; ++qi)
+        MESSI_CUDA(enqueue_query(ix, ws, ws, iv, qp, dq + (size_t)qi * ix->len, did + (size_t)qi * k,
+                                 ddist + (size_t)qi * k, s, evn));
     MESSI_CUDA(cudaGetLastError());
     ws->last = messi_stats{};
     ws->last.queries = nq;
@@ -755,14 +784,103 @@ static messi_status replay_lb_batches(messi_index *ix, Workspace *ws, const Inde
     return MESSI_OK;
 }
 
+// Batched DTW: the queries' per-query kernel sequences run side by side on up
+// to kDtwStreams streams, each with a workspace of its own, so that the small
+// grids of one query (its seed leaf, the DTW of few candidates) share the GPU
+// with the others' work.  The streams start after the caller's stream reaches
+// this call and the caller's stream continues once all of them are done.
+static messi_status run_dtw_batched(messi_index *ix, Workspace *ws, const float *dq, uint32_t nq, uint32_t k,
+                                    const QueryParams &qp, long long *did, float *ddist, cudaStream_t s)
+{
+    const unsigned want = std::min<unsigned>(kDtwStreams, nq);
+    while (ws->sub.size() < want) {
+        Workspace *sw = new Workspace();
+        cudaStream_t t = nullptr;
+        cudaEvent_t e = nullptr;
+        if (ensure_workspace(ix, sw) != MESSI_OK ||
+            cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (t) cudaStreamDestroy(t);
+            free_workspace(*sw);
+            delete sw;
+            break;   // run on the streams there is memory for
+        }
+        ws->sub.push_back(sw);
+        ws->sub_streams.push_back(t);
+        ws->sub_done.push_back(e);
+    }
+    if (!ws->fork && !cuda_ok(cudaEventCreateWithFlags(&ws->fork, cudaEventDisableTiming), "messi_query_batched: event"))
+        return MESSI_ECUDA;
+    const unsigned S = std::min<unsigned>(want, (unsigned)ws->sub.size());
+    if (S == 0) return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate a DTW stream workspace");
+    const IndexView iv = view_of(ix);
+    MESSI_CUDA(cudaEventRecord(ws->fork, s));
+    for (unsigned j = 0; j < S; ++j) {
+        MESSI_CUDA(cudaStreamWaitEvent(ws->sub_streams[j], ws->fork, 0));
+        MESSI_CUDA(cudaMemsetAsync(ws->sub[j]->slot.acc, 0, sizeof(QueryCounters), ws->sub_streams[j]));
+    }
+    size_t evn = 0;
+    for (uint32_t qi = 0; qi < nq; ++qi) {
+        const unsigned j = qi % S;
+        MESSI_CUDA(enqueue_query(ix, ws->sub[j], ws, iv, qp, dq + (size_t)qi * ix->len, did + (size_t)qi * k,
+                                 ddist + (size_t)qi * k, ws->sub_streams[j], evn));
+    }
+    const QueryCounters *accs[kDtwStreams];
+    for (unsigned j = 0; j < S; ++j) {
+        MESSI_CUDA(cudaEventRecord(ws->sub_done[j], ws->sub_streams[j]));
+        MESSI_CUDA(cudaStreamWaitEvent(s, ws->sub_done[j], 0));
+        accs[j] = ws->sub[j]->slot.acc;
+    }
+    launch_add_counters(ws->slot.acc, accs, (int)S, s);
+    ++ws->launches;
+    return MESSI_OK;
+}
+
 messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, uint32_t nq, uint32_t k,
                          messi_dist dist, uint32_t window, uint32_t batch, int64_t *ids, float *dists,
                          messi_stream stream)
 {
     messi_status chk = query_args(ix, queries, nq, k, dist, window, ids, dists);
     if (chk != MESSI_OK) return chk;
-    // DTW queries take the per-query kernels (the fused batch kernel is ED)
-    if (dist == MESSI_DTW) return run_plain(ix, ws, queries, nq, k, dist, window, ids, dists, stream);
+    if (dist == MESSI_DTW) {
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        ensure_attributes();
+        if ((chk = ensure_workspace(ix, ws)) != MESSI_OK) return chk;
+        const bool hq = !is_device_ptr(queries), hi = !is_device_ptr(ids), hd = !is_device_ptr(dists);
+        const size_t qbytes = (size_t)nq * ix->len * 4, ibytes = (size_t)nq * k * 8, dbytes = (size_t)nq * k * 4;
+        const size_t need = (hq ? align256(qbytes) : 0) + (hi ? align256(ibytes) : 0) + (hd ? align256(dbytes) : 0);
+        if (need && !ensure_stage(ws, need)) return fail(MESSI_ENOMEM, "messi_query_batched: cannot allocate staging buffers");
+        char *stage = static_cast<char *>(ws->stage_block);
+        const float *dq = queries;
+        long long *did = reinterpret_cast<long long *>(ids);
+        float *ddist = dists;
+        size_t so = 0;
+        if (hq) {
+            dq = reinterpret_cast<const float *>(stage + so);
+            MESSI_CUDA(cudaMemcpyAsync(stage + so, queries, qbytes, cudaMemcpyHostToDevice, s));
+            so += align256(qbytes);
+        }
+        if (hi) { did = reinterpret_cast<long long *>(stage + so); so += align256(ibytes); }
+        if (hd) { ddist = reinterpret_cast<float *>(stage + so); so += align256(dbytes); }
+        const unsigned long long launches0 = ws->launches;
+        ws->scan_ev.clear();
+        ws->query_ev.clear();
+        ws->refine_ev.clear();
+        const QueryParams qp = make_params(ix, k, (int)dist, window);
+        if ((chk = run_dtw_batched(ix, ws, dq, nq, k, qp, did, ddist, s)) != MESSI_OK) return chk;
+        MESSI_CUDA(cudaGetLastError());
+        ws->last = messi_stats{};
+        ws->last.queries = nq;
+        ws->last.kernel_launches = ws->launches - launches0;
+        ws->last_stream = s;
+        ws->last_batched = false;
+        if (hi) MESSI_CUDA(cudaMemcpyAsync(ids, did, ibytes, cudaMemcpyDeviceToHost, s));
+        if (hd) MESSI_CUDA(cudaMemcpyAsync(dists, ddist, dbytes, cudaMemcpyDeviceToHost, s));
+        // the call synchronises, as the other batched forms do
+        MESSI_CUDA(cudaStreamSynchronize(s));
+        return MESSI_OK;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ensure_attributes();
     const unsigned B = std::min<unsigned>(batch ? batch : ix->tune_batch, nq);
@@ -791,6 +909,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
     const unsigned long long launches0 = ws->launches;
     ws->scan_ev.clear();
     ws->query_ev.clear();
+    ws->refine_ev.clear();
     size_t evn = 0;
     unsigned long long screened = 0;
     bool use_tc = ix->batch_mode == 1;
@@ -956,6 +1075,7 @@ messi_status messi_query_stats(const messi_index *cix, messi_stats *out)
     out->tie_rechecks = c.tie_rechecks;
     out->leaves_live = c.leaves_live;
     out->row_bytes = c.row_bytes;
+    out->dtw_cells = c.dtw_cells;
     if (ix->profiling) {
         double sum = 0.0;
         for (auto &pr : ws->scan_ev) {
@@ -965,6 +1085,14 @@ messi_status messi_query_stats(const messi_index *cix, messi_stats *out)
         }
         out->scan_ms = sum;
         out->scan_launches = ws->scan_ev.size();
+        double rsum = 0.0;
+        for (auto &pr : ws->refine_ev) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ws->ev_pool[pr.first], ws->ev_pool[pr.second]);
+            rsum += ms;
+        }
+        out->refine_ms = rsum;
+        out->refine_launches = ws->refine_ev.size();
         std::vector<double> lat;
         for (auto &pr : ws->query_ev) {
             float ms = 0.f;

@@ -46,6 +46,13 @@ __device__ __forceinline__ float warp_min(float v)
     return v;
 }
 
+// Hint: bring the 128-byte line holding p into L1 (no effect on results; an
+// address inside an allocation is required, as for a load).
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // ---------------------------------------------------------------- PTX: TMA
 __device__ __forceinline__ unsigned smem_u32(const void *p)
 {

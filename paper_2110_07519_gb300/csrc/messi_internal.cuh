@@ -49,7 +49,7 @@ constexpr unsigned kSpinLimit = 1u << 22;
 // ------------------------------------------------------- per-query state
 struct QueryCounters {
     unsigned long long lb_evaluated, lb_survivors, lbk_survivors, seeded, refined, abandoned,
-        bsf_updates, tie_rechecks, leaves_live, row_bytes;
+        bsf_updates, tie_rechecks, leaves_live, row_bytes, dtw_cells;
 };
 
 struct QueryState {
@@ -169,8 +169,14 @@ struct Workspace {
     cudaStream_t capture_stream = nullptr;
     unsigned long long tile_count = 0;   // scan tiles of the plain slot's stamp array
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, int>> scan_ev, query_ev;   // pairs of event indices
+    std::vector<std::pair<int, int>> scan_ev, query_ev, refine_ev;   // pairs of event indices
     unsigned long long launches = 0;
+    // batched DTW: per-query pipelines overlapped on several streams, each
+    // with a workspace of its own
+    std::vector<Workspace *> sub;
+    std::vector<cudaStream_t> sub_streams;
+    std::vector<cudaEvent_t> sub_done;
+    cudaEvent_t fork = nullptr;
 };
 void free_workspace(Workspace &w);
 }  // namespace messi
@@ -280,8 +286,10 @@ void launch_seed(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cud
 // which must differ from every earlier query's on this slot), then the
 // lower-bound scan of the live tiles.
 void launch_scan(const IndexView &iv, const QueryParams &qp, QuerySlot slot, unsigned epoch, cudaStream_t s);
+// ev0 / ev1 (may be null): recorded around the final refinement kernel
+// (k_refine_ed for ED, the banded DTW for DTW)
 void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s,
-                   unsigned long long *launches);
+                   unsigned long long *launches, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 void launch_finalize(const IndexView &iv, const QueryParams &qp, QuerySlot slot, long long *ids,
                      float *dists, cudaStream_t s);
 void launch_lower_bounds(const IndexView &iv, QuerySlot slot, float *lb2_by_id, cudaStream_t s);
@@ -318,6 +326,9 @@ void launch_batch(const IndexView &iv, const QueryParams &qp, const QuerySlot *s
                   unsigned ctas_per_sm, unsigned *counter, cudaStream_t s, unsigned long long *launches,
                   cudaEvent_t ev0, cudaEvent_t ev1);
 void launch_reset_state(QuerySlot slot, cudaStream_t s);
+// dst[0] += src[0] + ... + src[n-1] (counter accumulators of several slots)
+void launch_add_counters(QueryCounters *dst, const QueryCounters *const *src, int n, cudaStream_t s);
+constexpr int kDtwStreams = 4;       // streams of the batched DTW form
 float band_factor(int dist, int len);
 
 }  // namespace messi

@@ -1186,7 +1186,7 @@ k_fused_ed(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, un
 // independently through their own candidates (a strided share of the list).
 template <int R>
 __device__ __forceinline__ float thread_dtw(const float *__restrict__ qs, const float *__restrict__ x, int n, int r,
-                                            float thr)
+                                            float thr, int &rows)
 {
     constexpr int W = 2 * R + 1;
     const float INF = f_inf();
@@ -1212,6 +1212,7 @@ __device__ __forceinline__ float thread_dtw(const float *__restrict__ qs, const 
             left = v;
             rmin = fminf(rmin, v);
         }
+        rows = i + 1;
         if (rmin > thr) return rmin;
         // slide the candidate window by one
 #pragma unroll
@@ -1235,7 +1236,7 @@ k_dtw_thread(IndexView iv, QueryParams qp, QuerySlot slot)
     const unsigned lo = MODE ? st->seed_lo : 0u;
     const unsigned count = MODE ? st->seed_hi - st->seed_lo : ld_volatile_u32(&st->ord_count);
     const unsigned T = gridDim.x * blockDim.x;
-    unsigned long long done = 0, aband = 0;
+    unsigned long long done = 0, aband = 0, cells = 0;
     for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += T) {
         const unsigned pos = MODE ? lo + e : slot.surv_pos[e];
         const float thr = MODE ? f_inf() : prune_threshold(ld_volatile_u64(&st->thr), qp.F);
@@ -1246,7 +1247,9 @@ k_dtw_thread(IndexView iv, QueryParams qp, QuerySlot slot)
             if (order_floor(order_bucket(lb)) > thr) break;
             if (lb > thr) continue;
         }
-        const float d2 = thread_dtw<R>(qs, iv.raw + (unsigned long long)pos * iv.len, iv.len, qp.r, thr);
+        int rows = 0;
+        const float d2 = thread_dtw<R>(qs, iv.raw + (unsigned long long)pos * iv.len, iv.len, qp.r, thr, rows);
+        cells += (unsigned long long)rows * (unsigned)(2 * qp.r + 1);   // band cells of the rows computed
         if (MODE) {
             slot.seedbuf[e] = pack_cand(d2, iv.ids[pos]);
         } else if (d2 <= thr) {
@@ -1260,6 +1263,7 @@ k_dtw_thread(IndexView iv, QueryParams qp, QuerySlot slot)
         if (done) atomicAdd(&st->c.refined, done);
         if (aband) atomicAdd(&st->c.abandoned, aband);
     }
+    if (cells) atomicAdd(&st->c.dtw_cells, cells);
 }
 
 // LB_Keogh + LB_Improved of one candidate, one thread, one pass over the row
@@ -1288,6 +1292,7 @@ __device__ __forceinline__ float lbk_improved_thread(const float *__restrict__ q
     const int lo_b = 2 * (R - r);       // first window slot inside [p - r, p + r]
     float acc1 = 0.f, acc2 = 0.f;
     for (int i = 0; i < n + r; ++i) {
+        if ((i & 31) == 0 && i + 64 < n) prefetch_l1(x + i + 64);   // two lines ahead
         float h = hw[W - 1];
         if (i < n) {
             const float c = __ldg(x + i), u = Us[i], l = Ls[i];
@@ -1347,6 +1352,10 @@ __device__ __forceinline__ float lbk_improved_blocks(const float *__restrict__ q
     }
     float acc1 = 0.f, acc2 = 0.f;
     for (int j0 = 0; j0 < n + R; j0 += W) {
+        // this lane's row is read one value at a time: ask L1 for the lines
+        // of the next block early so several rows' misses overlap
+        if (j0 + W < n) prefetch_l1(x + j0 + W);
+        if (j0 + W + 32 < n) prefetch_l1(x + j0 + W + 32);
         float pmx = 0.f, pmn = 0.f;
 #pragma unroll
         for (int k = 0; k < W; ++k) {
@@ -1721,6 +1730,7 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
             atomicAdd(&acc->tie_rechecks, st->c.tie_rechecks);
             atomicAdd(&acc->leaves_live, st->c.leaves_live);
             atomicAdd(&acc->row_bytes, st->c.row_bytes);
+            atomicAdd(&acc->dtw_cells, st->c.dtw_cells);
         }
         return;
     }
@@ -1791,6 +1801,7 @@ __device__ __forceinline__ void finalize_body(const IndexView &iv, const QueryPa
         atomicAdd(&acc->tie_rechecks, st->c.tie_rechecks);
         atomicAdd(&acc->leaves_live, st->c.leaves_live);
         atomicAdd(&acc->row_bytes, st->c.row_bytes);
+        atomicAdd(&acc->dtw_cells, st->c.dtw_cells);
     }
 }
 
@@ -1902,10 +1913,12 @@ void launch_scan(const IndexView &iv, const QueryParams &qp, QuerySlot slot, uns
 }
 
 void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, cudaStream_t s,
-                   unsigned long long *launches)
+                   unsigned long long *launches, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     if (qp.dist == 0) {
+        if (ev0) cudaEventRecord(ev0, s);
         k_refine_ed<<<num_sms() * 3, kRefineThreads, iv.len * 4, s>>>(iv, qp, slot);   // one wave: 3 blocks per SM
+        if (ev1) cudaEventRecord(ev1, s);
         if (launches) *launches += 1;
     } else {
         if (!launch_lbk_thread(iv, qp, slot, s)) {
@@ -1915,11 +1928,13 @@ void launch_refine(const IndexView &iv, const QueryParams &qp, QuerySlot slot, c
             k_lbk<<<num_sms() * 4, wpb * 32, (size_t)iv.len * 12 + (size_t)wpb * 16 * iv.len, s>>>(iv, qp, slot, wpb);
         }
         launch_order(qp, slot, 1, slot.surv_pos, slot.surv_lb, s);
+        if (ev0) cudaEventRecord(ev0, s);
         if (!launch_dtw_thread<0>(iv, qp, slot, s)) {
             const int wpb = dtw_warps_per_block(iv.len);
             const size_t sm = (size_t)iv.len * 4 + (size_t)wpb * 3 * iv.len * 4;
             k_dtw<<<num_sms() * 4, wpb * 32, sm, s>>>(iv, qp, slot);
         }
+        if (ev1) cudaEventRecord(ev1, s);
         if (launches) *launches += 5;
     }
 }
@@ -1975,6 +1990,38 @@ void launch_batch_finalize(const IndexView &iv, const QueryParams &qp, const Que
 {
     k_finalize_batch<<<B, kFinThreads, kFinSmem, s>>>(iv, qp, slots_dev, ids, dists, redo);
     if (launches) *launches += 1;
+}
+
+struct CounterSrcs {
+    const QueryCounters *p[kDtwStreams];
+};
+
+__global__ void k_add_counters(QueryCounters *dst, CounterSrcs src, int n)
+{
+    if (threadIdx.x != 0) return;
+    QueryCounters t{};
+    for (int i = 0; i < n; ++i) {
+        const QueryCounters &c = *src.p[i];
+        t.lb_evaluated += c.lb_evaluated;
+        t.lb_survivors += c.lb_survivors;
+        t.lbk_survivors += c.lbk_survivors;
+        t.seeded += c.seeded;
+        t.refined += c.refined;
+        t.abandoned += c.abandoned;
+        t.bsf_updates += c.bsf_updates;
+        t.tie_rechecks += c.tie_rechecks;
+        t.leaves_live += c.leaves_live;
+        t.row_bytes += c.row_bytes;
+        t.dtw_cells += c.dtw_cells;
+    }
+    *dst = t;
+}
+
+void launch_add_counters(QueryCounters *dst, const QueryCounters *const *src, int n, cudaStream_t s)
+{
+    CounterSrcs cs{};
+    for (int i = 0; i < n && i < kDtwStreams; ++i) cs.p[i] = src[i];
+    k_add_counters<<<1, 32, 0, s>>>(dst, cs, std::min(n, kDtwStreams));
 }
 
 void launch_lower_bounds(const IndexView &iv, QuerySlot slot, float *lb2_by_id, cudaStream_t s)

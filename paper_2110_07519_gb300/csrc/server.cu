@@ -5,8 +5,9 @@
 // on submit.  Worker threads, one per CUDA stream, repeatedly form a batch:
 // they admit queued requests in arrival order while the device memory charged
 // to admitted-but-unfinished requests stays within the budget, group them by
-// (distance, window), run the group through the batched kernels (ED) or the
-// per-query kernels (DTW) with k = the largest k in the group, and hand each
+// (distance, window), run the group through the batched forms (ED: the
+// tensor-core screen or the lower-bound batch kernels; DTW: per-query kernel
+// sequences overlapped on several streams) with k = the largest k in the group, and hand each
 // request the first k of its row -- the k-NN answer is a prefix of the
 // (k_max)-NN answer under the (distance, id) order, so a request gets the same
 // result alone or in any mix.  A batch on one stream overlaps with the batch
@@ -162,9 +163,8 @@ void worker_loop(messi_server *srv, Worker *w)
         if (e != cudaSuccess) st = MESSI_ECUDA;
         if (st == MESSI_OK) {
             const messi_dist d = batch[0].dist;
-            st = (d == MESSI_ED) ? run_batched(ix, &w->ws, w->d_q, B, kmax, d, 0, B, w->d_ids, w->d_d, w->stream)
-                                 : run_plain(ix, &w->ws, w->d_q, B, kmax, d, batch[0].window, w->d_ids, w->d_d,
-                                             w->stream);
+            st = run_batched(ix, &w->ws, w->d_q, B, kmax, d, d == MESSI_DTW ? batch[0].window : 0u, B, w->d_ids,
+                             w->d_d, w->stream);
         }
         if (st == MESSI_OK) {
             e = cudaMemcpyAsync(w->h_ids, w->d_ids, (size_t)B * kmax * 8, cudaMemcpyDeviceToHost, w->stream);

@@ -71,13 +71,38 @@ def test_batched_host_buffers_and_ties(m):
     assert ids[0].tolist() == [3, 10_000, 19_999]
 
 
-def test_batched_dtw_takes_per_query_kernels(m, coll):
+@pytest.mark.parametrize("nq,k,r", [(1, 1, 12), (6, 2, 12), (13, 5, 25), (13, 1, 0)])
+def test_batched_dtw_overlapped_streams(m, coll, nq, k, r):
+    """The batched DTW form (per-query kernel sequences on several streams,
+    each with its own workspace): the FP64 oracle's ids and distances, equal
+    to the per-query path's, for batches smaller and larger than the number
+    of streams; the counters add up over the streams."""
     x, ix, q = coll
     sub = x[:20_000]
     iy = m.messi_build(torch.from_numpy(sub).cuda(), 16, 256)
-    ids, d = m.messi_query_batched(iy, torch.from_numpy(q[:6]).cuda(), k=2, dist=m.MESSI_DTW, window=12)
+    qd = torch.from_numpy(q[:nq].copy()).cuda()
+    ids, d = m.messi_query_batched(iy, qd, k=k, dist=m.MESSI_DTW, window=r)
     m.messi_check(iy)
-    check(ids, d, *oracle.knn(sub, q[:6], 2, oracle.DTW, 12))
+    st = m.messi_query_stats(iy)
+    check(ids, d, *oracle.knn(sub, q[:nq], k, oracle.DTW, r))
+    pids, pd = m.messi_query(iy, qd, k=k, dist=m.MESSI_DTW, window=r)
+    m.messi_check(iy)
+    sp = m.messi_query_stats(iy)
+    assert np.array_equal(ids.cpu().numpy(), pids.cpu().numpy())
+    assert np.array_equal(d.cpu().numpy(), pd.cpu().numpy())
+    # the same work, counted over the streams
+    assert st["queries"] == sp["queries"] == nq
+    assert st["lb_evaluated"] == sp["lb_evaluated"]
+    assert st["seeded"] == sp["seeded"]
+
+
+def test_batched_dtw_host_buffers(m, coll):
+    x, ix, q = coll
+    sub = x[:20_000]
+    iy = m.messi_build(torch.from_numpy(sub).cuda(), 16, 256)
+    ids, d = m.messi_query_batched(iy, q[:9], k=3, dist=m.MESSI_DTW, window=12)   # numpy in and out
+    m.messi_check(iy)
+    check(ids, d, *oracle.knn(sub, q[:9], 3, oracle.DTW, 12))
 
 
 def test_lb_form_graph_replay_matches_oracle(m, coll):

@@ -1184,6 +1184,33 @@ k_fused_ed(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, un
 // the warp wavefront -- and abandons when a row minimum exceeds the live
 // threshold (every warping path crosses every row).  Threads advance
 // independently through their own candidates (a strided share of the list).
+template <int R, bool CHECK>
+__device__ __forceinline__ float dtw_row(float (&D)[2 * R + 1], const float (&xw)[2 * R + 1], float qi, int i, int n,
+                                         int r)
+{
+    constexpr int W = 2 * R + 1;
+    const float INF = f_inf();
+    float left = INF, rmin = INF;
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+        const float up = (b + 1 < W) ? D[b + 1] : INF;
+        const float best = fminf(fminf(D[b], up), left);
+        const float d = qi - xw[b];
+        float v;
+        if (CHECK) {
+            const int j = i - R + b;
+            const bool inside = j >= 0 && j < n && (b - R <= r) && (R - b <= r);
+            v = inside ? d * d + best : INF;
+        } else {
+            v = d * d + best;
+        }
+        D[b] = v;
+        left = v;
+        rmin = fminf(rmin, v);
+    }
+    return rmin;
+}
+
 template <int R>
 __device__ __forceinline__ float thread_dtw(const float *__restrict__ qs, const float *__restrict__ x, int n, int r,
                                             float thr, int &rows)
@@ -1197,21 +1224,14 @@ __device__ __forceinline__ float thread_dtw(const float *__restrict__ qs, const 
         const int j = b - R;                              // x index of band cell b in row 0
         xw[b] = (j >= 0 && j < n) ? __ldg(x + j) : 0.f;
     }
+    // rows whose whole band lies inside the matrix, when the window is the
+    // band reach itself, need no per-cell test: [R, n - R)
+    const bool exact = r == R;
+    const int in_lo = exact ? R : n, in_hi = exact ? n - R : n;
     for (int i = 0; i < n; ++i) {
         const float qi = qs[i];
-        float left = INF, rmin = INF;
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            const int j = i - R + b;
-            const float up = (b + 1 < W) ? D[b + 1] : INF;
-            const float best = fminf(fminf(D[b], up), left);
-            const float d = qi - xw[b];
-            const bool inside = j >= 0 && j < n && (b - R <= r) && (R - b <= r);
-            const float v = inside ? d * d + best : INF;
-            D[b] = v;
-            left = v;
-            rmin = fminf(rmin, v);
-        }
+        const float rmin = (i >= in_lo && i < in_hi) ? dtw_row<R, false>(D, xw, qi, i, n, r)
+                                                     : dtw_row<R, true>(D, xw, qi, i, n, r);
         rows = i + 1;
         if (rmin > thr) return rmin;
         // slide the candidate window by one

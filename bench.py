@@ -635,7 +635,14 @@ def run_serve(args, ws, rank, local):
             lat = np.array(lat)
             res_mode[str(rate)] = {"offered_qps": rate, "completed": total, "served_qps": total / wall,
                                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                                   "batches": st["batches"], "inflight_peak": st["inflight_peak"]}
+                                   "ed": {"requests": int((~kinds).sum()),
+                                          "p50_ms": float(np.percentile(lat[~kinds], 50)) if (~kinds).any() else None,
+                                          "p99_ms": float(np.percentile(lat[~kinds], 99)) if (~kinds).any() else None},
+                                   "dtw": {"requests": int(kinds.sum()),
+                                           "p50_ms": float(np.percentile(lat[kinds], 50)) if kinds.any() else None,
+                                           "p99_ms": float(np.percentile(lat[kinds], 99)) if kinds.any() else None},
+                                   "batches": st["batches"], "inflight_peak": st["inflight_peak"],
+                                   "budget_waits": st["budget_waits"], "wall_s": wall}
             print(json.dumps({"mode": "serve-partial", "batch_kernels": mode_name, "rate": rate,
                               **res_mode[str(rate)]}), file=sys.stderr, flush=True)
         out[mode_name] = res_mode

@@ -240,9 +240,18 @@ messi_status messi_server_create(messi_index *ix, const messi_server_config *cfg
         }
     }
     const unsigned maxB = srv->cfg.max_batch, len = (unsigned)ix->len, kx = srv->cfg.max_k;
+    // worker 0 takes the ED batches: its stream gets the highest priority, so
+    // that the block scheduler starts its (short, whole-SM) screen launches
+    // ahead of the long DTW work queued on the other workers' streams
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        prio_low = prio_high = 0;
+    }
     for (uint32_t i = 0; i < srv->cfg.streams; ++i) {
         Worker *w = new Worker();
-        bool ok = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) == cudaSuccess &&
+        const int prio = (i == 0 && srv->cfg.streams > 1) ? prio_high : prio_low;
+        bool ok = cudaStreamCreateWithPriority(&w->stream, cudaStreamNonBlocking, prio) == cudaSuccess &&
                   cudaMallocHost(&w->h_q, (size_t)maxB * len * 4) == cudaSuccess &&
                   cudaMallocHost(&w->h_ids, (size_t)maxB * kx * 8) == cudaSuccess &&
                   cudaMallocHost(&w->h_d, (size_t)maxB * kx * 4) == cudaSuccess &&

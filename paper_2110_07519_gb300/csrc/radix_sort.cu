@@ -11,7 +11,9 @@
 //   1. per-tile digit histograms (tile = 4096 items),
 //   2. an exclusive scan over the digit-major histogram table,
 //   3. a stable scatter: inside a tile, items are ranked by (warp, round,
-//      lane) with __match_any_sync, so equal digits keep their input order.
+//      lane) with __match_any_sync, so equal digits keep their input order,
+//      sorted within the tile in shared memory and written out digit run by
+//      digit run.
 #include "messi_internal.cuh"
 
 namespace messi {
@@ -50,60 +52,103 @@ k_hist(const uint4 *__restrict__ keys, unsigned long long n, int byte, unsigned 
     hist[(unsigned long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kRsThreads)
+// Stable scatter of one tile through shared memory: the tile's keys and
+// payloads are staged in input order (coalesced), each item gets its place
+// in the tile sorted by digit -- the digit's start in the tile, plus the
+// items of that digit in earlier warps, plus its rank among the warp's equal
+// digits (ranked by round, then lane, so input order is kept) -- and the
+// sorted tile is written out so that consecutive threads write consecutive
+// addresses of a digit's run.
+constexpr int kRsSmem = kRsTile * 16 + kRsTile * 4 + kRsTile * 2;   // keys, payloads, local permutation
+
+__global__ void __launch_bounds__(kRsThreads, 2)
 k_scatter(const uint4 *__restrict__ keys, const unsigned int *__restrict__ vals, uint4 *__restrict__ keys_out,
           unsigned int *__restrict__ vals_out, unsigned long long n, int byte,
           const unsigned int *__restrict__ offs, unsigned long long ntiles)
 {
+    extern __shared__ __align__(16) unsigned char rsm[];
+    uint4 *sk = reinterpret_cast<uint4 *>(rsm);
+    unsigned *sv = reinterpret_cast<unsigned *>(rsm + kRsTile * 16);
+    unsigned short *perm = reinterpret_cast<unsigned short *>(rsm + kRsTile * 20);
     __shared__ unsigned whist[kRsWarps][256];
+    __shared__ unsigned lstart[256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long tbase = (unsigned long long)blockIdx.x * kRsTile;
+    const unsigned tn = (unsigned)min((unsigned long long)kRsTile, n - tbase);
+    for (unsigned i = threadIdx.x; i < tn; i += kRsThreads) {
+        sk[i] = keys[tbase + i];
+        sv[i] = vals[tbase + i];
+    }
     for (int d = lane; d < 256; d += 32) whist[warp][d] = 0u;
-    __syncwarp();
+    __syncthreads();
+    // ranks within the warp: items warp*512 + r*32 + lane of the tile
     const unsigned lt = (1u << lane) - 1u;
-    const unsigned long long base = (unsigned long long)blockIdx.x * kRsTile + (unsigned long long)warp * 32 * kRsRounds;
-
-    uint4 k[kRsRounds];
-    unsigned v[kRsRounds];
-    unsigned rank[kRsRounds];
+    unsigned dr[kRsRounds];   // digit << 16 | rank
 #pragma unroll
     for (int r = 0; r < kRsRounds; ++r) {
-        unsigned long long idx = base + (unsigned long long)r * 32 + lane;
-        bool valid = idx < n;
-        if (valid) {
-            k[r] = keys[idx];
-            v[r] = vals[idx];
-        }
-        unsigned d = valid ? digit_of(k[r], byte) : 256u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned i = warp * 32 * kRsRounds + r * 32 + lane;
+        const bool valid = i < tn;
+        const unsigned d = valid ? digit_of(sk[i], byte) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
         unsigned before = 0u;
         if (valid) before = whist[warp][d];
         __syncwarp();
-        rank[r] = before + __popc(peers & lt);
+        dr[r] = (d << 16) | (before + __popc(peers & lt));
         if (valid && (__ffs(peers) - 1) == lane) whist[warp][d] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
     {
+        // per digit (one per thread): earlier warps' counts, and the tile total
+        const int d = threadIdx.x;
         unsigned run = 0u;
-        const int d = threadIdx.x;                 // 256 threads, one digit each
 #pragma unroll
         for (int w = 0; w < kRsWarps; ++w) {
-            unsigned t = whist[w][d];
+            const unsigned t = whist[w][d];
             whist[w][d] = run;
             run += t;
+        }
+        lstart[d] = run;   // the digit's count for now
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // exclusive scan of the 256 digit counts, 8 per lane
+        unsigned c[8], sum = 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            c[j] = lstart[lane * 8 + j];
+            sum += c[j];
+        }
+        unsigned inc = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += y;
+        }
+        unsigned run = inc - sum;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            lstart[lane * 8 + j] = run;
+            run += c[j];
         }
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRsRounds; ++r) {
-        unsigned long long idx = base + (unsigned long long)r * 32 + lane;
-        if (idx < n) {
-            unsigned d = digit_of(k[r], byte);
-            unsigned long long dst = (unsigned long long)offs[(unsigned long long)d * ntiles + blockIdx.x] +
-                                     whist[warp][d] + rank[r];
-            keys_out[dst] = k[r];
-            vals_out[dst] = v[r];
+        const unsigned i = warp * 32 * kRsRounds + r * 32 + lane;
+        if (i < tn) {
+            const unsigned d = dr[r] >> 16;
+            perm[lstart[d] + whist[warp][d] + (dr[r] & 0xffffu)] = (unsigned short)i;
         }
+    }
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < tn; i += kRsThreads) {
+        const unsigned src = perm[i];
+        const uint4 k = sk[src];
+        const unsigned d = digit_of(k, byte);
+        const unsigned long long dst = (unsigned long long)offs[(unsigned long long)d * ntiles + blockIdx.x] + (i - lstart[d]);
+        keys_out[dst] = k;
+        vals_out[dst] = sv[src];
     }
 }
 
@@ -226,6 +271,13 @@ void radix_sort_keys(uint4 *keys, unsigned int *vals, uint4 *keys_alt, unsigned 
     b = (b + 255) & ~(size_t)255;
     void *scan_tmp = static_cast<char *>(temp) + b;
 
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kRsSmem);
+        attr_set[dev] = true;
+    }
     int first = (128 - key_bits) / 8;          // least significant byte holding used bits
     uint4 *ki = keys, *ko = keys_alt;
     unsigned *vi = vals, *vo = vals_alt;
@@ -233,7 +285,7 @@ void radix_sort_keys(uint4 *keys, unsigned int *vals, uint4 *keys_alt, unsigned 
     for (int byte = first; byte < 16; ++byte, ++passes) {
         k_hist<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ki, n, byte, hist, ntiles);
         exclusive_scan_u32(hist, offs, entries, scan_tmp, s, launches);
-        k_scatter<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ki, vi, ko, vo, n, byte, offs, ntiles);
+        k_scatter<<<(unsigned)ntiles, kRsThreads, kRsSmem, s>>>(ki, vi, ko, vo, n, byte, offs, ntiles);
         if (launches) *launches += 2;
         uint4 *tk = ki; ki = ko; ko = tk;
         unsigned *tv = vi; vi = vo; vo = tv;

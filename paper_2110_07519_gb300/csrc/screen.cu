@@ -9,7 +9,9 @@
 //               + 2^-24 sqrt(len) 1.002 (|q| + |x|)          (f16 rounding of
 //                 both operands incl. subnormals, FP32 accumulation)
 //   plus 4u (|x|^2 + |q|^2 + 2|q||x|) for the FP32 evaluation of s and the
-//   FP32 rounding of the norms (computed in FP64).
+//   FP32 rounding of the norms (the query norms computed in FP64, the row
+//   norms as compensated FP32 sums within 1e-9 of exact before rounding;
+//   the bound's constant carries 0.03u of slack for that).
 // so s - eps <= true d^2 <= s + eps.  A pair is a candidate when
 // s - eps <= U_q, U_q an upper bound of the query's true k-th squared
 // distance; for k <= 16 the k-th smallest s + eps met so far also tightens
@@ -74,7 +76,32 @@ __device__ __forceinline__ float tc_coef(int len)
 }
 
 // ------------------------------------------------------- screen copy
-// One warp per series: f16 copy in tile layout, FP64 squared norm -> xn (FP32,
+// Squared norms in FP32 arithmetic, carried as an unevaluated sum hi + lo of
+// two floats (GB300's FP64 rate is low): each product x*x is split exactly
+// into p + e (e = fma(x, x, -p)), both are added into (hi, lo) with an exact
+// two-sum on hi; lanes then combine their pairs across the warp the same way.
+// For all-positive terms the pair differs from the exact sum by at most
+// about (n u)^2 of it (n terms per lane or per warp step, u = 2^-24), far
+// below the FP32 rounding of the final norm; the one FP64 addition hi + lo
+// per row keeps that accuracy until the norm is rounded.
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, float b)
+{
+    const float s = a.hi + b;
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (b - bb);   // a.hi + b = s + err exactly
+    return {s, a.lo + err};
+}
+__device__ __forceinline__ F2 f2_add2(F2 a, F2 b)
+{
+    F2 t = f2_add(a, b.hi);
+    t.lo += b.lo;
+    return t;
+}
+
+// One warp per series: f16 copy in tile layout, squared norm -> xn (FP32,
 // nearest) and |x| rounded up.
 __global__ void __launch_bounds__(256)
 k_make_screen_copy(const float *__restrict__ raw, unsigned long long N, int len, __half *__restrict__ tiles,
@@ -88,7 +115,7 @@ k_make_screen_copy(const float *__restrict__ raw, unsigned long long N, int len,
         const unsigned long long tile = row / kTcRows;
         const unsigned r = (unsigned)(row % kTcRows);
         unsigned char *tbase = reinterpret_cast<unsigned char *>(tiles) + tile * (unsigned long long)kTcRows * len * 2;
-        double ss = 0.0;
+        F2 ss = {0.f, 0.f};
         for (int k0 = lane * 8; k0 < len; k0 += 256) {
             float v[8];
             if (row < N) {
@@ -99,22 +126,32 @@ k_make_screen_copy(const float *__restrict__ raw, unsigned long long N, int len,
 #pragma unroll
                 for (int i = 0; i < 8; ++i) v[i] = 0.f;
             }
-            __align__(16) __half h[8];
+            __align__(16) __half2 h[4];
+            bool big = false;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) h[i] = __floats2half2_rn(v[2 * i], v[2 * i + 1]);   // two per instruction
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                if (fabsf(v[i]) > 65000.f) atomicOr(bad, 1u);
-                h[i] = __float2half_rn(v[i]);
-                ss = __dadd_rn(ss, __dmul_rn((double)v[i], (double)v[i]));
+                big = big || fabsf(v[i]) > 65000.f;
+                const float pr = __fmul_rn(v[i], v[i]);
+                const float pe = __fmaf_rn(v[i], v[i], -pr);     // v^2 = pr + pe exactly
+                ss = f2_add(ss, pr);
+                ss.lo = __fadd_rn(ss.lo, pe);
             }
+            if (big) atomicOr(bad, 1u);
             const unsigned ck = chunk_k(len);
             *reinterpret_cast<uint4 *>(tbase + (unsigned)(k0 / ck) * (kTcRows * ck * 2) +
                                        tc_offset(r, (unsigned)(k0 % ck), ck)) = *reinterpret_cast<uint4 *>(h);
         }
 #pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+        for (int off = 16; off >= 1; off >>= 1) {
+            const F2 o = {__shfl_xor_sync(0xffffffffu, ss.hi, off), __shfl_xor_sync(0xffffffffu, ss.lo, off)};
+            ss = f2_add2(ss, o);
+        }
         if (lane == 0) {
-            xn[row] = (float)ss;
-            xnorm[row] = __double2float_ru(sqrt(ss * (1.0 + 1e-12)));
+            const double sd = (double)ss.hi + (double)ss.lo;
+            xn[row] = (float)sd;
+            xnorm[row] = __double2float_ru(sqrt(sd * (1.0 + 1e-9)));
         }
     }
 }

@@ -1,7 +1,7 @@
 // summarize.cu -- PAA + SAX of every series (Sec. 2.2; ConvertToiSAX in
 // Algorithm 3).
 //
-// One warp per series.  Lanes read the row as float4 (coalesced), sum each
+// One warp per pair of series.  Lanes read each row as float4 (coalesced), sum each
 // segment in FP32 with shuffles and pick the symbol by binary search over
 // FP32 copies of the breakpoints.  The symbol must equal the one an exact
 // FP64 evaluation gives (PAA as the FP64 sequential sum divided by m, then
@@ -59,8 +59,8 @@ k_summarize(const float *__restrict__ series, unsigned long long n, int len, int
 {
     __shared__ float sb32[kMaxCard];
     __shared__ double sb64[kMaxCard];
-    __shared__ float seg_sum[kSumThreads / 32][kMaxSegments];
-    __shared__ float seg_abs[kSumThreads / 32][kMaxSegments];
+    __shared__ float seg_sum[kSumThreads / 32][2 * kMaxSegments];
+    __shared__ float seg_abs[kSumThreads / 32][2 * kMaxSegments];
     for (int i = threadIdx.x; i < kMaxCard; i += blockDim.x) {
         sb32[i] = i < card - 1 ? beta32[i] : __int_as_float(0x7f800000);
         sb64[i] = i < card - 1 ? beta64[i] : __longlong_as_double(0x7ff0000000000000ll);
@@ -73,51 +73,69 @@ k_summarize(const float *__restrict__ series, unsigned long long n, int len, int
     const int n4 = len >> 2;
     const int m = len / w;
     const int rounds = (n4 + 31) >> 5;
+    // rows are taken two at a time: both are read and reduced as before, then
+    // lanes 0-15 finish the first row and lanes 16-31 the second (symbols,
+    // key, word), so the per-row work after the sums is shared by a pair
+    const int half = lane >> 4, seg = lane & 15;
 
-    for (unsigned long long row = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + wib; row < n;
-         row += nwarps) {
-        const float4 *x4 = reinterpret_cast<const float4 *>(series + row * (unsigned long long)len);
-        float acc = 0.f, aac = 0.f;
-        for (int t = 0; t < rounds; ++t) {
-            int i = lane + 32 * t;
-            float v = 0.f, a = 0.f;
-            if (i < n4) {
-                float4 f = __ldg(x4 + i);
-                v = (f.x + f.y) + (f.z + f.w);
-                a = (fabsf(f.x) + fabsf(f.y)) + (fabsf(f.z) + fabsf(f.w));
-            }
-            if (M4 <= 32) {
+    for (unsigned long long pair = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + wib; 2 * pair < n;
+         pair += nwarps) {
+        // the next pair of this warp: into L2 while this one is reduced
+        {
+            const unsigned long long nxt = 2 * (pair + nwarps);
+            for (int i = lane * 32; i < 2 * len; i += 32 * 32)
+                if (nxt * (unsigned long long)len + i < n * (unsigned long long)len)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(series + nxt * (unsigned long long)len + i));
+        }
 #pragma unroll
-                for (int off = M4 / 2; off >= 1; off >>= 1) {
-                    v += __shfl_xor_sync(0xffffffffu, v, off);
-                    a += __shfl_xor_sync(0xffffffffu, a, off);
+        for (int h = 0; h < 2; ++h) {
+            const unsigned long long row = 2 * pair + h;
+            if (row >= n) break;
+            const float4 *x4 = reinterpret_cast<const float4 *>(series + row * (unsigned long long)len);
+            float acc = 0.f, aac = 0.f;
+            for (int t = 0; t < rounds; ++t) {
+                int i = lane + 32 * t;
+                float v = 0.f, a = 0.f;
+                if (i < n4) {
+                    float4 f = __ldg(x4 + i);
+                    v = (f.x + f.y) + (f.z + f.w);
+                    a = (fabsf(f.x) + fabsf(f.y)) + (fabsf(f.z) + fabsf(f.w));
                 }
-                if ((lane & (M4 - 1)) == 0 && i < n4) {
-                    seg_sum[wib][i / M4] = v;
-                    seg_abs[wib][i / M4] = a;
-                }
-            } else {
-                acc += v;
-                aac += a;
-                if (((t + 1) & (M4 / 32 - 1)) == 0) {
+                if (M4 <= 32) {
 #pragma unroll
-                    for (int off = 16; off >= 1; off >>= 1) {
-                        acc += __shfl_xor_sync(0xffffffffu, acc, off);
-                        aac += __shfl_xor_sync(0xffffffffu, aac, off);
+                    for (int off = M4 / 2; off >= 1; off >>= 1) {
+                        v += __shfl_xor_sync(0xffffffffu, v, off);
+                        a += __shfl_xor_sync(0xffffffffu, a, off);
                     }
-                    if (lane == 0) {
-                        seg_sum[wib][(32 * t) / M4] = acc;
-                        seg_abs[wib][(32 * t) / M4] = aac;
+                    if ((lane & (M4 - 1)) == 0 && i < n4) {
+                        seg_sum[wib][16 * h + i / M4] = v;
+                        seg_abs[wib][16 * h + i / M4] = a;
                     }
-                    acc = 0.f;
-                    aac = 0.f;
+                } else {
+                    acc += v;
+                    aac += a;
+                    if (((t + 1) & (M4 / 32 - 1)) == 0) {
+#pragma unroll
+                        for (int off = 16; off >= 1; off >>= 1) {
+                            acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                            aac += __shfl_xor_sync(0xffffffffu, aac, off);
+                        }
+                        if (lane == 0) {
+                            seg_sum[wib][16 * h + (32 * t) / M4] = acc;
+                            seg_abs[wib][16 * h + (32 * t) / M4] = aac;
+                        }
+                        acc = 0.f;
+                        aac = 0.f;
+                    }
                 }
             }
         }
         __syncwarp();
 
+        const unsigned long long row = 2 * pair + half;
+        const bool has = seg < w && row < n;
         int sym = 0;
-        if (lane < w) {
+        if (has) {
             const float S = seg_sum[wib][lane];
             const float A = seg_abs[wib][lane];
             if (status && !(isfinite(S) && isfinite(A))) atomicOr(status, kStInvalidQuery);
@@ -130,7 +148,7 @@ k_summarize(const float *__restrict__ series, unsigned long long n, int len, int
             if (sym > 0) ok = ok && (p - sb32[sym - 1] > marg);
             if (sym < card - 1) ok = ok && (sb32[sym] - p > marg);
             if (!ok) {
-                const float *xs = series + row * (unsigned long long)len + lane * m;
+                const float *xs = series + row * (unsigned long long)len + seg * m;
                 double sum = 0.0;
                 for (int t = 0; t < m; ++t) sum = __dadd_rn(sum, (double)xs[t]);
                 sym = symbol_fp64(__ddiv_rn(sum, (double)m), sb64, card);
@@ -138,11 +156,13 @@ k_summarize(const float *__restrict__ series, unsigned long long n, int len, int
         }
 
         // interleaved key: for each bit plane j, the j-th most significant
-        // bit of every segment's symbol, segment 0 first
+        // bit of every segment's symbol, segment 0 first (each half of the
+        // warp builds its own row's key from its 16 ballot bits)
         unsigned long long khi = 0ull, klo = 0ull;
         for (int j = 0; j < bits; ++j) {
-            unsigned mask = __ballot_sync(0xffffffffu, lane < w && ((sym >> (bits - 1 - j)) & 1));
-            unsigned field = __brev(mask) >> (32 - w);
+            const unsigned mask = __ballot_sync(0xffffffffu, has && ((sym >> (bits - 1 - j)) & 1));
+            const unsigned mh = half ? (mask >> 16) : (mask & 0xffffu);
+            const unsigned field = __brev(mh) >> (32 - w);
             shl128_or(khi, klo, w, field);
         }
         const int used = w * bits;
@@ -152,13 +172,14 @@ k_summarize(const float *__restrict__ series, unsigned long long n, int len, int
             else { khi = (khi << sh) | (klo >> (64 - sh)); klo <<= sh; }
         }
 
-        unsigned v = (lane < w) ? ((unsigned)sym << (8 * (lane & 3))) : 0u;
+        unsigned v = has ? ((unsigned)sym << (8 * (seg & 3))) : 0u;
         v |= __shfl_xor_sync(0xffffffffu, v, 1);
         v |= __shfl_xor_sync(0xffffffffu, v, 2);
-        unsigned w1 = __shfl_sync(0xffffffffu, v, 4);
-        unsigned w2 = __shfl_sync(0xffffffffu, v, 8);
-        unsigned w3 = __shfl_sync(0xffffffffu, v, 12);
-        if (lane == 0) {
+        const int hb = lane & 16;
+        unsigned w1 = __shfl_sync(0xffffffffu, v, hb + 4);
+        unsigned w2 = __shfl_sync(0xffffffffu, v, hb + 8);
+        unsigned w3 = __shfl_sync(0xffffffffu, v, hb + 12);
+        if (seg == 0 && row < n) {
             sax_out[row] = make_uint4(v, w1, w2, w3);
             if (key_out)
                 key_out[row] = make_uint4((unsigned)(khi >> 32), (unsigned)khi, (unsigned)(klo >> 32),
@@ -179,7 +200,7 @@ void launch_summarize(const float *series, unsigned long long n, int len, int w,
     int bits = 0;
     while ((1 << bits) < card) ++bits;
     const int m4 = (len / w) / 4;
-    unsigned long long rows_per_block = kSumThreads / 32;
+    unsigned long long rows_per_block = 2 * (kSumThreads / 32);   // a pair of rows per warp
     unsigned long long want = (n + rows_per_block - 1) / rows_per_block;
     unsigned long long cap = (unsigned long long)num_sms() * 8;
     unsigned grid = (unsigned)(want < cap ? want : cap);

@@ -220,6 +220,8 @@ struct TcWs {
     __half *qtiles, *qtiles2;       // the batch's query tiles; those screened again, gathered
     float *qconst;
     unsigned *Ubits, *cand_count, *flags, *active, *cand_pos, *n_active, *qmap;
+    float *tkinit;                  // per query: the seed leaf's k best upper ends
+    uint2 *srange;                  // per query: the seed leaf's positions
 };
 
 TcWs tc_ws_view(messi_index *ix, Workspace *ws)
@@ -236,6 +238,8 @@ TcWs tc_ws_view(messi_index *ix, Workspace *ws)
     w.n_active = reinterpret_cast<unsigned *>(p); p += 256;
     w.qtiles2 = reinterpret_cast<__half *>(p); p += align256((size_t)P * ix->len * 2);
     w.qmap = reinterpret_cast<unsigned *>(p); p += align256((size_t)P * 4);
+    w.tkinit = reinterpret_cast<float *>(p); p += align256((size_t)P * kTcTopKHost * 4);
+    w.srange = reinterpret_cast<uint2 *>(p); p += align256((size_t)P * 8);
     w.cand_pos = reinterpret_cast<unsigned *>(p);
     return w;
 }
@@ -250,7 +254,7 @@ messi_status ensure_tc_workspace(messi_index *ix, Workspace *ws, unsigned B)
     }
     const size_t P = (B + 127) / 128 * 128;
     const size_t bytes = 2 * align256(P * ix->len * 2) + align256(P * 16) + 5 * align256(P * 4) + 256 +
-                         P * kTcCap * 4;
+                         align256(P * kTcTopKHost * 4) + align256(P * 8) + P * kTcCap * 4;
     if (cudaMalloc(&ws->tcws_block, bytes) != cudaSuccess) {
         cudaGetLastError();
         ws->tcws_block = nullptr;
@@ -927,7 +931,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
         const TcWs w = tc_ws_view(ix, ws);
         launch_batch_seed(iv, qp, ws->bslots_dev, nb, dq + (size_t)g * ix->len, s, &ws->launches);
         launch_tc_qprep(ws->bslots_dev, nb, ix->len, qp, w.qtiles, w.qconst, w.Ubits, w.cand_count, w.flags,
-                        w.active, s);
+                        w.active, w.tkinit, w.srange, s);
         ++ws->launches;
         // pass 0 screens the batch; later passes only the queries whose
         // candidate lists overflowed, gathered into the first query tiles
@@ -941,7 +945,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
                 cudaEventRecord(pool_event(ws, evn++), s);
             }
             launch_tc_screen(ix->screen16, ix->xn, ix->xnorm, qt, w.qconst, w.Ubits, w.cand_count, w.cand_pos,
-                             w.active, qm, kTcCap, ix->N, ix->len, count, (int)k, ix->status, s);
+                             w.active, qm, w.tkinit, w.srange, kTcCap, ix->N, ix->len, count, (int)k, ix->status, s);
             screened += count;
             if (ix->profiling) {
                 cudaEventRecord(pool_event(ws, evn++), s);

@@ -162,7 +162,8 @@ k_make_screen_copy(const float *__restrict__ raw, unsigned long long N, int len,
 __global__ void __launch_bounds__(256)
 k_tc_qprep(const QuerySlot *__restrict__ slots, unsigned B, int len, QueryParams qp, __half *__restrict__ qtiles,
            float *__restrict__ qconst, unsigned *__restrict__ Ubits, unsigned *__restrict__ cand_count,
-           unsigned *__restrict__ flags, unsigned *__restrict__ active)
+           unsigned *__restrict__ flags, unsigned *__restrict__ active, float *__restrict__ tkinit,
+           uint2 *__restrict__ srange)
 {
     __shared__ double part[8];
     const unsigned b = blockIdx.x;        // padded up to a multiple of kTcQ
@@ -217,6 +218,19 @@ k_tc_qprep(const QuerySlot *__restrict__ slots, unsigned B, int len, QueryParams
         cand_count[b] = 0;
         flags[b] = f;
         active[b] = (real && f == 0) ? 1u : 0u;
+        // the seed leaf's k best, widened like U (their k-th is U itself)
+        uint2 sr = make_uint2(0u, 0u);
+        if (real && f == 0) {
+            const QueryState *st = slots[b].st;
+            sr = make_uint2(st->seed_lo, st->seed_hi);
+            const unsigned kc = st->kcount;
+            for (int j = 0; j < (int)kTcTopKHost; ++j)
+                tkinit[b * (int)kTcTopKHost + j] = (j < qp.k && (unsigned)j < kc) ? prune_threshold(slots[b].karr[j], qp.F)
+                                                                         : __int_as_float(0x7f800000);
+        } else {
+            for (int j = 0; j < (int)kTcTopKHost; ++j) tkinit[b * (int)kTcTopKHost + j] = __int_as_float(0x7f800000);
+        }
+        srange[b] = sr;
     }
 }
 
@@ -261,6 +275,8 @@ struct ScreenArgs {
     unsigned *cand_pos;       // [QT*128][cap]
     const unsigned *active;   // [QT*128]: nonzero when the query collects candidates this pass
     const unsigned *qmap;     // [B]: batch index of each screened query (nullptr: the identity)
+    const float *tkinit;      // [batch][kTcTopK]: upper ends of the seed leaf's k best (1 < k <= kTcTopK)
+    const uint2 *srange;      // [batch]: the seed leaf's positions [x, y)
     unsigned B;               // queries screened (rows of qtiles in use)
     unsigned cap;
     unsigned qpc;             // query tiles per CTA (1 or 2)
@@ -375,6 +391,7 @@ __device__ __forceinline__ bool epi_bar_any(bool v)
 // taken with a bounded spin; a lane that does not get the lock skips its
 // update, which only leaves the bound looser.
 constexpr int kTcTopK = 16;
+static_assert(kTcTopK == (int)kTcTopKHost, "top-k list length shared with the workspace layout");
 static_assert((kTcSmemBudget - (size_t)2 * kTcQ * kTcResidentLen * 2 - (size_t)2 * kTcQ * kTcTopK * 4) /
                       (kTcRows * 64 * 2) >= 4,
               "two query tiles of the longest resident length, their top-k lists and 4 ring stages fit");
@@ -411,6 +428,7 @@ struct CandidateSink {
     int *lock;           // shared: top-k list locks
     float *topk;         // shared: [QPC * 128][k] top-k lists (1 < k <= kTcTopK)
     const unsigned *qmap;
+    const uint2 *srange; // the seed leaf's positions, whose rows the lists already hold
     unsigned long long N;
     unsigned cap, B;
     int k;
@@ -428,6 +446,12 @@ __device__ __noinline__ void screen_candidate(CandidateSink a, unsigned ql, unsi
     const unsigned o = atomicAdd(&a.cand_count[qj], 1u);
     if (o < a.cap) a.cand_pos[(unsigned long long)qj * a.cap + o] = (unsigned)row;
     if (a.k > kTcTopK) return;
+    // a row of the seed leaf is already in the lists (they start from the
+    // seed's k best): a second entry for it would make the k-th too small
+    if (a.k > 1) {
+        const uint2 sr = a.srange[qj];
+        if (row >= sr.x && row < sr.y) return;
+    }
     // upper end of the estimate: s + eps, rounded up
     const float shat = fmaf(-2.f, acc, xn + qn);
     const float eps = fmaf(xnrm, alpha, gamma + kKappaP * xn);
@@ -658,13 +682,16 @@ k_tc_screen(ScreenArgs a)
             // alpha >= 0: its bits order like the values
             if (own_act) atomicMax(&s_amax, __float_as_uint(a.qconst[4 * own_qj + 1]));
         }
-        if (use_topk)
-            for (unsigned i = tid; i < acc_cols * (unsigned)a.k; i += kTcEpiWarps * 32)
-                topk[i] = __int_as_float(0x7f800000);
+        // each query's list starts from the upper ends of its seed leaf's k
+        // best rows (distinct rows; the screen does not enter them again)
+        if (use_topk && (unsigned)tid < acc_cols)
+            for (int j = 0; j < a.k; ++j)
+                topk[(unsigned)tid * a.k + j] = own_act ? a.tkinit[own_qj * kTcTopK + j] : __int_as_float(0x7f800000);
         epi_bar_sync();
         const float amax = __uint_as_float(s_amax);
         const float one_m_kappa = 1.f - kKappaP;
-        const CandidateSink sink{a.qconst, a.cand_count, a.cand_pos, a.Ubits, sE, sU, sLock, topk, a.qmap, a.N, a.cap, a.B, a.k};
+        const CandidateSink sink{a.qconst, a.cand_count, a.cand_pos, a.Ubits, sE, sU, sLock, topk, a.qmap, a.srange,
+                                 a.N, a.cap, a.B, a.k};
         // series norms of the next tile are fetched one tile ahead
         float nxt_xn = 0.f, nxt_nrm = 0.f;
         auto fetch_norms = [&](unsigned long long j) {
@@ -868,10 +895,11 @@ void launch_make_screen_copy(const float *raw, unsigned long long N, int len, __
 
 void launch_tc_qprep(const QuerySlot *slots, unsigned B, int len, const QueryParams &qp, __half *qtiles,
                      float *qconst, unsigned *Ubits, unsigned *cand_count, unsigned *flags, unsigned *active,
-                     cudaStream_t s)
+                     float *tkinit, uint2 *srange, cudaStream_t s)
 {
     const unsigned padded = (B + kTcQ - 1) / kTcQ * kTcQ;
-    k_tc_qprep<<<padded, 256, 0, s>>>(slots, B, len, qp, qtiles, qconst, Ubits, cand_count, flags, active);
+    k_tc_qprep<<<padded, 256, 0, s>>>(slots, B, len, qp, qtiles, qconst, Ubits, cand_count, flags, active, tkinit,
+                                      srange);
 }
 
 void launch_tc_next_pass(const QuerySlot *slots, unsigned B, const QueryParams &qp, unsigned cap, unsigned *Ubits,
@@ -884,10 +912,12 @@ void launch_tc_next_pass(const QuerySlot *slots, unsigned B, const QueryParams &
 
 void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm, const __half *qtiles,
                       const float *qconst, unsigned *Ubits, unsigned *cand_count, unsigned *cand_pos,
-                      const unsigned *active, const unsigned *qmap, unsigned cap, unsigned long long N, int len,
-                      unsigned B, int k, unsigned *status, cudaStream_t s)
+                      const unsigned *active, const unsigned *qmap, const float *tkinit, const uint2 *srange,
+                      unsigned cap, unsigned long long N, int len, unsigned B, int k, unsigned *status, cudaStream_t s)
 {
     ScreenArgs a;
+    a.tkinit = tkinit;
+    a.srange = srange;
     a.rtiles = rtiles;
     a.xn = xn;
     a.xnorm = xnorm;

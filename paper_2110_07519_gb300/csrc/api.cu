@@ -537,6 +537,7 @@ messi_status messi_build(const float *series, uint64_t n, uint32_t len, uint32_t
         return bail(MESSI_ENOMEM, "messi_build: cannot allocate sort buffers");
     if (cudaMalloc(&ix->ids, n * 4) != cudaSuccess) return bail(MESSI_ENOMEM, "messi_build: out of device memory");
 
+    NvtxRange r_build("messi:build");
     // a non-finite value makes its segment sum non-finite; the kernel flags it
     // in the status word, read once the build has finished
     launch_summarize(dseries, n, ix->len, ix->w, ix->card, ix->beta64, beta32, sax_tmp, keys, ix->ids,
@@ -602,22 +603,27 @@ static cudaError_t enqueue_query(messi_index *ix, Workspace *qws, Workspace *ews
                                  size_t &evn)
 {
     const QuerySlot slot = qws->slot;
+    NvtxRange r_query("messi:query");
     int eq0 = -1, es0 = -1;
     if (ix->profiling >= 2) {
         eq0 = (int)evn;
         cudaEventRecord(pool_event(ews, evn++), s);
     }
+    nvtxRangePushA("messi:prep+seed");
     launch_prep(iv, qp, slot, q, s);
     if (ix->hold_lock) {   // test hook: the k-array lock starts out held
         const cudaError_t e = cudaMemsetAsync(&slot.st->lock, 0xff, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
     }
     launch_seed(iv, qp, slot, s, &ews->launches);
+    nvtxRangePop();
     if (ix->profiling) {
         es0 = (int)evn;
         cudaEventRecord(pool_event(ews, evn++), s);
     }
+    nvtxRangePushA("messi:scan");
     launch_scan(iv, qp, slot, next_epoch(qws, s), s);
+    nvtxRangePop();
     if (ix->profiling) {
         cudaEventRecord(pool_event(ews, evn++), s);
         ews->scan_ev.push_back({es0, es0 + 1});
@@ -628,8 +634,10 @@ static cudaError_t enqueue_query(messi_index *ix, Workspace *qws, Workspace *ews
         r0 = pool_event(ews, evn++);
         r1 = pool_event(ews, evn++);
     }
+    nvtxRangePushA("messi:refine+finalize");
     launch_refine(iv, qp, slot, s, &ews->launches, r0, r1);
     launch_finalize(iv, qp, slot, ids, dists, s);
+    nvtxRangePop();
     ews->launches += 3;
     if (ix->profiling >= 2) {
         cudaEventRecord(pool_event(ews, evn++), s);
@@ -928,6 +936,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
             eq0 = (int)evn;
             cudaEventRecord(pool_event(ws, evn++), s);
         }
+        NvtxRange r_batch("messi:screened batch");
         const TcWs w = tc_ws_view(ix, ws);
         launch_batch_seed(iv, qp, ws->bslots_dev, nb, dq + (size_t)g * ix->len, s, &ws->launches);
         launch_tc_qprep(ws->bslots_dev, nb, ix->len, qp, w.qtiles, w.qconst, w.Ubits, w.cand_count, w.flags,

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include <cuda_fp16.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/messi.h"
 
@@ -240,6 +241,15 @@ struct messi_index {
 namespace messi {
 
 // ------------------------------------------------------------ host helpers
+// NVTX range over a host scope (build phases, a call, the stages of a query
+// as they are enqueued), for profilers that read NVTX; a no-op otherwise.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 void set_error(const std::string &msg);
 messi_status fail(messi_status st, const std::string &msg);
 bool cuda_ok(cudaError_t e, const char *what);

@@ -506,6 +506,8 @@ k_tc_screen(ScreenArgs a)
     __shared__ int sLock[2 * kTcQ];                  // top-k list locks
     __shared__ unsigned s_amax;                      // bits of the CTA's largest alpha
     __shared__ volatile int s_fail;
+    __shared__ unsigned s_fills[kTcMaxStages];                 // bulk-copy fills issued per ring stage
+    __shared__ __align__(8) unsigned long long bar_drain;      // the MMA warp's last commit
     const unsigned len = a.len;
     constexpr unsigned ck = KS * 16;
     const unsigned nch = len / ck;
@@ -536,7 +538,9 @@ k_tc_screen(ScreenArgs a)
         for (unsigned i = 0; i < NS; ++i) {
             mbar_init(&bar_full[i], 1);
             mbar_init(&bar_empty[i], 1);
+            s_fills[i] = 0u;
         }
+        mbar_init(&bar_drain, 1);
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bar_accf[i], 1);
             mbar_init(&bar_acce[i], kTcEpiWarps);
@@ -585,6 +589,7 @@ k_tc_screen(ScreenArgs a)
                                  reinterpret_cast<const unsigned char *>(a.qtiles) +
                                      ((unsigned long long)(qt0 + qi) * nch + c) * chunk_bytes,
                                  chunk_bytes, &bar_full[st]);
+                atomicAdd(&s_fills[st], 1u);
                 st += 2;
                 while (st >= NS) {
                     st -= NS;
@@ -635,6 +640,8 @@ k_tc_screen(ScreenArgs a)
                 if (lane == 0 && !s_fail) tc_commit(&bar_accf[ab]);
                 __syncwarp();
             }
+            // completes once every MMA this thread issued has finished
+            if (lane == 0) tc_commit(&bar_drain);
         }
     } else if (warp == kTcRelayWarp) {
         // ------------------------------------------------ relay
@@ -754,7 +761,24 @@ k_tc_screen(ScreenArgs a)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (s_fail && tid == 0) atomicOr(a.status, kStTimeout);
+    if (tid == 0 && nt > 0) {
+        // the MMA warp's final commit arrives once every MMA it issued has
+        // finished (and after its earlier commits): wait for it before TMEM
+        // and the barriers in shared memory are released
+        const bool drained = mbar_wait_bounded(&bar_drain, 0);
+        if (s_fail || !drained) {
+            atomicOr(a.status, kStTimeout);
+            // after a wait ran out, copies may also be in flight: the last
+            // bulk-copy fill of every ring stage (fill f completes phase f of
+            // its barrier) and the query tiles land first; each wait bounded
+            for (unsigned i = 0; i < NS; ++i)
+                if (s_fills[i]) mbar_wait_bounded(&bar_full[i], (s_fills[i] - 1u) & 1u);
+            if (!qstream) mbar_wait_bounded(&bar_q, 0);
+        }
+    } else if (s_fail && tid == 0) {
+        atomicOr(a.status, kStTimeout);
+    }
+    __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 

@@ -151,19 +151,21 @@ def scan_source_sha(kernel: str = "k_lb_scan"):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(n_series: int, kernel: str):
+def profiled_traffic(units: float, kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
-    to n_series, or None when its source changed since it was captured."""
+    to the units one launch processes (series for the screen, scanned words
+    for the lower-bound scan), or None when its source changed since it was
+    captured."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     try:
         text = open(path).read()
     except OSError:
         return None
     sha = re.search(r"source_sha:\s*(\w+)", text)
-    per = re.search(r"dram_bytes_per_series:\s*([0-9.eE+-]+)", text)
+    per = re.search(r"dram_bytes_per_(?:series|word):\s*([0-9.eE+-]+)", text)
     if not sha or not per or sha.group(1) != scan_source_sha(kernel):
         return None
-    return float(per.group(1)) * n_series
+    return float(per.group(1)) * units
 
 
 def replica_elapsed_ms(pg, elapsed_ms, device="cpu"):
@@ -529,7 +531,8 @@ def run_messi(args, ws, rank, local):
         forms["plain"]["per_class"] = per_class
     head_form = max(forms, key=lambda f: forms[f]["value"])
     head = forms[head_form]
-    traffic = profiled_traffic(args.n, head["roofline"]["kernel"])
+    hk = head["roofline"]["kernel"]
+    traffic = profiled_traffic(head["counters"]["words_scanned_per_query"] if hk == "k_lb_scan" else args.n, hk)
     head["roofline"]["traffic"] = traffic
 
     # end to end through the C ABI with host buffers (pinned), copies inside

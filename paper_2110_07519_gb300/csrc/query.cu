@@ -1176,69 +1176,117 @@ k_fused_ed(IndexView iv, QueryParams qp, const QuerySlot *__restrict__ slots, un
 }
 
 // ------------------------------------------------- DTW, one thread per candidate
-// Band of width W = 2R+1 (R >= r, the window; band cells farther than r from
-// the diagonal are +inf) held in registers: D[b] is the cell (i, i - R + b) of
-// the current row, xw[b] the candidate value x[i - R + b].  Row by row each
-// thread updates its band in place (diagonal = old D[b], up = old D[b+1],
-// left = new D[b-1]) -- the same recurrence, operands and FP32 operations as
-// the warp wavefront -- and abandons when a row minimum exceeds the live
-// threshold (every warping path crosses every row).  Threads advance
-// independently through their own candidates (a strided share of the list).
-template <int R, bool CHECK>
-__device__ __forceinline__ float dtw_row(float (&D)[2 * R + 1], const float (&xw)[2 * R + 1], float qi, int i, int n,
-                                         int r)
+// The recurrence is symmetric in its two series (the band |i - j| <= r and
+// the three predecessors map onto themselves under a transpose, and
+// (q_i - x_j)^2 = (x_j - q_i)^2 exactly), so the walk goes column by column
+// of the candidate: D[b] is the cell (i, j) = (j - R + b, j) of column j in
+// a band of width W = 2R+1 (R >= r; band cells farther than r from the
+// diagonal are +inf), held in registers.  Column by column each thread
+// updates its band in place (diagonal = old D[b], from the previous column
+// = old D[b+1], from the same column = new D[b-1]) and abandons when a
+// column minimum exceeds the live threshold (every warping path crosses
+// every column; the minimum is taken every fourth column).  The candidate
+// contributes one value per column; the query values of the band come from
+// shared memory, where the query is stored four times, shifted by 0..3
+// points and padded with +inf, so that any four consecutive values are one
+// aligned 16-byte load (a broadcast: every thread of a warp walks the same
+// query).  A band cell off the ends of the query meets a +inf value, so its
+// cost (x_j - inf)^2 is +inf and it stays +inf without a test; when the
+// window equals the reach (r == R) no cell needs a test at all.  Threads
+// advance independently through their own candidates (a strided share of
+// the list).
+constexpr int kDtwPad = 36;   // padding of each shifted copy: >= 32 + 3, a multiple of 4
+
+// floats per shifted copy of an n-point query (a multiple of 4, so that
+// every copy starts 16-byte aligned)
+__host__ __device__ __forceinline__ int dtw_qstride(int n) { return (n + 2 * kDtwPad + 3) & ~3; }
+
+// minimum of three floats in one instruction
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// fill the four shifted copies: Qs[s * S + t] = q[t + s - kDtwPad] (+inf outside)
+__device__ __forceinline__ void dtw_fill_query(float *Qs, const float *__restrict__ q, int n)
+{
+    const int S = dtw_qstride(n);
+    for (int e = threadIdx.x; e < 4 * S; e += blockDim.x) {
+        const int sh = e / S, t = e - sh * S;
+        const int m = t + sh - kDtwPad;
+        Qs[e] = (m >= 0 && m < n) ? q[m] : f_inf();
+    }
+}
+
+// one column; BAND: cells farther than r from the diagonal are forced to
+// +inf (only when r < R)
+template <int R, bool BAND>
+__device__ __forceinline__ void dtw_col(float (&D)[2 * R + 1], const float *__restrict__ Qs, int S, float xj, int j,
+                                        int r)
 {
     constexpr int W = 2 * R + 1;
+    constexpr int NV = (W + 3) / 4;
     const float INF = f_inf();
-    float left = INF, rmin = INF;
+    // q[j - R + b] for b = 0 .. W-1, from the copy whose shift aligns them
+    const int t0 = j - R + kDtwPad;
+    const int sh = t0 & 3;
+    const float4 *qv = reinterpret_cast<const float4 *>(Qs + sh * S + (t0 - sh));
+    float left = INF;
 #pragma unroll
-    for (int b = 0; b < W; ++b) {
-        const float up = (b + 1 < W) ? D[b + 1] : INF;
-        const float best = fminf(fminf(D[b], up), left);
-        const float d = qi - xw[b];
-        float v;
-        if (CHECK) {
-            const int j = i - R + b;
-            const bool inside = j >= 0 && j < n && (b - R <= r) && (R - b <= r);
-            v = inside ? d * d + best : INF;
-        } else {
-            v = d * d + best;
+    for (int c = 0; c < NV; ++c) {
+        const float4 q4 = qv[c];
+        const float qq[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int b = 4 * c + u;
+            if (b < W) {
+                const float up = (b + 1 < W) ? D[b + 1] : INF;
+                const float best = min3f(D[b], up, left);
+                const float d = xj - qq[u];
+                float v = d * d + best;
+                if (BAND) v = (b - R <= r && R - b <= r) ? v : INF;
+                D[b] = v;
+                left = v;
+            }
         }
-        D[b] = v;
-        left = v;
-        rmin = fminf(rmin, v);
     }
-    return rmin;
+}
+
+// minimum of the band
+template <int R>
+__device__ __forceinline__ float dtw_band_min(const float (&D)[2 * R + 1])
+{
+    constexpr int W = 2 * R + 1;
+    float m = D[0];
+#pragma unroll
+    for (int b = 1; b + 1 < W; b += 2) m = min3f(m, D[b], D[b + 1]);
+    return m;
 }
 
 template <int R>
-__device__ __forceinline__ float thread_dtw(const float *__restrict__ qs, const float *__restrict__ x, int n, int r,
-                                            float thr, int &rows)
+__device__ __forceinline__ float thread_dtw(const float *__restrict__ Qs, const float *__restrict__ x, int n, int r,
+                                            float thr, int &cols)
 {
     constexpr int W = 2 * R + 1;
     const float INF = f_inf();
-    float D[W], xw[W];
+    const int S = dtw_qstride(n);
+    float D[W];
 #pragma unroll
-    for (int b = 0; b < W; ++b) {
-        D[b] = (b == R) ? 0.f : INF;                      // row -1: only the diagonal of (0, 0) is open
-        const int j = b - R;                              // x index of band cell b in row 0
-        xw[b] = (j >= 0 && j < n) ? __ldg(x + j) : 0.f;
-    }
-    // rows whose whole band lies inside the matrix, when the window is the
-    // band reach itself, need no per-cell test: [R, n - R)
-    const bool exact = r == R;
-    const int in_lo = exact ? R : n, in_hi = exact ? n - R : n;
-    for (int i = 0; i < n; ++i) {
-        const float qi = qs[i];
-        const float rmin = (i >= in_lo && i < in_hi) ? dtw_row<R, false>(D, xw, qi, i, n, r)
-                                                     : dtw_row<R, true>(D, xw, qi, i, n, r);
-        rows = i + 1;
-        if (rmin > thr) return rmin;
-        // slide the candidate window by one
-#pragma unroll
-        for (int b = 0; b + 1 < W; ++b) xw[b] = xw[b + 1];
-        const int jn = i + 1 + R;
-        xw[W - 1] = (jn < n) ? __ldg(x + jn) : 0.f;
+    for (int b = 0; b < W; ++b) D[b] = (b == R) ? 0.f : INF;   // column -1: only the diagonal of (0, 0) is open
+    const bool band = r != R;
+    float xn = __ldg(x);
+    for (int j = 0; j < n; ++j) {
+        const float xj = xn;
+        if (j + 1 < n) xn = __ldg(x + j + 1);
+        if (band) dtw_col<R, true>(D, Qs, S, xj, j, r);
+        else dtw_col<R, false>(D, Qs, S, xj, j, r);
+        cols = j + 1;
+        if ((j & 3) == 3) {
+            const float cmin = dtw_band_min<R>(D);
+            if (cmin > thr) return cmin;
+        }
     }
     return D[R];
 }
@@ -1250,8 +1298,8 @@ k_dtw_thread(IndexView iv, QueryParams qp, QuerySlot slot)
     extern __shared__ __align__(16) unsigned char dsm[];
     QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
-    float *qs = reinterpret_cast<float *>(dsm);
-    for (int i = threadIdx.x; i < iv.len; i += blockDim.x) qs[i] = slot.q[i];
+    float *Qs = reinterpret_cast<float *>(dsm);
+    dtw_fill_query(Qs, slot.q, iv.len);
     __syncthreads();
     const unsigned lo = MODE ? st->seed_lo : 0u;
     const unsigned count = MODE ? st->seed_hi - st->seed_lo : ld_volatile_u32(&st->ord_count);
@@ -1267,9 +1315,9 @@ k_dtw_thread(IndexView iv, QueryParams qp, QuerySlot slot)
             if (order_floor(order_bucket(lb)) > thr) break;
             if (lb > thr) continue;
         }
-        int rows = 0;
-        const float d2 = thread_dtw<R>(qs, iv.raw + (unsigned long long)pos * iv.len, iv.len, qp.r, thr, rows);
-        cells += (unsigned long long)rows * (unsigned)(2 * qp.r + 1);   // band cells of the rows computed
+        int cols = 0;
+        const float d2 = thread_dtw<R>(Qs, iv.raw + (unsigned long long)pos * iv.len, iv.len, qp.r, thr, cols);
+        cells += (unsigned long long)cols * (unsigned)(2 * qp.r + 1);   // band cells of the columns computed
         if (MODE) {
             slot.seedbuf[e] = pack_cand(d2, iv.ids[pos]);
         } else if (d2 <= thr) {
@@ -1346,43 +1394,71 @@ __device__ __forceinline__ float lbk_improved_thread(const float *__restrict__ q
 }
 
 // The same bound when the window is exactly R (r == R), with the extremes of
-// each window from van Herk / Gil-Werman blocks of W = 2R + 1 steps instead of
-// a scan of the window: within a block, a running prefix extreme; from the
-// previous block, its suffix extremes (a window ending at block slot k is the
-// previous block's slots k + 1 .. W - 1 and the current slots 0 .. k).  The
-// previous block's slot k is last read at step k - 1, so step k overwrites it
-// with the new value, and the block's end turns the new values into suffix
-// extremes in place.  About six min / max per step instead of 3W.
+// each window from van Herk / Gil-Werman blocks instead of a scan of the
+// window.  The blocks hold B = W + 1 = 2R + 2 steps, one more than the window
+// W = 2R + 1, so that B is even (a multiple of 4 when R is odd) and every
+// block starts on a vector boundary: the row and the envelope are read two or
+// four points per load (the row's loads are the filter's bottleneck: each
+// lane reads its own row, so a warp's load touches 32 lines).  A window
+// ending at block slot k covers:
+//   k <= B - 3: the previous block's slots k + 2 .. B - 1 (its suffix
+//               extreme) and the current slots 0 .. k (a running prefix);
+//   k =  B - 2: the current slots 0 .. B - 2 (the prefix);
+//   k =  B - 1: the current slots 1 .. B - 1 (the block's own suffix from 1,
+//               formed first at the block's end).
+// The previous block's slot k is last read at step k - 2, so step k
+// overwrites it with the new value, and the block's end turns the new values
+// into suffix extremes in place.  About six min / max per step instead of 3W.
 template <int R>
 __device__ __forceinline__ float lbk_improved_blocks(const float *__restrict__ qs, const float *__restrict__ Us,
                                                      const float *__restrict__ Ls, const float *__restrict__ x,
                                                      int n, float thr)
 {
     constexpr int W = 2 * R + 1;
-    float smx[W], smn[W];
+    constexpr int B = W + 1;
+    constexpr int VW = (B % 4 == 0) ? 4 : 2;   // points per vector load (n is a multiple of 4)
+    float smx[B], smn[B];
     float hlast;
     {
         const float c0 = __ldg(x);
         hlast = fminf(fmaxf(c0, Ls[0]), Us[0]);
 #pragma unroll
-        for (int b = 0; b < W; ++b) {
+        for (int b = 0; b < B; ++b) {
             smx[b] = hlast;
             smn[b] = hlast;
         }
     }
     float acc1 = 0.f, acc2 = 0.f;
-    for (int j0 = 0; j0 < n + R; j0 += W) {
-        // this lane's row is read one value at a time: ask L1 for the lines
-        // of the next block early so several rows' misses overlap
-        if (j0 + W < n) prefetch_l1(x + j0 + W);
-        if (j0 + W + 32 < n) prefetch_l1(x + j0 + W + 32);
+    for (int j0 = 0; j0 < n + R; j0 += B) {
+        // this lane's row: ask L1 for the lines of the next block early so
+        // several rows' misses overlap
+        if (j0 + B < n) prefetch_l1(x + j0 + B);
+        if (j0 + B + 32 < n) prefetch_l1(x + j0 + B + 32);
         float pmx = 0.f, pmn = 0.f;
+        float cv[VW], uv[VW], lv[VW];
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
+        for (int k = 0; k < B; ++k) {
             const int j = j0 + k;
+            if (k % VW == 0 && j < n) {   // j0 and k are multiples of VW: aligned, and j + VW <= n
+                if (VW == 4) {
+                    const float4 c4 = __ldg(reinterpret_cast<const float4 *>(x + j));
+                    const float4 u4 = *reinterpret_cast<const float4 *>(Us + j);
+                    const float4 l4 = *reinterpret_cast<const float4 *>(Ls + j);
+                    cv[0] = c4.x; cv[1] = c4.y; cv[VW > 2 ? 2 : 0] = c4.z; cv[VW > 3 ? 3 : 0] = c4.w;
+                    uv[0] = u4.x; uv[1] = u4.y; uv[VW > 2 ? 2 : 0] = u4.z; uv[VW > 3 ? 3 : 0] = u4.w;
+                    lv[0] = l4.x; lv[1] = l4.y; lv[VW > 2 ? 2 : 0] = l4.z; lv[VW > 3 ? 3 : 0] = l4.w;
+                } else {
+                    const float2 c2 = __ldg(reinterpret_cast<const float2 *>(x + j));
+                    const float2 u2 = *reinterpret_cast<const float2 *>(Us + j);
+                    const float2 l2 = *reinterpret_cast<const float2 *>(Ls + j);
+                    cv[0] = c2.x; cv[1] = c2.y;
+                    uv[0] = u2.x; uv[1] = u2.y;
+                    lv[0] = l2.x; lv[1] = l2.y;
+                }
+            }
             float h = hlast;
             if (j < n) {
-                const float c = __ldg(x + j), u = Us[j], l = Ls[j];
+                const float c = cv[k % VW], u = uv[k % VW], l = lv[k % VW];
                 float d = 0.f;
                 if (c > u) d = __fsub_rd(c, u);
                 else if (c < l) d = __fsub_rd(l, c);
@@ -1392,10 +1468,22 @@ __device__ __forceinline__ float lbk_improved_blocks(const float *__restrict__ q
             }
             pmx = (k == 0) ? h : fmaxf(pmx, h);
             pmn = (k == 0) ? h : fminf(pmn, h);
-            const float mx = (k + 1 < W) ? fmaxf(smx[k + 1 < W ? k + 1 : 0], pmx) : pmx;
-            const float mn = (k + 1 < W) ? fminf(smn[k + 1 < W ? k + 1 : 0], pmn) : pmn;
+            float mx = pmx, mn = pmn;
+            if (k + 2 < B) {
+                mx = fmaxf(smx[k + 2 < B ? k + 2 : 0], pmx);
+                mn = fminf(smn[k + 2 < B ? k + 2 : 0], pmn);
+            }
             smx[k] = h;
             smn[k] = h;
+            if (k + 1 == B) {
+#pragma unroll
+                for (int kk = B - 2; kk >= 0; --kk) {
+                    smx[kk] = fmaxf(smx[kk], smx[kk + 1]);
+                    smn[kk] = fminf(smn[kk], smn[kk + 1]);
+                }
+                mx = smx[1];
+                mn = smn[1];
+            }
             const int p = j - R;
             if (p >= 0 && p < n) {
                 const float qv = qs[p];
@@ -1405,21 +1493,13 @@ __device__ __forceinline__ float lbk_improved_blocks(const float *__restrict__ q
                 acc2 = __fadd_rd(acc2, __fmul_rd(d, d));
             }
         }
-#pragma unroll
-        for (int k = W - 2; k >= 0; --k) {
-            smx[k] = fmaxf(smx[k], smx[k + 1]);
-            smn[k] = fminf(smn[k], smn[k + 1]);
-        }
         if (__fadd_rd(acc1, acc2) > thr) break;
     }
     return __fadd_rd(acc1, acc2);
 }
 
-// The DTW filter with one candidate per lane: a warp takes 32 scan survivors
-// at a time, each lane bounds its own; passing candidates are appended to
-// surv2 / surv2_lb with one atomic per warp.
 template <int R>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (R <= 25) ? 2 : 1)
 k_lbk_thread(IndexView iv, QueryParams qp, QuerySlot slot)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -1489,10 +1569,14 @@ bool launch_dtw_thread(const IndexView &iv, const QueryParams &qp, const QuerySl
 {
     const int R = dtw_thread_reach(qp.r);
     const unsigned grid = num_sms() * 8;
-    const size_t sm = (size_t)iv.len * 4;
+    const size_t sm = (size_t)4 * dtw_qstride(iv.len) * sizeof(float);   // the four shifted query copies
     switch (R) {
-#define MESSI_DTW_CASE(RR) \
-    case RR: k_dtw_thread<RR, MODE><<<grid, 128, sm, s>>>(iv, qp, slot); return true;
+#define MESSI_DTW_CASE(RR)                                                                                \
+    case RR:                                                                                              \
+        if (sm > 48 * 1024)                                                                               \
+            cudaFuncSetAttribute(k_dtw_thread<RR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        k_dtw_thread<RR, MODE><<<grid, 128, sm, s>>>(iv, qp, slot);                                       \
+        return true;
         MESSI_DTW_CASE(0)
         MESSI_DTW_CASE(1)
         MESSI_DTW_CASE(2)

@@ -39,7 +39,11 @@ constexpr int kTcQ = 128;           // N: queries per tile
 constexpr float kKappa = 2.4e-7f;   // 4u: FP32 evaluation of s and rounding of the norms
 constexpr float kKappaP = 7.2e-7f;  // 12u: kappa plus the rounding of the rearranged test
 constexpr int kTcMaxStages = 16;
-constexpr size_t kTcSmemBudget = 216 * 1024;   // dynamic shared memory of one screen CTA
+// dynamic shared memory of one screen CTA: the 227 KB a block may hold, less
+// the kernel's 4 KB of static shared memory and 1 KB of margin, so that at
+// 256 points two resident query tiles (128 KB), top-k lists up to k = 14 and
+// five 16 KB ring stages fit together
+constexpr size_t kTcSmemBudget = 222 * 1024;
 
 // K width of one streamed chunk of a series tile: the largest of 64, 32, 16
 // dividing len.  A tile is stored chunk-major: chunk c (k in [c*ck, c*ck+ck))
@@ -68,6 +72,14 @@ __host__ __device__ __forceinline__ unsigned qtile_offset(unsigned r, unsigned k
 {
     const unsigned qc = query_chunk(len);
     return qc ? (k / qc) * (kTcQ * qc * 2) + tc_offset(r, k % qc, qc) : tc_offset(r, k, len);
+}
+
+// minimum of three floats in one instruction
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
 
 __device__ __forceinline__ float tc_coef(int len)
@@ -726,22 +738,35 @@ k_tc_screen(ScreenArgs a)
                     float acc[64];
                     tmem_ld64(tmem + ((lg * 32) << 16) + ab * acc_cols + cbeg + h, acc);
                     const float4 *e4 = reinterpret_cast<const float4 *>(&sE[cbeg + h]);
-                    bool hit = false;
+                    // v = E_q - 2 acc rounded down is at most its exact value, so
+                    // min over q of v <= r whenever a pair passes 2 acc + r >= E_q
+                    // exactly; one minimum per group of 16 queries
+                    float mn[4];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float4 e = e4[i];
-                        hit |= __fmaf_ru(2.f, acc[4 * i + 0], r) >= e.x;
-                        hit |= __fmaf_ru(2.f, acc[4 * i + 1], r) >= e.y;
-                        hit |= __fmaf_ru(2.f, acc[4 * i + 2], r) >= e.z;
-                        hit |= __fmaf_ru(2.f, acc[4 * i + 3], r) >= e.w;
+                    for (int gq = 0; gq < 4; ++gq) {
+                        float m0 = __int_as_float(0x7f800000), m1 = m0;
+#pragma unroll
+                        for (int i = 4 * gq; i < 4 * gq + 4; ++i) {
+                            const float4 e = e4[i];
+                            m0 = min3f(m0, __fmaf_rd(-2.f, acc[4 * i + 0], e.x), __fmaf_rd(-2.f, acc[4 * i + 1], e.y));
+                            m1 = min3f(m1, __fmaf_rd(-2.f, acc[4 * i + 2], e.z), __fmaf_rd(-2.f, acc[4 * i + 3], e.w));
+                        }
+                        mn[gq] = fminf(m0, m1);
                     }
+                    const bool hit = min3f(mn[0], mn[1], fminf(mn[2], mn[3])) <= r;
                     if (__any_sync(0xffffffffu, hit)) {
-                        // unrolled so the accumulators stay in registers
+                        // the groups some lane flagged, each pair re-tested in the
+                        // kernel's rearranged form; unrolled so the accumulators
+                        // stay in registers
 #pragma unroll
-                        for (int i = 0; i < 64; ++i) {
-                            const unsigned ql = cbeg + h + i;
-                            if (__fmaf_ru(2.f, acc[i], r) >= sE[ql])
-                                screen_candidate(sink, ql, qt0 * kTcQ + ql, row, acc[i], xn, xnrm);
+                        for (int gq = 0; gq < 4; ++gq) {
+                            if (!__any_sync(0xffffffffu, mn[gq] <= r)) continue;
+#pragma unroll
+                            for (int i = 16 * gq; i < 16 * gq + 16; ++i) {
+                                const unsigned ql = cbeg + h + i;
+                                if (__fmaf_ru(2.f, acc[i], r) >= sE[ql])
+                                    screen_candidate(sink, ql, qt0 * kTcQ + ql, row, acc[i], xn, xnrm);
+                            }
                         }
                     }
                 }

@@ -2,10 +2,13 @@
 
 When the window reach equals the kernel's template reach, the second
 LB_Improved term takes each point's envelope of h (the candidate clamped into
-the query's envelope) from blocks of W = 2R + 1 points: a prefix max/min over
-the current block and a suffix max/min over the previous one, read R points
-behind the newest; below it, the register-window walk reads the newest 2r + 1
-of 2R + 1 slots.  This restates both walks step by step (float32 values,
+the query's envelope, a window of W = 2R + 1 points) from blocks of B = W + 1
+points: a window ending at block slot k <= B - 3 is the previous block's
+suffix from slot k + 2 and the current block's prefix to k; at k = B - 2 the
+prefix alone; at k = B - 1 the current block's own suffix from slot 1.  The
+row and the envelope are read 4 points per load when B is a multiple of 4,
+else 2, from positions that are multiples of that width.  Below the template
+reach, the register-window walk reads the newest 2r + 1 of 2R + 1 slots.  This restates both walks step by step (float32 values,
 sums rounded toward -inf) and checks that (a) every envelope it forms equals
 the window max/min of h taken directly, clipped at the ends, and (b) the
 bound never exceeds the oracle's FP64 LB_Improved."""
@@ -26,17 +29,25 @@ def rd32(fr: Fr) -> float:
 
 def blocked_model(q, U, L, x, R):
     n, W = q.size, 2 * R + 1
+    B = W + 1
+    VW = 4 if B % 4 == 0 else 2
+    assert n % 4 == 0                      # series lengths are multiples of 4
     hlast = float(min(max(x[0], L[0]), U[0]))
-    smx, smn = [hlast] * W, [hlast] * W
+    smx, smn = [hlast] * B, [hlast] * B
     acc1 = acc2 = 0.0
     env = {}
-    for j0 in range(0, n + R, W):
+    for j0 in range(0, n + R, B):
         pmx = pmn = 0.0
-        for k in range(W):
+        cv = uv = lv = None
+        for k in range(B):
             j = j0 + k
+            if k % VW == 0 and j < n:
+                assert j % VW == 0 and j + VW <= n             # an aligned vector load inside the row
+                cv, uv, lv = x[j:j + VW], U[j:j + VW], L[j:j + VW]
             h = hlast
             if j < n:
-                c, u, l = float(x[j]), float(U[j]), float(L[j])
+                c, u, l = float(cv[k % VW]), float(uv[k % VW]), float(lv[k % VW])
+                assert (c, u, l) == (float(x[j]), float(U[j]), float(L[j]))
                 d = 0.0
                 if c > u:
                     d = rd32(Fr(c) - Fr(u))
@@ -47,10 +58,16 @@ def blocked_model(q, U, L, x, R):
                 hlast = h
             pmx = h if k == 0 else max(pmx, h)
             pmn = h if k == 0 else min(pmn, h)
-            mx = max(smx[k + 1], pmx) if k + 1 < W else pmx
-            mn = min(smn[k + 1], pmn) if k + 1 < W else pmn
+            mx, mn = pmx, pmn
+            if k + 2 < B:
+                mx, mn = max(smx[k + 2], pmx), min(smn[k + 2], pmn)
             smx[k] = h
             smn[k] = h
+            if k + 1 == B:
+                for kk in range(B - 2, -1, -1):
+                    smx[kk] = max(smx[kk], smx[kk + 1])
+                    smn[kk] = min(smn[kk], smn[kk + 1])
+                mx, mn = smx[1], smn[1]
             p = j - R
             if 0 <= p < n:
                 env[p] = (mx, mn)
@@ -61,13 +78,11 @@ def blocked_model(q, U, L, x, R):
                 elif qv < mn:
                     d = rd32(Fr(mn) - Fr(qv))
                 acc2 = rd32(Fr(acc2) + Fr(rd32(Fr(d) * Fr(d))))
-        for k in range(W - 2, -1, -1):
-            smx[k] = max(smx[k], smx[k + 1])
-            smn[k] = min(smn[k], smn[k + 1])
     return rd32(Fr(acc1) + Fr(acc2)), env
 
 
-@pytest.mark.parametrize("n,R", [(16, 1), (16, 4), (33, 2), (100, 6), (128, 12), (256, 25), (40, 13)])
+@pytest.mark.parametrize("n,R", [(16, 1), (16, 4), (36, 2), (100, 6), (128, 12), (256, 25), (40, 13),
+                                 (8, 0), (64, 32), (256, 20), (12, 8)])
 def test_blocked_envelopes_and_bound(n, R):
     rng = np.random.default_rng(n * 31 + R)
     for trial in range(20):

@@ -14,6 +14,7 @@ whose f16 rounding errors all share one sign (the worst case of the f16
 term), on rows near the f16 subnormal range and near its maximum, for every
 length the screen takes (16 .. 2048)."""
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -130,6 +131,16 @@ def rd(v):
     return float(r) if float(r) <= v else float(np.nextafter(r, np.float32(-np.inf)))
 
 
+def rd_exact(v):
+    # a rational rounded down to float32 (the fma's single rounding)
+    r = np.float32(float(v))
+    while Fraction(float(r)) > v:
+        r = np.nextafter(r, np.float32(-np.inf))
+    while Fraction(float(np.nextafter(r, np.float32(np.inf)))) <= v:
+        r = np.nextafter(r, np.float32(np.inf))
+    return float(r)
+
+
 def norms(v):
     ss = 0.0
     for t in v.astype(np.float64):
@@ -170,6 +181,9 @@ def test_candidate_test_has_no_false_negatives(n, scale):
             E = rd(rd(qn - gamma) - U)                               # __fsub_rd twice
             r = ru(xnrm * alpha + ru(-xn * omk))                     # __fmaf_ru(xnrm, amax, __fmul_ru(..))
             assert ru(2.0 * c + r) >= E, (n, scale, sigma, mode)     # __fmaf_ru(2, acc, r) >= E
+            # the warp's first test: E - 2 acc by a packed FMA rounded down, its
+            # minimum over the queries against r
+            assert rd_exact(Fraction(E) - 2 * Fraction(c)) <= r, (n, scale, sigma, mode)
             lhs = rn(xnrm * alpha + rn(2.0 * c + rn(-xn * omk)))     # fmaf(xnrm, alpha, fmaf(2, acc, -xn omk))
             assert lhs >= E, (n, scale, sigma, mode)
 

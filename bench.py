@@ -143,10 +143,22 @@ def measured_peak_hbm():
 
 
 def scan_source_sha(kernel: str = "k_lb_scan"):
+    """Hash of the source a traffic figure was measured on: the screen's files
+    whole; for the scan, the part of query.cu from its code table to the end
+    of the scan kernel, and the shared device helpers."""
     h = hashlib.sha256()
-    files = ("screen.cu", "tc.cuh", "device_common.cuh") if kernel == "k_tc_screen" else ("query.cu", "device_common.cuh")
-    for name in files:
-        with open(os.path.join(ROOT, "paper_2110_07519_gb300", "csrc", name), "rb") as f:
+    csrc = os.path.join(ROOT, "paper_2110_07519_gb300", "csrc")
+    if kernel == "k_tc_screen":
+        for name in ("screen.cu", "tc.cuh", "device_common.cuh"):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    else:
+        with open(os.path.join(csrc, "query.cu"), "rb") as f:
+            text = f.read()
+        a = text.find(b"struct ScanCodes {")
+        b = text.find(b"// ------------------------------------------------------------ ED refine")
+        h.update(text[a:b] if 0 <= a < b else text)
+        with open(os.path.join(csrc, "device_common.cuh"), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 

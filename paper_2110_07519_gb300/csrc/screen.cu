@@ -38,12 +38,14 @@ constexpr int kTcRows = 128;        // M: series per tile
 constexpr int kTcQ = 128;           // N: queries per tile
 constexpr float kKappa = 2.4e-7f;   // 4u: FP32 evaluation of s and rounding of the norms
 constexpr float kKappaP = 7.2e-7f;  // 12u: kappa plus the rounding of the rearranged test
+static_assert(kKappaP >= 3.f * kKappa, "the rearranged test's slack covers kappa and 8u more");
 constexpr int kTcMaxStages = 16;
 // dynamic shared memory of one screen CTA: the 227 KB a block may hold, less
-// the kernel's 4 KB of static shared memory and 1 KB of margin, so that at
-// 256 points two resident query tiles (128 KB), top-k lists up to k = 14 and
-// five 16 KB ring stages fit together
-constexpr size_t kTcSmemBudget = 222 * 1024;
+// the kernel's 5.4 KB of static shared memory (barriers, per-query bounds,
+// the candidate queue) and some margin, so that at 256 points two resident
+// query tiles (128 KB), top-k lists up to k = 12 and five 16 KB ring stages
+// fit together
+constexpr size_t kTcSmemBudget = 221 * 1024;
 
 // K width of one streamed chunk of a series tile: the largest of 64, 32, 16
 // dividing len.  A tile is stored chunk-major: chunk c (k in [c*ck, c*ck+ck))
@@ -344,9 +346,15 @@ struct ScreenArgs {
 // may leave the looser one in place; every stored E_q still derives from a
 // valid U_q, so the test stays conservative.
 constexpr int kTcEpiWarps = 8;
-constexpr int kTcCtrlThreads = kTcEpiWarps * 32 + 128;    // + 2 producer warps + MMA warp + relay warp
+// + 2 producer warps + MMA warp + relay warp + candidate warp
+constexpr int kTcCtrlThreads = kTcEpiWarps * 32 + 160;
 constexpr int kTcProdWarp0 = kTcEpiWarps, kTcMmaWarp = kTcEpiWarps + 1, kTcProdWarp1 = kTcEpiWarps + 2,
-              kTcRelayWarp = kTcEpiWarps + 3;
+              kTcRelayWarp = kTcEpiWarps + 3, kTcCandWarp = kTcEpiWarps + 4;
+// Candidate queue of a CTA: the epilogue warps append the pairs that pass
+// their test and the candidate warp records them (global slot, top-k list,
+// bounds), so the epilogue never waits on that work.  Entry t lives in slot
+// t mod kTcCq and is ready once its sequence word holds t + 1.
+constexpr unsigned kTcCq = 64;
 
 // Named barrier 3: the MMA warp and the relay warp, once per chunk.
 __device__ __forceinline__ void relay_bar_sync() { asm volatile("bar.sync 3, 64;" ::: "memory"); }
@@ -428,10 +436,10 @@ __device__ __forceinline__ void topk_unlock(int *l)
     atomicExch(l, 0);
 }
 
-// Rare path of the epilogue: the pair (query, series row) passed the test
-// with the CTA's largest alpha; re-test it with the query's own alpha, record
-// it as a candidate, and for k <= kTcTopK lower the query's bound U with the
-// upper end of its estimate.
+// A queued pair (query, series row) passed the epilogue's test with the CTA's
+// largest alpha: the candidate warp re-tests it with the query's own alpha,
+// records it as a candidate, and for k <= kTcTopK lowers the query's bound U
+// with the upper end of its estimate.
 struct CandidateSink {
     const float *qconst;
     unsigned *cand_count, *cand_pos, *Ubits;
@@ -446,8 +454,8 @@ struct CandidateSink {
     int k;
 };
 
-__device__ __noinline__ void screen_candidate(CandidateSink a, unsigned ql, unsigned qc, unsigned long long row,
-                                              float acc, float xn, float xnrm)
+__device__ __forceinline__ void screen_candidate(const CandidateSink &a, unsigned ql, unsigned qc, unsigned long long row,
+                                                 float acc, float xn, float xnrm)
 {
     if (row >= a.N || qc >= a.B) return;
     const unsigned qj = a.qmap ? a.qmap[qc] : qc;      // the query's batch index
@@ -493,6 +501,34 @@ __device__ __noinline__ void screen_candidate(CandidateSink a, unsigned ql, unsi
     }
 }
 
+// Epilogue side of the candidate queue (the warp converged): the lanes whose
+// pair passed reserve consecutive entries with one shared atomic, each waits
+// (bounded) until its slot is free, writes the entry and publishes it.  A
+// slot t stays free once the candidate warp has taken entries up to t - kTcCq.
+__device__ __forceinline__ void cq_push(bool pass, unsigned row, unsigned ql, float acc, uint4 *q, unsigned *seq,
+                                        unsigned *tail, volatile unsigned *head, volatile int *fail)
+{
+    const unsigned bal = __ballot_sync(0xffffffffu, pass);
+    if (!bal) return;
+    const unsigned lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(tail, (unsigned)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (!pass) return;
+    const unsigned t = base + __popc(bal & ((1u << lane) - 1u));
+    for (unsigned it = 0; t - *head >= kTcCq; ++it) {
+        if (it >= kSpinLimit || *fail) {   // (after a failure the candidate warp may be gone)
+            *fail = 1;
+            return;
+        }
+        __nanosleep(32);
+    }
+    __threadfence_block();
+    q[t % kTcCq] = make_uint4(row, ql, __float_as_uint(acc), 0u);
+    __threadfence_block();
+    *reinterpret_cast<volatile unsigned *>(&seq[t % kTcCq]) = t + 1u;
+}
+
 // One chunk of KS 16-wide k-steps: series operand `rd` (ring stage) against
 // the query operand `qd`; k-step kk starts kk * 256 bytes further in both.
 template <int KS>
@@ -520,6 +556,12 @@ k_tc_screen(ScreenArgs a)
     __shared__ volatile int s_fail;
     __shared__ unsigned s_fills[kTcMaxStages];                 // bulk-copy fills issued per ring stage
     __shared__ __align__(8) unsigned long long bar_drain;      // the MMA warp's last commit
+    __shared__ uint4 s_cq[kTcCq];                              // candidate queue: row, query slot, acc bits
+    __shared__ unsigned s_cq_seq[kTcCq];                       // slot ready for entry t: t + 1
+    __shared__ unsigned s_cq_tail;                             // entries reserved
+    __shared__ volatile unsigned s_cq_head;                    // entries taken by the candidate warp
+    __shared__ unsigned s_epi_done;                            // epilogue warps finished
+    __shared__ volatile unsigned s_epi_tiles;                  // tiles finished by epilogue warp 0
     const unsigned len = a.len;
     constexpr unsigned ck = KS * 16;
     const unsigned nch = len / ck;
@@ -553,6 +595,11 @@ k_tc_screen(ScreenArgs a)
             s_fills[i] = 0u;
         }
         mbar_init(&bar_drain, 1);
+        for (unsigned i = 0; i < kTcCq; ++i) s_cq_seq[i] = 0u;
+        s_cq_tail = 0u;
+        s_cq_head = 0u;
+        s_epi_done = 0u;
+        s_epi_tiles = 0u;
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bar_accf[i], 1);
             mbar_init(&bar_acce[i], kTcEpiWarps);
@@ -678,6 +725,69 @@ k_tc_screen(ScreenArgs a)
                 }
             }
         }
+    } else if (warp == kTcCandWarp) {
+        // ------------------------------------------------ candidates
+        // Takes the queued pairs in order, up to 32 at a time (one per lane),
+        // until every epilogue warp has finished and the queue is empty.  The
+        // idle wait is bounded and counts only while the epilogue makes no
+        // progress.
+        const CandidateSink sink{a.qconst, a.cand_count, a.cand_pos, a.Ubits, sE, sU, sLock, topk, a.qmap, a.srange,
+                                 a.N, a.cap, a.B, a.k};
+        unsigned head = 0, idle = 0, seen = 0;
+        bool ok = true;
+        for (;;) {
+            const unsigned tail = ld_volatile_u32(&s_cq_tail);
+            if (head == tail) {
+                if (ld_volatile_u32(&s_epi_done) == kTcEpiWarps) {
+                    __threadfence_block();
+                    if (ld_volatile_u32(&s_cq_tail) == head) break;
+                    continue;
+                }
+                const unsigned prog = s_epi_tiles + ld_volatile_u32(&s_epi_done);
+                if (prog != seen) {
+                    seen = prog;
+                    idle = 0;
+                } else if (++idle >= kSpinLimit) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+                continue;
+            }
+            const unsigned n = min(32u, tail - head);
+            uint4 e = make_uint4(0u, 0u, 0u, 0u);
+            bool got = true;
+            if ((unsigned)lane < n) {
+                const unsigned t = head + lane;
+                for (unsigned it = 0; ld_volatile_u32(&s_cq_seq[t % kTcCq]) != t + 1u; ++it) {
+                    if (it >= kSpinLimit) {
+                        got = false;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                __threadfence_block();
+                if (got) e = s_cq[t % kTcCq];
+            }
+            if (!__all_sync(0xffffffffu, got)) {
+                ok = false;
+                break;
+            }
+            head += n;
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                s_cq_head = head;   // the slots read above may be written again
+            }
+            if ((unsigned)lane < n) {
+                const unsigned long long row = e.x;
+                const bool rv = row < a.N;
+                screen_candidate(sink, e.y, qt0 * kTcQ + e.y, row, __uint_as_float(e.z), rv ? a.xn[row] : 0.f,
+                                 rv ? a.xnorm[row] : 0.f);
+            }
+            __syncwarp();
+        }
+        if (!ok) s_fail = 1;
     } else {
         // ------------------------------------------------ epilogue
         const unsigned lg = (unsigned)(warp & 3);             // TMEM lane group of this warp
@@ -709,8 +819,6 @@ k_tc_screen(ScreenArgs a)
         epi_bar_sync();
         const float amax = __uint_as_float(s_amax);
         const float one_m_kappa = 1.f - kKappaP;
-        const CandidateSink sink{a.qconst, a.cand_count, a.cand_pos, a.Ubits, sE, sU, sLock, topk, a.qmap, a.srange,
-                                 a.N, a.cap, a.B, a.k};
         // series norms of the next tile are fetched one tile ahead
         float nxt_xn = 0.f, nxt_nrm = 0.f;
         auto fetch_norms = [&](unsigned long long j) {
@@ -728,7 +836,7 @@ k_tc_screen(ScreenArgs a)
             const float r = row < a.N ? __fmaf_ru(xnrm, amax, __fmul_ru(-xn, one_m_kappa)) : __int_as_float(0xff800000);
             fetch_norms(j + 1);
             const bool okw = mbar_wait_bounded(&bar_accf[ab], (unsigned)((j >> 1) & 1));
-            if (epi_bar_any(!okw)) {
+            if (epi_bar_any(!okw || s_fail)) {
                 s_fail = 1;
                 break;
             }
@@ -756,16 +864,16 @@ k_tc_screen(ScreenArgs a)
                     const bool hit = min3f(mn[0], mn[1], fminf(mn[2], mn[3])) <= r;
                     if (__any_sync(0xffffffffu, hit)) {
                         // the groups some lane flagged, each pair re-tested in the
-                        // kernel's rearranged form; unrolled so the accumulators
-                        // stay in registers
+                        // kernel's rearranged form and queued for the candidate
+                        // warp; unrolled so the accumulators stay in registers
 #pragma unroll
                         for (int gq = 0; gq < 4; ++gq) {
                             if (!__any_sync(0xffffffffu, mn[gq] <= r)) continue;
 #pragma unroll
                             for (int i = 16 * gq; i < 16 * gq + 16; ++i) {
                                 const unsigned ql = cbeg + h + i;
-                                if (__fmaf_ru(2.f, acc[i], r) >= sE[ql])
-                                    screen_candidate(sink, ql, qt0 * kTcQ + ql, row, acc[i], xn, xnrm);
+                                cq_push(__fmaf_ru(2.f, acc[i], r) >= sE[ql], (unsigned)row, ql, acc[i], s_cq, s_cq_seq,
+                                        &s_cq_tail, &s_cq_head, &s_fail);
                             }
                         }
                     }
@@ -774,6 +882,7 @@ k_tc_screen(ScreenArgs a)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_acce[ab]);
+            if (warp == 0 && lane == 0) s_epi_tiles = (unsigned)(j + 1);   // progress, for the candidate warp
             // pick up bounds lowered by the other CTAs of these query tiles
             // (and repair an E_q that a race left looser than its U_q)
             if (own_act && (j & 63) == 63) {
@@ -781,6 +890,12 @@ k_tc_screen(ScreenArgs a)
                 const unsigned old = atomicMin(&sU[tid], G);
                 sE[tid] = __fsub_rd(__fsub_rd(own_qn, own_gamma), __uint_as_float(min(old, G)));
             }
+        }
+        // this warp's entries are all published: tell the candidate warp
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            atomicAdd(&s_epi_done, 1u);
         }
     }
     tc_fence_before();

@@ -39,8 +39,8 @@ namespace messi {
 namespace {
 
 constexpr int kPrepThreads = 256;
-constexpr int kScanThreads = 512;
-constexpr int kScanWpt = 2;
+constexpr int kScanThreads = 256;
+constexpr int kScanWpt = 4;
 constexpr int kScanTileWords = kScanThreads * kScanWpt;   // 1024 words, 16 KB
 static_assert(kScanTileWords == kScanTileWordsHost, "scan tile size shared with the workspace layout");
 constexpr int kScanStages = 4;

@@ -220,7 +220,8 @@ struct TcWs {
     __half *qtiles, *qtiles2;       // the batch's query tiles; those screened again, gathered
     float *qconst;
     unsigned *Ubits, *cand_count, *flags, *active, *cand_pos, *n_active, *qmap;
-    float *tkinit;                  // per query: the seed leaf's k best upper ends
+    float *tkinit;                  // per query: its k smallest upper ends (from the seed leaf's k best)
+    unsigned *glock;                // per query: the lock of that list
     uint2 *srange;                  // per query: the seed leaf's positions
 };
 
@@ -239,6 +240,7 @@ TcWs tc_ws_view(messi_index *ix, Workspace *ws)
     w.qtiles2 = reinterpret_cast<__half *>(p); p += align256((size_t)P * ix->len * 2);
     w.qmap = reinterpret_cast<unsigned *>(p); p += align256((size_t)P * 4);
     w.tkinit = reinterpret_cast<float *>(p); p += align256((size_t)P * kTcTopKHost * 4);
+    w.glock = reinterpret_cast<unsigned *>(p); p += align256((size_t)P * 4);
     w.srange = reinterpret_cast<uint2 *>(p); p += align256((size_t)P * 8);
     w.cand_pos = reinterpret_cast<unsigned *>(p);
     return w;
@@ -253,7 +255,7 @@ messi_status ensure_tc_workspace(messi_index *ix, Workspace *ws, unsigned B)
         ws->tcws_block = nullptr;
     }
     const size_t P = (B + 127) / 128 * 128;
-    const size_t bytes = 2 * align256(P * ix->len * 2) + align256(P * 16) + 5 * align256(P * 4) + 256 +
+    const size_t bytes = 2 * align256(P * ix->len * 2) + align256(P * 16) + 6 * align256(P * 4) + 256 +
                          align256(P * kTcTopKHost * 4) + align256(P * 8) + P * kTcCap * 4;
     if (cudaMalloc(&ws->tcws_block, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -940,7 +942,7 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
         const TcWs w = tc_ws_view(ix, ws);
         launch_batch_seed(iv, qp, ws->bslots_dev, nb, dq + (size_t)g * ix->len, s, &ws->launches);
         launch_tc_qprep(ws->bslots_dev, nb, ix->len, qp, w.qtiles, w.qconst, w.Ubits, w.cand_count, w.flags,
-                        w.active, w.tkinit, w.srange, s);
+                        w.active, w.tkinit, w.glock, w.srange, s);
         ++ws->launches;
         // pass 0 screens the batch; later passes only the queries whose
         // candidate lists overflowed, gathered into the first query tiles
@@ -954,7 +956,8 @@ messi_status run_batched(messi_index *ix, Workspace *ws, const float *queries, u
                 cudaEventRecord(pool_event(ws, evn++), s);
             }
             launch_tc_screen(ix->screen16, ix->xn, ix->xnorm, qt, w.qconst, w.Ubits, w.cand_count, w.cand_pos,
-                             w.active, qm, w.tkinit, w.srange, kTcCap, ix->N, ix->len, count, (int)k, ix->status, s);
+                             w.active, qm, w.tkinit, w.glock, pass == 0 ? 1 : 0, w.srange, kTcCap, ix->N, ix->len,
+                             count, (int)k, ix->status, s);
             screened += count;
             if (ix->profiling) {
                 cudaEventRecord(pool_event(ws, evn++), s);

@@ -314,15 +314,15 @@ void launch_make_screen_copy(const float *raw, unsigned long long N, int len, __
 constexpr unsigned kTcTopKHost = 16;   // longest per-query top-k list of the screen
 void launch_tc_qprep(const QuerySlot *slots, unsigned B, int len, const QueryParams &qp, __half *qtiles,
                      float *qconst, unsigned *Ubits, unsigned *cand_count, unsigned *flags, unsigned *active,
-                     float *tkinit, uint2 *srange, cudaStream_t s);
+                     float *tkinit, unsigned *glock, uint2 *srange, cudaStream_t s);
 void launch_tc_next_pass(const QuerySlot *slots, unsigned B, const QueryParams &qp, unsigned cap, unsigned *Ubits,
                          unsigned *cand_count, unsigned *active, unsigned *n_active, const __half *qtiles,
                          __half *qtiles2, unsigned *qmap, int len, cudaStream_t s);
 void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm, const __half *qtiles,
                       const float *qconst, unsigned *Ubits, unsigned *cand_count, unsigned *cand_pos,
-                      const unsigned *active, const unsigned *qmap, const float *tkinit, const uint2 *srange,
-                      unsigned cap, unsigned long long N, int len, unsigned B, int k, unsigned *status,
-                      cudaStream_t s);
+                      const unsigned *active, const unsigned *qmap, float *topk, unsigned *glock, int lists,
+                      const uint2 *srange, unsigned cap, unsigned long long N, int len, unsigned B, int k,
+                      unsigned *status, cudaStream_t s);
 void launch_tc_recheck(const IndexView &iv, const QueryParams &qp, const QuerySlot *slots, unsigned B,
                        const unsigned *cand_count, const unsigned *cand_pos, unsigned cap, const unsigned *active,
                        cudaStream_t s);

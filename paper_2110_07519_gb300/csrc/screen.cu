@@ -41,10 +41,9 @@ constexpr float kKappaP = 7.2e-7f;  // 12u: kappa plus the rounding of the rearr
 static_assert(kKappaP >= 3.f * kKappa, "the rearranged test's slack covers kappa and 8u more");
 constexpr int kTcMaxStages = 16;
 // dynamic shared memory of one screen CTA: the 227 KB a block may hold, less
-// the kernel's 5.4 KB of static shared memory (barriers, per-query bounds,
+// the kernel's 5 KB of static shared memory (barriers, per-query bounds,
 // the candidate queue) and some margin, so that at 256 points two resident
-// query tiles (128 KB), top-k lists up to k = 12 and five 16 KB ring stages
-// fit together
+// query tiles (128 KB) and five 16 KB ring stages fit together
 constexpr size_t kTcSmemBudget = 221 * 1024;
 
 // K width of one streamed chunk of a series tile: the largest of 64, 32, 16
@@ -177,7 +176,7 @@ __global__ void __launch_bounds__(256)
 k_tc_qprep(const QuerySlot *__restrict__ slots, unsigned B, int len, QueryParams qp, __half *__restrict__ qtiles,
            float *__restrict__ qconst, unsigned *__restrict__ Ubits, unsigned *__restrict__ cand_count,
            unsigned *__restrict__ flags, unsigned *__restrict__ active, float *__restrict__ tkinit,
-           uint2 *__restrict__ srange)
+           unsigned *__restrict__ glock, uint2 *__restrict__ srange)
 {
     __shared__ double part[8];
     const unsigned b = blockIdx.x;        // padded up to a multiple of kTcQ
@@ -245,6 +244,7 @@ k_tc_qprep(const QuerySlot *__restrict__ slots, unsigned B, int len, QueryParams
             for (int j = 0; j < (int)kTcTopKHost; ++j) tkinit[b * (int)kTcTopKHost + j] = __int_as_float(0x7f800000);
         }
         srange[b] = sr;
+        glock[b] = 0u;
     }
 }
 
@@ -289,7 +289,10 @@ struct ScreenArgs {
     unsigned *cand_pos;       // [QT*128][cap]
     const unsigned *active;   // [QT*128]: nonzero when the query collects candidates this pass
     const unsigned *qmap;     // [B]: batch index of each screened query (nullptr: the identity)
-    const float *tkinit;      // [batch][kTcTopK]: upper ends of the seed leaf's k best (1 < k <= kTcTopK)
+    float *topk;              // [batch][kTcTopK]: the query's k smallest upper ends met so far (1 < k <= kTcTopK),
+                              // starting from the seed leaf's k best; updated under glock
+    unsigned *glock;          // [batch]: lock of each query's list
+    int lists;                // 1: this pass adds to the lists (the first; later passes meet the rows again)
     const uint2 *srange;      // [batch]: the seed leaf's positions [x, y)
     unsigned B;               // queries screened (rows of qtiles in use)
     unsigned cap;
@@ -403,37 +406,39 @@ __device__ __forceinline__ bool epi_bar_any(bool v)
     return r != 0;
 }
 
-// k <= kTcTopK: each query of a CTA keeps the k smallest upper ends met in
-// that CTA (ascending; each from a different row, since a CTA meets every
-// (query, row) pair at most once), and the k-th of them bounds the query's
-// k-th squared distance from above just as the single best does for k = 1.
-// The list lives in shared memory and is updated under a per-query lock
-// taken with a bounded spin; a lane that does not get the lock skips its
-// update, which only leaves the bound looser.
+// k <= kTcTopK: each query keeps, in global memory, the k smallest upper
+// ends met by any CTA (ascending; each from a different row, since the
+// screen meets every (query, row) pair once and the list starts from the
+// seed leaf's k best, whose rows it skips), and the k-th of them bounds the
+// query's k-th squared distance from above just as the single best does for
+// k = 1.  The candidate warps update it under a per-query lock taken with a
+// bounded spin; a lane that does not get the lock skips its update, which
+// only leaves the bound looser.  One list for all CTAs, not one per CTA: a
+// CTA meets 1/G of the rows, so its own k-th would sit far above the
+// query's.
 constexpr int kTcTopK = 16;
 static_assert(kTcTopK == (int)kTcTopKHost, "top-k list length shared with the workspace layout");
-static_assert((kTcSmemBudget - (size_t)2 * kTcQ * kTcResidentLen * 2 - (size_t)2 * kTcQ * kTcTopK * 4) /
-                      (kTcRows * 64 * 2) >= 4,
-              "two query tiles of the longest resident length, their top-k lists and 4 ring stages fit");
-static_assert((kTcSmemBudget - (size_t)2 * kTcQ * kTcTopK * 4) / (3 * kTcRows * 64 * 2) >= 4,
-              "streamed queries: 4 stages of a series chunk and two query chunks fit next to two top-k lists");
+static_assert((kTcSmemBudget - (size_t)2 * kTcQ * kTcResidentLen * 2) / (kTcRows * 64 * 2) >= 4,
+              "two query tiles of the longest resident length and 4 ring stages fit");
+static_assert(kTcSmemBudget / (3 * kTcRows * 64 * 2) >= 4,
+              "streamed queries: 4 stages of a series chunk and two query chunks fit");
 
-__device__ __forceinline__ bool topk_lock(int *l)
+__device__ __forceinline__ bool list_lock(unsigned *l)
 {
     for (int it = 0; it < 4096; ++it) {
-        if (atomicCAS(l, 0, 1) == 0) {
-            __threadfence_block();
+        if (atomicCAS(l, 0u, 1u) == 0u) {
+            __threadfence();
             return true;
         }
-        __nanosleep(32);
+        __nanosleep(64);
     }
     return false;
 }
 
-__device__ __forceinline__ void topk_unlock(int *l)
+__device__ __forceinline__ void list_unlock(unsigned *l)
 {
-    __threadfence_block();
-    atomicExch(l, 0);
+    __threadfence();
+    atomicExch(l, 0u);
 }
 
 // A queued pair (query, series row) passed the epilogue's test with the CTA's
@@ -445,13 +450,13 @@ struct CandidateSink {
     unsigned *cand_count, *cand_pos, *Ubits;
     float *sE;           // shared: E_q per query of the CTA
     unsigned *sU;        // shared: U_q bits
-    int *lock;           // shared: top-k list locks
-    float *topk;         // shared: [QPC * 128][k] top-k lists (1 < k <= kTcTopK)
+    float *topk;         // global: [batch][kTcTopK] lists (1 < k <= kTcTopK)
+    unsigned *glock;     // global: [batch] list locks
     const unsigned *qmap;
     const uint2 *srange; // the seed leaf's positions, whose rows the lists already hold
     unsigned long long N;
     unsigned cap, B;
-    int k;
+    int k, lists;
 };
 
 __device__ __forceinline__ void screen_candidate(const CandidateSink &a, unsigned ql, unsigned qc, unsigned long long row,
@@ -478,9 +483,10 @@ __device__ __forceinline__ void screen_candidate(const CandidateSink &a, unsigne
     const float up = fmaxf(__fmul_ru(__fadd_ru(shat, eps), 1.0000003f), 0.f);
     float bound = up;
     if (a.k > 1) {
-        volatile float *t = a.topk + (size_t)ql * a.k;
-        if (!(up < t[a.k - 1])) return;
-        if (!topk_lock(&a.lock[ql])) return;
+        if (!a.lists) return;   // a later pass: the pair may already be in the list
+        volatile float *t = a.topk + (size_t)qj * kTcTopK;
+        if (!(up < t[a.k - 1])) return;   // (read without the lock: a shortcut only)
+        if (!list_lock(&a.glock[qj])) return;
         int j = a.k - 1;
         if (up < t[j]) {
             while (j > 0 && t[j - 1] > up) {
@@ -490,7 +496,7 @@ __device__ __forceinline__ void screen_candidate(const CandidateSink &a, unsigne
             t[j] = up;
         }
         bound = t[a.k - 1];
-        topk_unlock(&a.lock[ql]);
+        list_unlock(&a.glock[qj]);
     }
     // bounds are >= 0 (or +inf): their bits order like the values
     const unsigned bb = __float_as_uint(bound);
@@ -551,7 +557,6 @@ k_tc_screen(ScreenArgs a)
     __shared__ unsigned tmem_base;
     __shared__ __align__(16) float sE[2 * kTcQ];     // E_q per query of the CTA (+inf: not tested)
     __shared__ unsigned sU[2 * kTcQ];                // U_q bits
-    __shared__ int sLock[2 * kTcQ];                  // top-k list locks
     __shared__ unsigned s_amax;                      // bits of the CTA's largest alpha
     __shared__ volatile int s_fail;
     __shared__ unsigned s_fills[kTcMaxStages];                 // bulk-copy fills issued per ring stage
@@ -575,7 +580,6 @@ k_tc_screen(ScreenArgs a)
     const unsigned stage_bytes = chunk_bytes * (qstream ? 1 + QPC : 1);
     unsigned char *qbuf = smem;
     unsigned char *ring = smem + (qstream ? 0 : QPC * qtile_bytes);
-    float *topk = reinterpret_cast<float *>(ring + NS * stage_bytes);   // [QPC * 128][k] when 1 < k <= kTcTopK
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned QG = (a.QT + QPC - 1) / QPC;               // query-tile groups
     const unsigned groups = gridDim.x / QG;                   // CTAs per query-tile group
@@ -731,8 +735,8 @@ k_tc_screen(ScreenArgs a)
         // until every epilogue warp has finished and the queue is empty.  The
         // idle wait is bounded and counts only while the epilogue makes no
         // progress.
-        const CandidateSink sink{a.qconst, a.cand_count, a.cand_pos, a.Ubits, sE, sU, sLock, topk, a.qmap, a.srange,
-                                 a.N, a.cap, a.B, a.k};
+        const CandidateSink sink{a.qconst, a.cand_count, a.cand_pos, a.Ubits, sE, sU, a.topk, a.glock, a.qmap,
+                                 a.srange, a.N, a.cap, a.B, a.k, a.lists};
         unsigned head = 0, idle = 0, seen = 0;
         bool ok = true;
         for (;;) {
@@ -795,7 +799,6 @@ k_tc_screen(ScreenArgs a)
         const unsigned ncol = acc_cols / 2;                   // queries (columns) of this warp: 128 or 64
         const unsigned cbeg = (unsigned)(warp >> 2) * ncol;
         const bool cols_live = cbeg < nq * kTcQ;              // one query tile in a QPC = 2 CTA: half idle
-        const bool use_topk = a.k > 1 && a.k <= kTcTopK;
         // thread t sets up (and later refreshes) the bounds of query t of the CTA
         const unsigned own_qc = qt0 * kTcQ + tid;
         const bool own_have = (unsigned)tid < nq * kTcQ && own_qc < a.B;
@@ -807,15 +810,9 @@ k_tc_screen(ScreenArgs a)
             const float U = own_have ? __uint_as_float(a.Ubits[own_qj]) : -1.f;
             sU[tid] = __float_as_uint(U);
             sE[tid] = own_act ? __fsub_rd(__fsub_rd(own_qn, own_gamma), U) : __int_as_float(0x7f800000);
-            sLock[tid] = 0;
             // alpha >= 0: its bits order like the values
             if (own_act) atomicMax(&s_amax, __float_as_uint(a.qconst[4 * own_qj + 1]));
         }
-        // each query's list starts from the upper ends of its seed leaf's k
-        // best rows (distinct rows; the screen does not enter them again)
-        if (use_topk && (unsigned)tid < acc_cols)
-            for (int j = 0; j < a.k; ++j)
-                topk[(unsigned)tid * a.k + j] = own_act ? a.tkinit[own_qj * kTcTopK + j] : __int_as_float(0x7f800000);
         epi_bar_sync();
         const float amax = __uint_as_float(s_amax);
         const float one_m_kappa = 1.f - kKappaP;
@@ -1023,20 +1020,14 @@ size_t screen_smem_bytes(int len)
     return kTcSmemBudget;
 }
 
-// bytes of the per-query top-k lists of a CTA with `qpc` query tiles
-static size_t screen_topk_bytes(unsigned qpc, int k)
-{
-    return (k > 1 && k <= kTcTopK) ? (size_t)qpc * kTcQ * k * sizeof(float) : 0;
-}
-
 // ring stages that fit next to `qpc` resident query tiles (or, streamed, with
-// their chunks inside each stage) and the top-k lists
-unsigned screen_stages(int len, unsigned qpc, int k)
+// their chunks inside each stage)
+unsigned screen_stages(int len, unsigned qpc)
 {
     const bool qstream = query_chunk((unsigned)len) != 0;
     const size_t chunk = (size_t)kTcRows * chunk_k((unsigned)len) * 2;
     const size_t stage = chunk * (qstream ? 1 + qpc : 1);
-    const size_t q = (qstream ? 0 : (size_t)qpc * kTcQ * len * 2) + screen_topk_bytes(qpc, k);
+    const size_t q = qstream ? 0 : (size_t)qpc * kTcQ * len * 2;
     const size_t left = kTcSmemBudget > q ? kTcSmemBudget - q : 0;
     return (unsigned)std::min<size_t>(kTcMaxStages, left / stage);
 }
@@ -1059,11 +1050,11 @@ void launch_make_screen_copy(const float *raw, unsigned long long N, int len, __
 
 void launch_tc_qprep(const QuerySlot *slots, unsigned B, int len, const QueryParams &qp, __half *qtiles,
                      float *qconst, unsigned *Ubits, unsigned *cand_count, unsigned *flags, unsigned *active,
-                     float *tkinit, uint2 *srange, cudaStream_t s)
+                     float *tkinit, unsigned *glock, uint2 *srange, cudaStream_t s)
 {
     const unsigned padded = (B + kTcQ - 1) / kTcQ * kTcQ;
     k_tc_qprep<<<padded, 256, 0, s>>>(slots, B, len, qp, qtiles, qconst, Ubits, cand_count, flags, active, tkinit,
-                                      srange);
+                                      glock, srange);
 }
 
 void launch_tc_next_pass(const QuerySlot *slots, unsigned B, const QueryParams &qp, unsigned cap, unsigned *Ubits,
@@ -1076,11 +1067,14 @@ void launch_tc_next_pass(const QuerySlot *slots, unsigned B, const QueryParams &
 
 void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm, const __half *qtiles,
                       const float *qconst, unsigned *Ubits, unsigned *cand_count, unsigned *cand_pos,
-                      const unsigned *active, const unsigned *qmap, const float *tkinit, const uint2 *srange,
-                      unsigned cap, unsigned long long N, int len, unsigned B, int k, unsigned *status, cudaStream_t s)
+                      const unsigned *active, const unsigned *qmap, float *topk, unsigned *glock, int lists,
+                      const uint2 *srange, unsigned cap, unsigned long long N, int len, unsigned B, int k,
+                      unsigned *status, cudaStream_t s)
 {
     ScreenArgs a;
-    a.tkinit = tkinit;
+    a.topk = topk;
+    a.glock = glock;
+    a.lists = lists;
     a.srange = srange;
     a.rtiles = rtiles;
     a.xn = xn;
@@ -1101,10 +1095,9 @@ void launch_tc_screen(const __half *rtiles, const float *xn, const float *xnorm,
     a.status = status;
     // two query tiles per CTA when they leave room for 4 ring stages: always
     // for len <= 256 (resident, 128 KB of tiles) and for every streamed length
-    // (4 stages of 48 KB next to 16 KB of top-k lists); one when the batch
-    // has a single query tile
-    a.qpc = (a.QT >= 2 && screen_stages(len, 2, k) >= 4) ? 2u : 1u;
-    a.stages = screen_stages(len, a.qpc, k);
+    // (4 stages of 48 KB); one when the batch has a single query tile
+    a.qpc = (a.QT >= 2 && screen_stages(len, 2) >= 4) ? 2u : 1u;
+    a.stages = screen_stages(len, a.qpc);
     const unsigned QG = (a.QT + a.qpc - 1) / a.qpc;
     const unsigned groups = std::max(1u, (unsigned)num_sms() / QG);
     const unsigned ks = chunk_k((unsigned)len) / 16;

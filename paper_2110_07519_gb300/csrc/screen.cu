@@ -41,10 +41,10 @@ constexpr float kKappaP = 7.2e-7f;  // 12u: kappa plus the rounding of the rearr
 static_assert(kKappaP >= 3.f * kKappa, "the rearranged test's slack covers kappa and 8u more");
 constexpr int kTcMaxStages = 16;
 // dynamic shared memory of one screen CTA: the 227 KB a block may hold, less
-// the kernel's 5 KB of static shared memory (barriers, per-query bounds,
+// the kernel's 8 KB of static shared memory (barriers, per-query bounds,
 // the candidate queue) and some margin, so that at 256 points two resident
 // query tiles (128 KB) and five 16 KB ring stages fit together
-constexpr size_t kTcSmemBudget = 221 * 1024;
+constexpr size_t kTcSmemBudget = 217 * 1024;
 
 // K width of one streamed chunk of a series tile: the largest of 64, 32, 16
 // dividing len.  A tile is stored chunk-major: chunk c (k in [c*ck, c*ck+ck))
@@ -95,8 +95,9 @@ __device__ __forceinline__ float tc_coef(int len)
 // two-sum on hi; lanes then combine their pairs across the warp the same way.
 // For all-positive terms the pair differs from the exact sum by at most
 // about (n u)^2 of it (n terms per lane or per warp step, u = 2^-24), far
-// below the FP32 rounding of the final norm; the one FP64 addition hi + lo
-// per row keeps that accuracy until the norm is rounded.
+// below the FP32 rounding of the final norm; hi + lo is rounded once, to
+// nearest for |x|^2 and upward (then widened) for |x|.  No FP64: this GPU's
+// FP64 rate made the square root the copy's bottleneck.
 struct F2 {
     float hi, lo;
 };
@@ -162,9 +163,11 @@ k_make_screen_copy(const float *__restrict__ raw, unsigned long long N, int len,
             ss = f2_add2(ss, o);
         }
         if (lane == 0) {
-            const double sd = (double)ss.hi + (double)ss.lo;
-            xn[row] = (float)sd;
-            xnorm[row] = __double2float_ru(sqrt(sd * (1.0 + 1e-9)));
+            // |x|^2 to nearest (one correctly rounded addition of the pair);
+            // |x| rounded up from the pair's sum rounded up and widened by
+            // 2^-20 (far above the pair's 1e-9 relative error), all in FP32
+            xn[row] = __fadd_rn(ss.hi, ss.lo);
+            xnorm[row] = __fsqrt_ru(__fmul_ru(__fadd_ru(ss.hi, ss.lo), 1.00000095367431640625f));
         }
     }
 }
@@ -357,7 +360,7 @@ constexpr int kTcProdWarp0 = kTcEpiWarps, kTcMmaWarp = kTcEpiWarps + 1, kTcProdW
 // their test and the candidate warp records them (global slot, top-k list,
 // bounds), so the epilogue never waits on that work.  Entry t lives in slot
 // t mod kTcCq and is ready once its sequence word holds t + 1.
-constexpr unsigned kTcCq = 64;
+constexpr unsigned kTcCq = 256;
 
 // Named barrier 3: the MMA warp and the relay warp, once per chunk.
 __device__ __forceinline__ void relay_bar_sync() { asm volatile("bar.sync 3, 64;" ::: "memory"); }

@@ -6,14 +6,17 @@ each product is split exactly into p + e (p = x*x rounded, e = fma(x, x, -p)),
 p enters hi through an exact two-sum whose error goes to lo, e is added to
 lo; lane l takes the values k0 .. k0+7 for k0 = 8 l, 8 l + 256, ...; the 32
 lanes then combine their pairs by an xor butterfly (offsets 16, 8, 4, 2, 1)
-and lane 0 forms hi + lo in FP64.  Restated here in float32 (numpy float32
-operations round to nearest like the kernel's; the exact product error of
-a float32 square is exact in float64 and fits a float32), the result must
-lie within 1e-9 of the exact squared norm -- the slack the screen's error
-bound keeps for the norms beyond their final FP32 rounding -- and the upper
-norm sqrt(sd (1 + 1e-9)) must not fall below the exact norm, for every
-length the screen takes, on random walks, constant rows, rows of one large
-and many tiny values, and rows near the f16 range limit."""
+and lane 0 rounds hi + lo once: to nearest for |x|^2, and upward, widened
+by 2^-20 and square-rooted upward for |x|, all in FP32.  Restated here in
+float32 (numpy float32 operations round to nearest like the kernel's; the
+exact product error of a float32 square is exact in float64 and fits a
+float32; the directed roundings by exact rational comparison), the pair
+must lie within 1e-9 of the exact squared norm -- the slack the screen's
+error bound keeps for the norms beyond their final FP32 rounding -- the
+nearest-rounded |x|^2 must equal the exact pair rounded once, and the upper
+norm must not fall below the exact norm, for every length the screen takes,
+on random walks, constant rows, rows of one large and many tiny values, and
+rows near the f16 range limit."""
 from fractions import Fraction
 
 import numpy as np
@@ -52,7 +55,27 @@ def kernel_norm(x):
             new.append((hi, F32(lo + b[1])))
         lanes = new
     hi, lo = lanes[0]
-    return float(hi) + float(lo)
+    return hi, lo
+
+
+def f32_round(fr: Fraction, up: bool) -> float:
+    # a rational rounded to float32, toward +inf (up) or -inf
+    r = np.float32(float(fr))
+    while (Fraction(float(r)) < fr) if up else (Fraction(float(r)) > fr):
+        r = np.nextafter(r, np.float32(np.inf if up else -np.inf))
+    return float(r)
+
+
+def upper_norm(hi, lo):
+    # __fsqrt_ru(__fmul_ru(__fadd_ru(hi, lo), 1 + 2^-20))
+    s = f32_round(Fraction(float(hi)) + Fraction(float(lo)), True)
+    s = f32_round(Fraction(s) * Fraction(1 + 2 ** -20), True)
+    r = np.float32(np.sqrt(s))
+    while Fraction(float(r)) ** 2 < Fraction(s):
+        r = np.nextafter(r, np.float32(np.inf))
+    while Fraction(float(np.nextafter(r, np.float32(-np.inf)))) ** 2 >= Fraction(s):
+        r = np.nextafter(r, np.float32(-np.inf))
+    return float(r)
 
 
 def rows(rng, n):
@@ -75,7 +98,10 @@ def test_compensated_norm_within_slack(n):
     for name, x in rows(rng, n).items():
         x = x.astype(F32)
         exact = sum(Fraction(float(v)) ** 2 for v in x)
-        sd = kernel_norm(x)
-        assert abs(Fraction(sd) - exact) <= Fraction(1, 10 ** 9) * exact, (n, name)
-        up = np.sqrt(sd * (1.0 + 1e-9))
+        hi, lo = kernel_norm(x)
+        sd = Fraction(float(hi)) + Fraction(float(lo))
+        assert abs(sd - exact) <= Fraction(1, 10 ** 9) * exact, (n, name)
+        # |x|^2 to nearest: one float32 addition of the pair, correctly rounded
+        assert float(np.float32(hi) + np.float32(lo)) == float(np.float32(float(sd)))
+        up = upper_norm(hi, lo)
         assert Fraction(up) ** 2 >= exact, (n, name)

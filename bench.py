@@ -143,13 +143,20 @@ def measured_peak_hbm():
 
 
 def scan_source_sha(kernel: str = "k_lb_scan"):
-    """Hash of the source a traffic figure was measured on: the screen's files
-    whole; for the scan, the part of query.cu from its code table to the end
-    of the scan kernel, and the shared device helpers."""
+    """Hash of the source a traffic figure was measured on: for the screen,
+    the part of screen.cu from its argument block to the end of the screen
+    kernel, and the tensor-core and shared device helpers; for the scan, the
+    part of query.cu from its code table to the end of the scan kernel, and
+    the shared device helpers."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2110_07519_gb300", "csrc")
     if kernel == "k_tc_screen":
-        for name in ("screen.cu", "tc.cuh", "device_common.cuh"):
+        with open(os.path.join(csrc, "screen.cu"), "rb") as f:
+            text = f.read()
+        a = text.find(b"struct ScreenArgs {")
+        b = text.find(b"// ----------------------------------------------------------- recheck")
+        h.update(text[a:b] if 0 <= a < b else text)
+        for name in ("tc.cuh", "device_common.cuh"):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(f.read())
     else:

@@ -115,59 +115,83 @@ __device__ __forceinline__ F2 f2_add2(F2 a, F2 b)
     return t;
 }
 
-// One warp per series: f16 copy in tile layout, squared norm -> xn (FP32,
-// nearest) and |x| rounded up.
+// One CTA per 128-row tile: each K chunk of the tile is converted into its
+// tensor-core layout in shared memory and written out as one contiguous
+// 4-16 KB block, so every global store is a full coalesced line; each warp
+// reads 16 rows, ck / 4 lanes per row with 16-byte loads, and every lane
+// keeps a compensated pair of its rows' squares across the chunks.  The
+// lanes of a row then combine their pairs by an xor butterfly: squared norm
+// -> xn (FP32, nearest) and |x| rounded up.
 __global__ void __launch_bounds__(256)
 k_make_screen_copy(const float *__restrict__ raw, unsigned long long N, int len, __half *__restrict__ tiles,
                    float *__restrict__ xn, float *__restrict__ xnorm, unsigned *__restrict__ bad)
 {
-    const int lane = threadIdx.x & 31;
-    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    const unsigned long long ntile_rows = ((N + kTcRows - 1) / kTcRows) * kTcRows;
-    for (unsigned long long row = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-         row < ntile_rows; row += nw) {
-        const unsigned long long tile = row / kTcRows;
-        const unsigned r = (unsigned)(row % kTcRows);
-        unsigned char *tbase = reinterpret_cast<unsigned char *>(tiles) + tile * (unsigned long long)kTcRows * len * 2;
-        F2 ss = {0.f, 0.f};
-        for (int k0 = lane * 8; k0 < len; k0 += 256) {
-            float v[8];
-            if (row < N) {
-                const float4 *src = reinterpret_cast<const float4 *>(raw + row * (unsigned long long)len + k0);
-                const float4 a = __ldg(src), b = __ldg(src + 1);
-                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-            } else {
+    __shared__ __align__(16) unsigned char cbuf[kTcRows * 64 * 2];   // one chunk of the tile (at most 16 KB)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned ck = chunk_k((unsigned)len);
+    const unsigned nch = (unsigned)len / ck;
+    const unsigned lpr = ck / 4;                 // lanes per row: one float4 each
+    const unsigned rpi = 32 / lpr;               // rows per warp load
+    const unsigned iters = 16 / rpi;             // loads per chunk for the warp's 16 rows (2, 4 or 8)
+    const unsigned sub = (unsigned)lane / lpr, part = (unsigned)lane % lpr;
+    const unsigned cbytes = kTcRows * ck * 2;
+    const unsigned long long RT = (N + kTcRows - 1) / kTcRows;
+    for (unsigned long long tile = blockIdx.x; tile < RT; tile += gridDim.x) {
+        unsigned char *tb = reinterpret_cast<unsigned char *>(tiles) + tile * (unsigned long long)kTcRows * len * 2;
+        F2 ss[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) v[i] = 0.f;
-            }
-            __align__(16) __half2 h[4];
-            bool big = false;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) h[i] = __floats2half2_rn(v[2 * i], v[2 * i + 1]);   // two per instruction
+        for (int i = 0; i < 8; ++i) ss[i] = {0.f, 0.f};
+        bool big = false;
+        for (unsigned c = 0; c < nch; ++c) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                big = big || fabsf(v[i]) > 65000.f;
-                const float pr = __fmul_rn(v[i], v[i]);
-                const float pe = __fmaf_rn(v[i], v[i], -pr);     // v^2 = pr + pe exactly
-                ss = f2_add(ss, pr);
-                ss.lo = __fadd_rn(ss.lo, pe);
-            }
-            if (big) atomicOr(bad, 1u);
-            const unsigned ck = chunk_k(len);
-            *reinterpret_cast<uint4 *>(tbase + (unsigned)(k0 / ck) * (kTcRows * ck * 2) +
-                                       tc_offset(r, (unsigned)(k0 % ck), ck)) = *reinterpret_cast<uint4 *>(h);
-        }
+                if ((unsigned)i < iters) {
+                    const unsigned r = (unsigned)warp * 16 + (unsigned)i * rpi + sub;   // row within the tile
+                    const unsigned long long row = tile * kTcRows + r;
+                    const unsigned k = part * 4;                                     // column within the chunk
+                    float v[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (row < N) {
+                        const float4 a4 = __ldg(reinterpret_cast<const float4 *>(
+                            raw + row * (unsigned long long)len + (unsigned long long)c * ck + k));
+                        v[0] = a4.x; v[1] = a4.y; v[2] = a4.z; v[3] = a4.w;
+                    }
 #pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-            const F2 o = {__shfl_xor_sync(0xffffffffu, ss.hi, off), __shfl_xor_sync(0xffffffffu, ss.lo, off)};
-            ss = f2_add2(ss, o);
+                    for (int e = 0; e < 4; ++e) {
+                        big = big || fabsf(v[e]) > 65000.f;
+                        const float pr = __fmul_rn(v[e], v[e]);
+                        const float pe = __fmaf_rn(v[e], v[e], -pr);     // v^2 = pr + pe exactly
+                        ss[i] = f2_add(ss[i], pr);
+                        ss[i].lo = __fadd_rn(ss[i].lo, pe);
+                    }
+                    __align__(8) __half2 h[2] = {__floats2half2_rn(v[0], v[1]), __floats2half2_rn(v[2], v[3])};
+                    *reinterpret_cast<uint2 *>(cbuf + tc_offset(r, k, ck)) = *reinterpret_cast<const uint2 *>(h);
+                }
+            }
+            __syncthreads();
+            for (unsigned o = threadIdx.x * 16u; o < cbytes; o += blockDim.x * 16u)
+                *reinterpret_cast<uint4 *>(tb + (unsigned long long)c * cbytes + o) =
+                    *reinterpret_cast<const uint4 *>(cbuf + o);
+            __syncthreads();
         }
-        if (lane == 0) {
-            // |x|^2 to nearest (one correctly rounded addition of the pair);
-            // |x| rounded up from the pair's sum rounded up and widened by
-            // 2^-20 (far above the pair's 1e-9 relative error), all in FP32
-            xn[row] = __fadd_rn(ss.hi, ss.lo);
-            xnorm[row] = __fsqrt_ru(__fmul_ru(__fadd_ru(ss.hi, ss.lo), 1.00000095367431640625f));
+        if (big) atomicOr(bad, 1u);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if ((unsigned)i < iters) {
+                F2 t = ss[i];
+                for (unsigned off = lpr / 2; off >= 1; off >>= 1) {
+                    const F2 o = {__shfl_xor_sync(0xffffffffu, t.hi, off), __shfl_xor_sync(0xffffffffu, t.lo, off)};
+                    t = f2_add2(t, o);
+                }
+                if (part == 0) {
+                    const unsigned long long row = tile * kTcRows + (unsigned)warp * 16 + (unsigned)i * rpi + sub;
+                    // |x|^2 to nearest (one correctly rounded addition of the
+                    // pair); |x| rounded up from the pair's sum rounded up and
+                    // widened by 2^-20 (far above the pair's 1e-9 relative
+                    // error), all in FP32
+                    xn[row] = __fadd_rn(t.hi, t.lo);
+                    xnorm[row] = __fsqrt_ru(__fmul_ru(__fadd_ru(t.hi, t.lo), 1.00000095367431640625f));
+                }
+            }
         }
     }
 }
@@ -1045,10 +1069,9 @@ void init_screen_attributes()
 void launch_make_screen_copy(const float *raw, unsigned long long N, int len, __half *tiles, float *xn, float *xnorm,
                              unsigned *bad, cudaStream_t s)
 {
-    const unsigned long long rows = ((N + kTcRows - 1) / kTcRows) * kTcRows;
-    const unsigned long long want = (rows + 7) / 8;
-    const unsigned long long cap = (unsigned long long)num_sms() * 16;
-    k_make_screen_copy<<<(unsigned)std::min(want, cap), 256, 0, s>>>(raw, N, len, tiles, xn, xnorm, bad);
+    const unsigned long long RT = (N + kTcRows - 1) / kTcRows;
+    const unsigned long long cap = (unsigned long long)num_sms() * 4;   // the resident CTAs
+    k_make_screen_copy<<<(unsigned)std::max(1ull, std::min(RT, cap)), 256, 0, s>>>(raw, N, len, tiles, xn, xnorm, bad);
 }
 
 void launch_tc_qprep(const QuerySlot *slots, unsigned B, int len, const QueryParams &qp, __half *qtiles,

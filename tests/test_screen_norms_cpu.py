@@ -4,9 +4,10 @@
 The kernel sums x_i^2 in FP32 arithmetic as an unevaluated pair hi + lo:
 each product is split exactly into p + e (p = x*x rounded, e = fma(x, x, -p)),
 p enters hi through an exact two-sum whose error goes to lo, e is added to
-lo; lane l takes the values k0 .. k0+7 for k0 = 8 l, 8 l + 256, ...; the 32
-lanes then combine their pairs by an xor butterfly (offsets 16, 8, 4, 2, 1)
-and lane 0 rounds hi + lo once: to nearest for |x|^2, and upward, widened
+lo; the row's lanes are ck / 4 for the tile's K chunk ck (64, 32 or 16), and
+lane j takes the four values 4 j .. 4 j + 3 of every chunk in order; the
+lanes then combine their pairs by an xor butterfly (offsets ck / 8 .. 1) and
+the first rounds hi + lo once: to nearest for |x|^2, and upward, widened
 by 2^-20 and square-rooted upward for |x|, all in FP32.  Restated here in
 float32 (numpy float32 operations round to nearest like the kernel's; the
 exact product error of a float32 square is exact in float64 and fits a
@@ -32,28 +33,36 @@ def two_sum_pair(hi, lo, b):
     return s, F32(lo + err)
 
 
+def chunk_k(n):
+    return 64 if n % 64 == 0 else 32 if n % 32 == 0 else 16
+
+
 def kernel_norm(x):
     x = x.astype(F32)
     n = len(x)
+    ck = chunk_k(n)
+    lpr = ck // 4                      # lanes per row, one float4 of each chunk
     lanes = []
-    for lane in range(32):
+    for j in range(lpr):
         hi, lo = F32(0), F32(0)
-        for k0 in range(lane * 8, n, 256):
-            for i in range(8):
-                v = x[k0 + i]
+        for c in range(n // ck):
+            for e in range(4):
+                v = x[c * ck + 4 * j + e]
                 p = F32(v * v)
-                e = F32(float(v) * float(v) - float(p))      # fma(v, v, -p): exact
+                err = F32(float(v) * float(v) - float(p))    # fma(v, v, -p): exact
                 hi, lo = two_sum_pair(hi, lo, p)
-                lo = F32(lo + e)
+                lo = F32(lo + err)
         lanes.append((hi, lo))
-    for off in (16, 8, 4, 2, 1):
+    off = lpr // 2
+    while off >= 1:
         new = []
-        for lane in range(32):
-            a = lanes[lane]
-            b = lanes[lane ^ off]
+        for j in range(lpr):
+            a = lanes[j]
+            b = lanes[j ^ off]
             hi, lo = two_sum_pair(a[0], a[1], b[0])
             new.append((hi, F32(lo + b[1])))
         lanes = new
+        off //= 2
     hi, lo = lanes[0]
     return hi, lo
 
@@ -92,7 +101,7 @@ def rows(rng, n):
     }
 
 
-@pytest.mark.parametrize("n", [16, 64, 128, 256, 512, 1024, 2048])
+@pytest.mark.parametrize("n", [16, 32, 48, 64, 96, 128, 256, 512, 1024, 2048])
 def test_compensated_norm_within_slack(n):
     rng = np.random.default_rng(n)
     for name, x in rows(rng, n).items():

@@ -887,9 +887,7 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
                     const int idx = base + t;
                     const float c = __ldg(x + idx);
                     P[idx] = fminf(fmaxf(c, Ls[idx]), Us[idx]);   // H: C clamped into [L, U]
-                    float d = 0.f;
-                    if (c > Us[idx]) d = __fsub_rd(c, Us[idx]);
-                    else if (c < Ls[idx]) d = __fsub_rd(Ls[idx], c);
+                    const float d = fmaxf(fmaxf(__fsub_rd(c, Us[idx]), __fsub_rd(Ls[idx], c)), 0.f);   // from [L, U]
                     acc = __fadd_rd(acc, __fmul_rd(d, d));
                 }
                 lbv = lbk_tail(acc);
@@ -941,9 +939,7 @@ k_lbk(IndexView iv, QueryParams qp, QuerySlot slot, int wpb)
                             L = fminf(Sm[lo], Pm[hi]);
                         }
                         const float c = qs[idx];
-                        float d = 0.f;
-                        if (c > U) d = __fsub_rd(c, U);
-                        else if (c < L) d = __fsub_rd(L, c);
+                        const float d = fmaxf(fmaxf(__fsub_rd(c, U), __fsub_rd(L, c)), 0.f);   // from [L, U]
                         acc2 = __fadd_rd(acc2, __fmul_rd(d, d));
                     }
                     // LB_Improved so far: the first term plus the query's part
@@ -1364,9 +1360,7 @@ __device__ __forceinline__ float lbk_improved_thread(const float *__restrict__ q
         float h = hw[W - 1];
         if (i < n) {
             const float c = __ldg(x + i), u = Us[i], l = Ls[i];
-            float d = 0.f;
-            if (c > u) d = __fsub_rd(c, u);
-            else if (c < l) d = __fsub_rd(l, c);
+            const float d = fmaxf(fmaxf(__fsub_rd(c, u), __fsub_rd(l, c)), 0.f);   // distance from [l, u]
             acc1 = __fadd_rd(acc1, __fmul_rd(d, d));
             h = fminf(fmaxf(c, l), u);
         }
@@ -1383,9 +1377,7 @@ __device__ __forceinline__ float lbk_improved_thread(const float *__restrict__ q
                 mn = fminf(mn, v);
             }
             const float qv = qs[p];
-            float d = 0.f;
-            if (qv > mx) d = __fsub_rd(qv, mx);
-            else if (qv < mn) d = __fsub_rd(mn, qv);
+            const float d = fmaxf(fmaxf(__fsub_rd(qv, mx), __fsub_rd(mn, qv)), 0.f);   // distance from [mn, mx]
             acc2 = __fadd_rd(acc2, __fmul_rd(d, d));
         }
         if (__fadd_rd(acc1, acc2) > thr) return __fadd_rd(acc1, acc2);
@@ -1459,9 +1451,9 @@ __device__ __forceinline__ float lbk_improved_blocks(const float *__restrict__ q
             float h = hlast;
             if (j < n) {
                 const float c = cv[k % VW], u = uv[k % VW], l = lv[k % VW];
-                float d = 0.f;
-                if (c > u) d = __fsub_rd(c, u);
-                else if (c < l) d = __fsub_rd(l, c);
+                // distance of c from [l, u] (at most one difference is
+                // positive): no branch, so the lanes of a warp stay together
+                const float d = fmaxf(fmaxf(__fsub_rd(c, u), __fsub_rd(l, c)), 0.f);
                 acc1 = __fadd_rd(acc1, __fmul_rd(d, d));
                 h = fminf(fmaxf(c, l), u);
                 hlast = h;
@@ -1486,10 +1478,9 @@ __device__ __forceinline__ float lbk_improved_blocks(const float *__restrict__ q
             }
             const int p = j - R;
             if (p >= 0 && p < n) {
+                // distance of q_p from [mn, mx], without a branch as above
                 const float qv = qs[p];
-                float d = 0.f;
-                if (qv > mx) d = __fsub_rd(qv, mx);
-                else if (qv < mn) d = __fsub_rd(mn, qv);
+                const float d = fmaxf(fmaxf(__fsub_rd(qv, mx), __fsub_rd(mn, qv)), 0.f);
                 acc2 = __fadd_rd(acc2, __fmul_rd(d, d));
             }
         }

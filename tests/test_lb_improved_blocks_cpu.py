@@ -48,11 +48,7 @@ def blocked_model(q, U, L, x, R):
             if j < n:
                 c, u, l = float(cv[k % VW]), float(uv[k % VW]), float(lv[k % VW])
                 assert (c, u, l) == (float(x[j]), float(U[j]), float(L[j]))
-                d = 0.0
-                if c > u:
-                    d = rd32(Fr(c) - Fr(u))
-                elif c < l:
-                    d = rd32(Fr(l) - Fr(c))
+                d = max(rd32(Fr(c) - Fr(u)), rd32(Fr(l) - Fr(c)), 0.0)     # the kernel's branch-free form
                 acc1 = rd32(Fr(acc1) + Fr(rd32(Fr(d) * Fr(d))))
                 h = min(max(c, l), u)
                 hlast = h
@@ -72,11 +68,7 @@ def blocked_model(q, U, L, x, R):
             if 0 <= p < n:
                 env[p] = (mx, mn)
                 qv = float(q[p])
-                d = 0.0
-                if qv > mx:
-                    d = rd32(Fr(qv) - Fr(mx))
-                elif qv < mn:
-                    d = rd32(Fr(mn) - Fr(qv))
+                d = max(rd32(Fr(qv) - Fr(mx)), rd32(Fr(mn) - Fr(qv)), 0.0)
                 acc2 = rd32(Fr(acc2) + Fr(rd32(Fr(d) * Fr(d))))
     return rd32(Fr(acc1) + Fr(acc2)), env
 

@@ -14,8 +14,8 @@ kernel's index arithmetic for the copies, the walk must reproduce the
 oracle's banded DTW (the textbook full-table recurrence, row by row over the
 query) bit for bit: the arithmetic is the same, only the storage and the
 order of the walk differ, so any indexing slip shows as a different value.
-The band minimum of every fourth column must also stay at or below the final
-distance (the kernel abandons on it)."""
+The band minimum of every column must also stay at or below the final
+distance (the kernel abandons on it, every fourth column)."""
 import math
 
 import numpy as np
@@ -64,8 +64,7 @@ def band_walk(q, x, R, r):
                 v = INF
             D[b] = v
             left = v
-        if j % 4 == 3:
-            cmins.append(min(D))
+        cmins.append(min(D))
     return D[R], cmins
 
 

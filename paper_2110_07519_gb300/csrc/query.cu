@@ -329,6 +329,47 @@ __device__ __forceinline__ void seed_select_body(const IndexView &iv, const Quer
     QueryState *st = slot.st;
     if (ld_volatile_u32(&st->invalid)) return;
     const unsigned cnt = st->seed_hi - st->seed_lo;
+    if (qp.k == 1) {
+        // the best seed alone: a block minimum instead of the sort (the
+        // packed keys order by distance, then id, like the sorted list)
+        __shared__ unsigned long long wmin[kFinThreads / 32];
+        unsigned long long mn = kEmpty;
+        for (unsigned i = threadIdx.x; i < cnt; i += blockDim.x) mn = min(mn, slot.seedbuf[i]);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+        if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = mn;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            mn = threadIdx.x < (blockDim.x >> 5) ? wmin[threadIdx.x] : kEmpty;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+            if (threadIdx.x == 0) wmin[0] = mn;
+        }
+        __syncthreads();
+        const unsigned long long T = cnt >= 1 ? wmin[0] : kEmpty;
+        if (threadIdx.x == 0 && cnt >= 1) slot.karr[0] = T;
+        const float band = prune_threshold(T, qp.F);
+        __shared__ unsigned nlog1;
+        if (threadIdx.x == 0) nlog1 = 0;
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const unsigned long long v = slot.seedbuf[i];
+            if (cand_d2(v) <= band) {
+                const unsigned li = atomicAdd(&nlog1, 1u);
+                if (li < slot.log_cap) slot.log[li] = v;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st->kcount = cnt >= 1 ? 1u : 0u;
+            st->thr = T;
+            st->log_count = nlog1;
+            st->seed_count = cnt;
+            st->c.seeded = cnt;
+            st->c.bsf_updates = T != kEmpty ? 1ull : 0ull;
+        }
+        return;
+    }
     unsigned npow = 1;
     while (npow < cnt) npow <<= 1;
     for (unsigned i = threadIdx.x; i < npow; i += blockDim.x) buf[i] = i < cnt ? slot.seedbuf[i] : kEmpty;

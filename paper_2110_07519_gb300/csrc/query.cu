@@ -86,6 +86,12 @@ __device__ __forceinline__ float table_entry(int s, int v, int w, int card, int 
     return __double2float_rd(__dmul_rd(__dmul_rd(d, d), (double)m));
 }
 
+// k <= q in the order of the 128-bit interleaved keys (x most significant)
+__device__ __forceinline__ bool key_le(const uint4 k, const uint4 q)
+{
+    return (k.x != q.x) ? k.x < q.x : (k.y != q.y) ? k.y < q.y : (k.z != q.z) ? k.z < q.z : k.w <= q.w;
+}
+
 // with_table = false leaves the table to k_prep's other blocks (one row each)
 __device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams &qp, const QuerySlot &slot,
                                           const float *__restrict__ query, bool with_table = true)
@@ -139,24 +145,36 @@ __device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams
         }
     }
     __syncthreads();
-    if (tid < w) {   // FP64 segment means, sequential as the reference does
-        double s = 0.0, su = 0.0, sl = 0.0;
-        for (int t = tid * m; t < (tid + 1) * m; ++t) {
-            s = __dadd_rn(s, (double)slot.q[t]);
-            if (qp.dist == 1) {
-                su = __dadd_rn(su, (double)slot.U[t]);
-                sl = __dadd_rn(sl, (double)slot.L[t]);
+    // FP64 segment means, each a sequential sum in index order: one warp per
+    // segment reads 32 points at a time and adds them in turn from shuffles
+    // (every lane carries the same sum)
+    const int lane = tid & 31, wib = tid >> 5;
+    for (int sg = wib; sg < w; sg += (int)(blockDim.x >> 5)) {
+        double sm = 0.0, su = 0.0, sl = 0.0;
+        for (int base = sg * m; base < (sg + 1) * m; base += 32) {
+            const int t = base + lane, cnt = min(32, (sg + 1) * m - base);
+            const float v = lane < cnt ? slot.q[t] : 0.f;
+            const float vu = (qp.dist == 1 && lane < cnt) ? slot.U[t] : 0.f;
+            const float vl = (qp.dist == 1 && lane < cnt) ? slot.L[t] : 0.f;
+            for (int j = 0; j < cnt; ++j) {
+                sm = __dadd_rn(sm, (double)__shfl_sync(0xffffffffu, v, j));
+                if (qp.dist == 1) {
+                    su = __dadd_rn(su, (double)__shfl_sync(0xffffffffu, vu, j));
+                    sl = __dadd_rn(sl, (double)__shfl_sync(0xffffffffu, vl, j));
+                }
             }
         }
-        paa[tid] = __ddiv_rn(s, (double)m);
-        paaU[tid] = __ddiv_rn(su, (double)m);
-        paaL[tid] = __ddiv_rn(sl, (double)m);
-        int lo = 0, hi = card - 1;
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (sbeta[mid] <= paa[tid]) lo = mid + 1; else hi = mid;
+        if (lane == 0) {
+            paa[sg] = __ddiv_rn(sm, (double)m);
+            paaU[sg] = __ddiv_rn(su, (double)m);
+            paaL[sg] = __ddiv_rn(sl, (double)m);
+            int lo = 0, hi = card - 1;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (sbeta[mid] <= paa[sg]) lo = mid + 1; else hi = mid;
+            }
+            sym[sg] = lo;
         }
-        sym[tid] = lo;
     }
     __syncthreads();
     // table: T[s][v] = m * d^2, every step rounded toward -inf
@@ -165,12 +183,15 @@ __device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams
             const int s = e / kMaxCard, v = e % kMaxCard;
             slot.lut[e] = s < w ? table_entry(s, v, w, card, m, qp.dist, paa[s], paaU[s], paaL[s], sbeta) : 0.f;
         }
-    if (tid == 0) {
-        // interleaved key of the query word
+    __shared__ uint4 qkey;
+    if (wib == 0) {
+        // interleaved key of the query word: for each bit plane j, the j-th
+        // most significant bit of every segment's symbol, segment 0 first
+        const int sy = lane < w ? sym[lane] : 0;
         unsigned long long khi = 0ull, klo = 0ull;
         for (int j = 0; j < iv.bits; ++j) {
-            unsigned field = 0u;
-            for (int s = 0; s < w; ++s) field = (field << 1) | ((sym[s] >> (iv.bits - 1 - j)) & 1);
+            const unsigned mask = __ballot_sync(0xffffffffu, lane < w && ((sy >> (iv.bits - 1 - j)) & 1));
+            const unsigned field = __brev(mask) >> (32 - w);
             khi = (khi << w) | (klo >> (64 - w));
             klo = (klo << w) | field;
         }
@@ -180,22 +201,35 @@ __device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams
             if (sh >= 64) { khi = klo << (sh - 64); klo = 0ull; }
             else { khi = (khi << sh) | (klo >> (64 - sh)); klo <<= sh; }
         }
-        const uint4 qk = make_uint4((unsigned)(khi >> 32), (unsigned)khi, (unsigned)(klo >> 32), (unsigned)klo);
-        st->qkey = qk;
-        // per segment a symbol where the table is 0: the query's own symbol
-        // (for DTW it lies between the envelope's symbols, where the table is 0)
-        unsigned qs[4] = {0u, 0u, 0u, 0u};
-        for (int s = 0; s < w; ++s) qs[s >> 2] |= (unsigned)sym[s] << (8 * (s & 3));
-        st->qsym = make_uint4(qs[0], qs[1], qs[2], qs[3]);
-        // seed leaf: the last leaf whose first key is <= the query key
-        unsigned long long lo = 0, hi = iv.L;   // count of leaves with key <= qk
-        while (lo < hi) {
-            unsigned long long mid = (lo + hi) >> 1;
-            const uint4 k = iv.leaf_key[mid];
-            bool le = (k.x != qk.x) ? k.x < qk.x : (k.y != qk.y) ? k.y < qk.y
-                    : (k.z != qk.z) ? k.z < qk.z : k.w <= qk.w;
-            if (le) lo = mid + 1; else hi = mid;
+        if (lane == 0) {
+            const uint4 qk = make_uint4((unsigned)(khi >> 32), (unsigned)khi, (unsigned)(klo >> 32), (unsigned)klo);
+            qkey = qk;
+            st->qkey = qk;
+            // per segment a symbol where the table is 0: the query's own symbol
+            // (for DTW it lies between the envelope's symbols, where the table is 0)
+            unsigned qs[4] = {0u, 0u, 0u, 0u};
+            for (int sg = 0; sg < w; ++sg) qs[sg >> 2] |= (unsigned)sym[sg] << (8 * (sg & 3));
+            st->qsym = make_uint4(qs[0], qs[1], qs[2], qs[3]);
         }
+    }
+    __syncthreads();
+    // seed leaf: the last leaf whose first key is <= the query key.  The count
+    // of such leaves (the keys ascend) lies in [lo, hi]; each round every
+    // thread tests one of blockDim.x evenly spaced pivots and the count of
+    // true answers narrows the range about blockDim.x + 1 times.
+    const uint4 qk = qkey;
+    unsigned long long lo = 0, hi = iv.L;
+    const unsigned nb = blockDim.x;
+    while (hi - lo > nb) {
+        const unsigned long long step = (hi - lo + nb) / (nb + 1);
+        const unsigned long long piv = lo + (tid + 1) * step - 1;
+        const int c = __syncthreads_count(piv < hi && key_le(iv.leaf_key[piv], qk));
+        const unsigned long long nlo = lo + (unsigned long long)c * step;
+        if ((unsigned)c < nb) hi = min(hi, lo + (unsigned long long)(c + 1) * step - 1);
+        lo = nlo;
+    }
+    lo += (unsigned long long)__syncthreads_count(lo + tid < hi && key_le(iv.leaf_key[lo + tid], qk));
+    if (tid == 0) {
         const unsigned long long leaf = lo > 0 ? lo - 1 : 0;
         unsigned long long a = iv.leaf_off[leaf], b = iv.leaf_off[leaf + 1];
         if (b - a > (unsigned long long)kSeedMax) b = a + kSeedMax;
@@ -239,18 +273,26 @@ __device__ __forceinline__ void prep_table_row(const IndexView &iv, const QueryP
             dn_pts[i] = dn;
         }
     __syncthreads();
-    if (tid == 0) {   // sequential FP64 sums, in prep_body's order
+    if (tid < 32) {   // sequential FP64 sums in prep_body's order, 32 points per load
         double a = 0.0, au = 0.0, al = 0.0;
-        for (int i = 0; i < m; ++i) {
-            a = __dadd_rn(a, (double)query[s * m + i]);
-            if (qp.dist == 1) {
-                au = __dadd_rn(au, (double)up_pts[i]);
-                al = __dadd_rn(al, (double)dn_pts[i]);
+        for (int base = 0; base < m; base += 32) {
+            const int cnt = min(32, m - base);
+            const float v = tid < cnt ? query[s * m + base + tid] : 0.f;
+            const float vu = (qp.dist == 1 && tid < cnt) ? up_pts[base + tid] : 0.f;
+            const float vl = (qp.dist == 1 && tid < cnt) ? dn_pts[base + tid] : 0.f;
+            for (int j = 0; j < cnt; ++j) {
+                a = __dadd_rn(a, (double)__shfl_sync(0xffffffffu, v, j));
+                if (qp.dist == 1) {
+                    au = __dadd_rn(au, (double)__shfl_sync(0xffffffffu, vu, j));
+                    al = __dadd_rn(al, (double)__shfl_sync(0xffffffffu, vl, j));
+                }
             }
         }
-        ps = __ddiv_rn(a, (double)m);
-        psu = __ddiv_rn(au, (double)m);
-        psl = __ddiv_rn(al, (double)m);
+        if (tid == 0) {
+            ps = __ddiv_rn(a, (double)m);
+            psu = __ddiv_rn(au, (double)m);
+            psl = __ddiv_rn(al, (double)m);
+        }
     }
     __syncthreads();
     for (int v = tid; v < kMaxCard; v += blockDim.x)

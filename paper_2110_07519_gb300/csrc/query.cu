@@ -86,6 +86,16 @@ __device__ __forceinline__ float table_entry(int s, int v, int w, int card, int 
     return __double2float_rd(__dmul_rd(__dmul_rd(d, d), (double)m));
 }
 
+// 1/m for m a power of two, built from its exponent bits.  A sum of at most
+// 4096 floats divided by such an m neither overflows nor leaves the normal
+// range of a double, so multiplying by 1/m gives the quotient exactly: the
+// same bits as the correctly rounded division.
+__device__ __forceinline__ double pow2_recip(int m)
+{
+    const int e = __ffs(m) - 1;   // m = 2^e
+    return __longlong_as_double((long long)(1023 - e) << 52);
+}
+
 // k <= q in the order of the 128-bit interleaved keys (x most significant)
 __device__ __forceinline__ bool key_le(const uint4 k, const uint4 q)
 {
@@ -165,9 +175,10 @@ __device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams
             }
         }
         if (lane == 0) {
-            paa[sg] = __ddiv_rn(sm, (double)m);
-            paaU[sg] = __ddiv_rn(su, (double)m);
-            paaL[sg] = __ddiv_rn(sl, (double)m);
+            const double inv_m = pow2_recip(m);
+            paa[sg] = __dmul_rn(sm, inv_m);
+            paaU[sg] = __dmul_rn(su, inv_m);
+            paaL[sg] = __dmul_rn(sl, inv_m);
             int lo = 0, hi = card - 1;
             while (lo < hi) {
                 int mid = (lo + hi) >> 1;
@@ -208,7 +219,9 @@ __device__ __forceinline__ void prep_body(const IndexView &iv, const QueryParams
             // per segment a symbol where the table is 0: the query's own symbol
             // (for DTW it lies between the envelope's symbols, where the table is 0)
             unsigned qs[4] = {0u, 0u, 0u, 0u};
-            for (int sg = 0; sg < w; ++sg) qs[sg >> 2] |= (unsigned)sym[sg] << (8 * (sg & 3));
+#pragma unroll
+            for (int sg = 0; sg < kMaxSegments; ++sg)
+                if (sg < w) qs[sg >> 2] |= (unsigned)sym[sg] << (8 * (sg & 3));
             st->qsym = make_uint4(qs[0], qs[1], qs[2], qs[3]);
         }
     }
@@ -289,9 +302,10 @@ __device__ __forceinline__ void prep_table_row(const IndexView &iv, const QueryP
             }
         }
         if (tid == 0) {
-            ps = __ddiv_rn(a, (double)m);
-            psu = __ddiv_rn(au, (double)m);
-            psl = __ddiv_rn(al, (double)m);
+            const double inv_m = pow2_recip(m);
+            ps = __dmul_rn(a, inv_m);
+            psu = __dmul_rn(au, inv_m);
+            psl = __dmul_rn(al, inv_m);
         }
     }
     __syncthreads();

@@ -1,4 +1,4 @@
-"""CPU models of two block-parallel steps of the query preparation (k_prep,
+"""CPU models of three steps of the query preparation (k_prep,
 csrc/query.cu), checked against their plain definitions.
 
 * Seed leaf (approxSearch, Sec. 3.1): the count of leaves whose first key is
@@ -12,6 +12,9 @@ csrc/query.cu), checked against their plain definitions.
   0 first.  The kernel collects each plane with one warp ballot (lane s holds
   segment s) and bit-reverses it; the definition is the bit-by-bit
   interleaving.
+* Segment means (Sec. 2.2, PAA): the FP64 sum of a segment's floats divided
+  by m, a power of two; the kernel multiplies by 1/m built from its exponent
+  bits, which must give the same bits as the division.
 """
 import bisect
 import random
@@ -111,3 +114,31 @@ def test_ballot_key_model_catches_a_missing_bit_reversal():
     assert interleave_ballot(sym, w, bits) == 1 << 127
     unreversed = 1 << (128 - w)               # the raw ballot, shifted to the top
     assert unreversed != interleave_bitwise(sym, w, bits)
+
+
+def pow2_recip_bits(m):
+    """The kernel's 1/m for m = 2^e: exponent field 1023 - e, mantissa 0."""
+    import struct
+    e = m.bit_length() - 1
+    return struct.unpack("<d", struct.pack("<q", (1023 - e) << 52))[0]
+
+
+@pytest.mark.parametrize("m", [4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096])
+def test_segment_mean_by_reciprocal_equals_division(m):
+    # the PAA of a segment is (sequential FP64 sum of its floats) / m; the
+    # kernel multiplies by the exact 1/m instead, which must give the same bits
+    import numpy as np
+    assert pow2_recip_bits(m) == 1.0 / m
+    rng = np.random.default_rng(m)
+    tiny = np.float32(1.4e-45)                 # the smallest subnormal float
+    cases = [rng.standard_normal(m).astype(np.float32) * s for s in (1e-38, 1e-3, 1.0, 1e30)]
+    cases.append(np.full(m, np.finfo(np.float32).max, dtype=np.float32))
+    cases.append(np.full(m, -np.finfo(np.float32).max, dtype=np.float32))
+    cases.append(np.array([tiny] + [0.0] * (m - 1), dtype=np.float32))
+    cases.append(np.array([tiny, -tiny] * (m // 2), dtype=np.float32))
+    for x in cases:
+        s = 0.0
+        for v in x:
+            s += float(v)
+        assert s * pow2_recip_bits(m) == s / m
+        assert np.float64(s * pow2_recip_bits(m)).tobytes() == np.float64(s / m).tobytes()
